@@ -1,0 +1,333 @@
+"""Benchmark: MPR reconstructions per second on one GB300 (and N GPUs, weak scaling).
+
+A step is one full MPR reconstruction (Alg. mpr: initialise, G generations of crossover,
+self-improvement of both populations and selection, then the aligned average) of one
+synthetic 512 x 512 single-shot pattern with P = 64 (2P = 128 individuals improved per
+generation), 10 generations x 200 RAAR iterations.  Inputs are synthetic (seeded), shaped
+like the paper's binned pnCCD data: beamstop, detector gap, saturation, Poisson noise.
+
+  value  : reconstructions/s with the pattern already resident on the device
+  e2e    : the same through the C ABI from host buffers (upload, run, download per step)
+  roofline: the dominant per-iteration kernel's algorithmic bytes / its average CUDA-event
+           duration, against the measured HBM copy bandwidth
+  cpu_baseline: the FP64 oracle on this host's cores over a bounded sample of the work
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+WORKLOADS = {
+    # name: (pattern recipe, seed, params)
+    "ell512": ("ell512", 0, dict(pop=64, iters_per_gen=200, generations=10, algorithm=2, beta=0.9,
+                                 sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
+    "sphere64": ("sphere64", 0, dict(pop=8, iters_per_gen=100, generations=5, algorithm=2, beta=0.9,
+                                     sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
+}
+PEAKS = ROOT / "MEASURED_PEAKS.json"
+GOLDEN_ORACLE = ROOT / "tests" / "golden" / "oracle_errors.json"
+
+
+def pixels_per_reconstruction(n, prm):
+    return 2 * prm["pop"] * prm["iters_per_gen"] * prm["generations"] * n * n
+
+
+def hbm_peak():
+    try:
+        d = json.loads(PEAKS.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for l in self.proc.stdout:
+            self.lines.append(l.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [c.strip() for c in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(pattern, prm, seconds=15.0):
+    """Time the FP64 oracle's self-improvement on a bounded sample of the workload."""
+    import oracle
+    n = pattern.n
+    I = np.fft.ifftshift(pattern.intensities.astype(np.float64))
+    mask = np.fft.ifftshift(pattern.mask)
+    M = np.sqrt(I)
+    cores = oracle.get_threads()
+    batch = cores
+    K = prm["sw_period"]
+    p = oracle.make_params(**{**prm, "iters_per_gen": 2 * K, "er_tail": min(prm["er_tail"], K)})
+    x = oracle.initialize(1, pattern.support0, I, mask, batch)
+    S = np.broadcast_to(pattern.support0, x.shape).copy()
+    a = int(pattern.support0.sum())
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        x, S, _ = oracle.improve(x, S, M, mask, p, prm["sw_sigma"], prm["sw_threshold"], a, a)
+        reps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    it_px = reps * batch * 2 * K * n * n
+    rate = it_px / dt
+    return {
+        "it_px_per_s": rate,
+        "value": rate / pixels_per_reconstruction(n, prm),
+        "cores": cores,
+        "seconds": dt,
+        "sample": f"{reps} self-improvement pass(es) of {batch} individuals x {2 * K} iterations "
+                  f"(RAAR + ER tail + shrink-wrap + error) at {n}x{n}; rate scaled by "
+                  f"{pixels_per_reconstruction(n, prm):.3g} iteration-pixels per reconstruction",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2409_07413_gb300 import synthetic
+    name, seed, prm = WORKLOADS[wl]
+    pat = synthetic.config_pattern(name, seed)
+    per = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(pat, prm, seconds=min(per, 3.0))
+    vals, cores, sample = [], 0, ""
+    for _ in range(args.steps):
+        r = oracle_sample(pat, prm, seconds=per)
+        vals.append(r["value"])
+        cores, sample = r["cores"], r["sample"]
+    v = statistics.mean(vals)
+    out = {
+        "impl": "reference", "metric": "MPR reconstructions/s", "value": v,
+        "unit": "reconstructions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / v if v > 0 else None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl, "n": pat.n, **prm},
+        "cpu_baseline": {"value": v, "unit": "reconstructions/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "reconstructions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, wl):
+    import torch
+
+    from paper_2409_07413_gb300 import spring, synthetic
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    name, seed, prm = WORKLOADS[wl]
+    pat = synthetic.config_pattern(name, seed)
+    n = pat.n
+    p = spring.params(**prm, seed=1000 + rank, use_graph=int(args.graph))
+    ctx = spring.Context(local)
+    dI = torch.from_numpy(pat.intensities).cuda()
+    dm = torch.from_numpy(pat.mask).cuda()
+    dS = torch.from_numpy(pat.support0).cuda()
+    prob = ctx.problem_device(dI, dm, dS)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        prob.run(p, want_arrays=False)
+    # ---- device-resident timed region
+    clocks = Clocks(local)
+    spring.stats_reset()
+    spring.stats_enable_timing(True)
+    barrier()
+    clocks.start()
+    l0 = spring.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, errs = [], []
+    ev0.record()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = prob.run(p, want_arrays=False)
+        step_ms.append(1000.0 * (time.perf_counter() - t0))
+        errs.append((r["final_error_avg"], r["final_error_best"]))
+    ev1.record()
+    barrier()
+    clk = clocks.stop()
+    launches = spring.launch_count() - l0
+    spring.stats_enable_timing(False)
+    ms = ev0.elapsed_time(ev1)
+    kst = {kc: spring.stats_get(kc) for kc in (spring.KC_ROW_ITER, spring.KC_COL_PM)}
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1000.0)
+
+    # ---- end to end through the C ABI from host buffers
+    h2d = pat.intensities.nbytes + pat.mask.nbytes + pat.support0.nbytes
+    d2h = 2 * n * n * 8 + n * n + prm["generations"] * 8 * 8 + 5 * 8
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        hp = ctx.problem(pat.intensities, pat.mask, pat.support0)
+        hp.run(p, want_arrays=True)
+        hp.destroy()
+    barrier()
+    te = time.perf_counter() - te0
+    e2e = ws * max(1, args.steps) / te
+
+    out = None
+    if rank == 0:
+        peak, peak_kind = hbm_peak()
+        dom = max(kst.items(), key=lambda kv: kv[1].total_ms)
+        kc, st = dom
+        avg_ms = st.total_ms / max(1, st.timed)
+        achieved = st.bytes_per_launch / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else None
+        other = kst[spring.KC_COL_PM if kc == spring.KC_ROW_ITER else spring.KC_ROW_ITER]
+        oavg = other.total_ms / max(1, other.timed)
+        traffic = None
+        prof = ROOT / "profiles" / "traffic.json"
+        if prof.exists():
+            try:
+                traffic = json.loads(prof.read_text()).get({0: "row_iter", 1: "col_pm"}[kc])
+            except Exception:
+                traffic = None
+        golden = {}
+        if GOLDEN_ORACLE.exists():
+            golden = json.loads(GOLDEN_ORACLE.read_text()).get(wl, {})
+        cpu = None
+        if ws == 1 and not args.no_cpu:
+            cpu = oracle_sample(pat, prm, seconds=args.cpu_seconds)
+            cpu = {k: cpu[k] for k in ("value", "cores", "sample")} | {"unit": "reconstructions/s",
+                                                                        "kind": "oracle"}
+        ea = [e[0] for e in errs]
+        eb = [e[1] for e in errs]
+        out = {
+            "metric": "MPR reconstructions/s", "value": value, "unit": "reconstructions/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{wl}: {n}x{n}, P={prm['pop']} (2P={2 * prm['pop']} improved), "
+                                   f"G={prm['generations']} x {prm['iters_per_gen']} RAAR iterations",
+                       "n": n, **prm, "l2": "inputs larger than L2 (run state 2P x N^2 x 25 B = "
+                                              f"{2 * prm['pop'] * n * n * 25 / 2**20:.0f} MiB)",
+                       "graph": bool(args.graph)},
+            "iteration_pixels_per_s": value * pixels_per_reconstruction(n, prm),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "error": {"final_error_avg": statistics.mean(ea), "final_error_best": statistics.mean(eb),
+                      "oracle": golden or None},
+            "roofline": {"bound": "hbm", "kernel": {0: "row_iter", 1: "col_pm"}[kc],
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "bytes_per_launch": st.bytes_per_launch, "avg_launch_ms": avg_ms,
+                         "launches_timed": st.timed,
+                         "other_kernel": {"name": {0: "row_iter", 1: "col_pm"}[1 - kc],
+                                          "avg_launch_ms": oavg,
+                                          "achieved": other.bytes_per_launch / (oavg / 1000.0) / 1e9 if oavg > 0 else None}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "reconstructions/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    prob.destroy()
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ell512", choices=sorted(WORKLOADS))
+    ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args, args.workload)
+    else:
+        run_ours(args, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,283 @@
+/* spring.h -- C ABI of libspring, a GB300 (sm_103a) implementation of the data-parallel
+ * hot path of Memetic Phase Retrieval (MPR), after Colombo et al., "SPRING: an effective
+ * and reliable framework for image reconstruction in single-particle Coherent
+ * Diffraction Imaging" (arXiv 2409.07413).  Citations name the paper's sections,
+ * equations and algorithms.
+ *
+ * General conventions (every entry point):
+ *  - Status: every call returns a spring_status; SPRING_OK = 0.  The library never
+ *    aborts.  On failure a message is kept for the calling thread (spring_last_error).
+ *  - Complex arrays are complex64: interleaved (re, im) float32 pairs, row-major N x N
+ *    per image, images contiguous (batch x N x N).
+ *  - Real-space arrays (densities, supports) are used in the caller's orientation.
+ *    Fourier-space arrays given to the problem API (intensities, mask) are
+ *    detector-centred (zero frequency at (N/2, N/2)); the operator API below takes them
+ *    in DFT order (zero frequency at index 0).
+ *  - The 2D Fourier transform is unitary (factor 1/N on an N x N transform, both
+ *    directions), so that sum |rho|^2 = sum |FT rho|^2 (App. "Initialization of the
+ *    starting densities").
+ *  - Modulus encoding (operator API): M is N x N float32 in DFT order; an entry >= 0 is
+ *    the measured modulus sqrt(I) (mask Xi = 1), an entry < 0 marks a pixel whose
+ *    intensity is not measured (Xi = 0: beamstop/hole, detector gap, saturation).
+ *  - Supports and masks are uint8, 0 or 1.
+ *  - Sizes: N in {64, 128, 192, 256, 512, 1024} (square patterns; N = 2^a or 3 * 2^a).
+ *    Other sizes return SPRING_E_INVALID.
+ *  - Streams: the operator API takes a cudaStream_t as void* (NULL = legacy default
+ *    stream) and is asynchronous on it; device pointers must be valid on the current
+ *    device.  Scratch memory is taken from the stream-ordered allocator of the current
+ *    device and returned before the call's work completes (stream order).
+ *  - Ownership: the library never takes ownership of caller buffers.  Handles
+ *    (contexts, problems) are released by their destroy/shutdown call.
+ */
+#ifndef SPRING_H
+#define SPRING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPRING_ABI_VERSION 1
+
+typedef enum {
+  SPRING_OK = 0,
+  SPRING_E_INVALID = 1,   /* bad argument: size, pointer, parameter range */
+  SPRING_E_NOMEM = 2,     /* device memory or HBM budget exhausted */
+  SPRING_E_CUDA = 3,      /* a CUDA runtime error (message via spring_last_error) */
+  SPRING_E_BUSY = 4,      /* not ready yet / still in use */
+  SPRING_E_TIMEOUT = 5,   /* a bounded wait ran out */
+  SPRING_E_NOT_FOUND = 6, /* unknown ticket */
+  SPRING_E_NUMERIC = 7,   /* NaN/Inf met in a reduction */
+  SPRING_E_CANCELLED = 8  /* the ticket was cancelled before it completed */
+} spring_status;
+
+typedef struct spring_ctx spring_ctx;         /* device, streams, HBM budget, scheduler */
+typedef struct spring_problem spring_problem; /* one diffraction pattern resident on device */
+
+/* Parameters of one MPR run (Table "params" of App. "Summary of the parameters and
+ * further considerations").  spring_params_default() fills the defaults shown. */
+typedef struct {
+  int pop;                 /* P >= 4, population size (default 8) */
+  int iters_per_gen;       /* iterations per individual per generation (100) */
+  int generations;         /* G >= 1 (5) */
+  int algorithm;           /* IA of the main sequence: 0 ER, 1 HIO, 2 RAAR (2) */
+  float beta;              /* HIO/RAAR beta in (0, 1] (0.9) */
+  float sw_sigma;          /* shrink-wrap Gaussian sigma, px (1.5) */
+  float sw_threshold;      /* shrink-wrap threshold tau in (0, 1] (0.2) */
+  float sw_sigma_end;      /* sigma at the last generation, linear in between (= sw_sigma) */
+  float sw_threshold_end;  /* tau at the last generation (= sw_threshold) */
+  int sw_period;           /* K: iterations between support updates (20) */
+  int er_tail;             /* ER iterations of the evaluation sequence (10) */
+  float chi;               /* phase range [-chi pi, chi pi]; 0.5 = positivity, >= 1 off (0.5) */
+  float cw;                /* crossover differential weight C_w in [0, 2] (0.4) */
+  float cp;                /* crossover tile probability C_p in [0, 1] (0.6) */
+  int tile_min, tile_max;  /* crossover tile sides; tile_max 0 = N/8 (4, 0) */
+  int init_n_spheres;      /* spheres per initial density N_init (5) */
+  float init_gamma;        /* gamma applied to |rho| at initialisation (1) */
+  float init_phi_max;      /* sphere phases uniform in [-phi_max, phi_max] (0) */
+  int precision;           /* 0: complex64 state; 1: FP16 storage, FP32 math (0) */
+  int use_graph;           /* 1: capture the run in a CUDA graph before launching (0) */
+  uint64_t seed;           /* key of the counter-based generator (0) */
+} spring_params;
+
+/* Result of one run.  Pointer members are caller-owned host buffers (may be NULL). */
+typedef struct {
+  float* rho_avg;          /* N*N complex64: average of the aligned population (Alg. mpr) */
+  float* rho_best;         /* N*N complex64: lowest-error individual */
+  uint8_t* support_avg;    /* N*N: union of the aligned supports (Eq. avgrec) */
+  double* gen_stats;       /* G x 8 per generation: best E, mean E, worst E, E(avg) (last
+                              generation only, else NaN), O_d (Eq. oversampling),
+                              replacement factor, mean complexity Gamma (Eq. complexity),
+                              mean |sum rho|; may be NULL */
+  double final_error_avg;  /* GetError (Eq. error_calc) of rho_avg on support_avg */
+  double final_error_best; /* error of rho_best */
+  double t_submit_s, t_admit_s, t_done_s; /* serving timestamps (monotonic seconds) */
+} spring_result;
+
+/* ---------------------------------------------------------------- context, errors */
+int spring_abi_version(void);
+const char* spring_status_string(spring_status s);
+/* Message of the last failed call made by this thread ("" if none).  Owned by the
+ * library; valid until the thread's next call. */
+const char* spring_last_error(void);
+void spring_params_default(spring_params* p);
+
+/* Open a context on CUDA device `device`.  hbm_budget_bytes bounds what the context's
+ * runs and admitted requests may hold on the device (0 = 90% of free memory at open).
+ * Starts the serving scheduler thread.  Errors: INVALID (device), CUDA. */
+spring_status spring_init(int device, size_t hbm_budget_bytes, spring_ctx** out);
+/* Close a context: BUSY if tickets are still queued or running (cancel or poll them
+ * first); otherwise stops the scheduler and frees the context. */
+spring_status spring_shutdown(spring_ctx* ctx);
+
+/* ---------------------------------------------------------------- problems
+ * The problem statement of the paper (Sec. "The phase problem and conventional
+ * approaches"; Eq. error_calc): measured intensities I = M^2, the mask Xi of measured
+ * pixels and an initial support.  I and mask are detector-centred host arrays of
+ * ny x nx (ny == nx == N); I >= 0 (negative values are treated as 0); support0 is in
+ * real space.  The library copies them to the device (M = sqrt(I) in DFT order, with
+ * the mask folded into M's sign); the caller keeps its arrays.
+ * Errors: INVALID (sizes, NULL), NOMEM, CUDA. */
+spring_status spring_problem_create(spring_ctx* ctx, int ny, int nx, const float* intensities,
+                                    const uint8_t* mask, const uint8_t* support0,
+                                    spring_problem** out);
+/* Same, from device buffers (e.g. torch tensors) on `stream` (cudaStream_t as void*).
+ * The call is asynchronous: the inputs must stay valid until `stream` reaches it. */
+spring_status spring_problem_create_device(spring_ctx* ctx, int ny, int nx,
+                                           const float* d_intensities, const uint8_t* d_mask,
+                                           const uint8_t* d_support0, void* stream,
+                                           spring_problem** out);
+/* BUSY if an unfinished ticket still references the problem. */
+spring_status spring_problem_destroy(spring_problem* prob);
+/* Device bytes one run of an N x N problem with parameters p holds (admission). */
+size_t spring_footprint_bytes(int n, const spring_params* p);
+
+/* ---------------------------------------------------------------- runs
+ * One blocking MPR reconstruction (Alg. mpr): Initialize; G x {Crossover (Alg.
+ * crossover), Improve of both populations (Alg. improve), Select (Alg. select)};
+ * Average.  Results go to the caller's buffers in *out.
+ * Errors: INVALID (parameters), NOMEM (budget), CUDA, NUMERIC. */
+spring_status spring_mpr_run(spring_problem* prob, const spring_params* p, spring_result* out);
+
+/* Serving: queue a run; requests are admitted while their footprint fits the HBM budget
+ * and advance concurrently on the device (continuous batching).  *ticket identifies the
+ * request.  The problem must stay alive until the ticket is polled or cancelled. */
+spring_status spring_submit(spring_ctx* ctx, spring_problem* prob, const spring_params* p,
+                            uint64_t* ticket);
+/* Wait up to timeout_us (0 = do not wait, < 0 = wait forever) for a ticket.  SPRING_OK
+ * fills *out (buffers as for spring_mpr_run) and retires the ticket; BUSY = not done yet;
+ * NOT_FOUND = unknown or already retired; CANCELLED; or the run's own error. */
+spring_status spring_poll(spring_ctx* ctx, uint64_t ticket, int timeout_us, spring_result* out);
+/* Cancel a queued or running ticket (it stops at its next generation boundary). */
+spring_status spring_cancel(spring_ctx* ctx, uint64_t ticket);
+
+/* ---------------------------------------------------------------- operators
+ * The steps of the hot path on caller device buffers.  The run above is composed of
+ * exactly these kernels.  All are asynchronous on `stream`. */
+
+/* a1/a3: unitary 2D DFT of `batch` complex64 images in place (inverse != 0: F^-1). */
+spring_status spring_fft2(void* data, int batch, int n, int inverse, void* stream);
+
+/* a1-a3: out = P_M x = F^-1[ M F x / |F x| where Xi = 1, F x elsewhere ]
+ * (Eq. pm with the masked form Eq. pm_full; a zero modulus takes phase 0).
+ * x and out: batch images (may alias).  M: one pattern shared by the batch. */
+spring_status spring_project_modulus(const void* x, void* out, const float* M, int batch,
+                                     int n, void* stream);
+
+/* a1-a4: n_iter iterations x <- U(x, P_M x) in place, U = ER (algorithm 0), HIO (1) or
+ * RAAR (2) (Sec. "The phase problem and conventional approaches"; ER = P_M P_S of
+ * App. "The phase problem as an optimization problem").  Per pixel, with m = P_M x and
+ * C = {S = 1 and |arg m| <= chi pi} (App. "Real-space constraints"):
+ *   ER: x' = m on C, 0 elsewhere;  HIO: x' = m on C, x - beta m elsewhere;
+ *   RAAR: x' = m on C, beta x + (1 - 2 beta) m elsewhere.
+ * S: batch supports.  Scratch: one batch x N x N complex64 work buffer. */
+spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batch, int n,
+                             int algorithm, float beta, float chi, int n_iter, void* stream);
+
+/* a5 smoothing: out = periodic convolution of |x| with the separable normalised Gaussian
+ * of width sigma (taps d = -r..r, r = ceil(4 sigma)); sigma = 0 copies |x|.
+ * out: batch x N x N float32.  sigma <= 64. */
+spring_status spring_smooth(const void* x, float* out, int batch, int n, float sigma,
+                            void* stream);
+/* a5 UpdateSupport (Eq. shrinkwrap): S = [rho_sigma >= tau max(rho_sigma)], per image.
+ * Scratch: the smoothed map and per-image maxima. */
+spring_status spring_update_support(const void* x, uint8_t* S, int batch, int n, float sigma,
+                                    float tau, void* stream);
+/* a5 UpdateSupportSize (App. "The modified Shrink-wrap"): S = the alpha[b] pixels of
+ * largest rho_sigma (equal values taken in increasing linear index), so the area is
+ * exactly alpha[b] (clamped to [0, N^2]).  alpha: DEVICE array of `batch` int64. */
+spring_status spring_update_support_size(const void* x, uint8_t* S, int batch, int n,
+                                         float sigma, const int64_t* alpha, void* stream);
+
+/* a6 GetError (Eq. error_calc): err[b] = sqrt( sum_Xi (|F[S x]| - M)^2 / sum_Xi M^2 ),
+ * accumulated in FP64 in a fixed order (deterministic).  err: DEVICE double[batch].
+ * Scratch: one work image per batch entry and per-block partial sums. */
+spring_status spring_fourier_error(const void* x, const uint8_t* S, const float* M, int batch,
+                                   int n, double* err, void* stream);
+
+/* a7 area bookkeeping (Alg. improve, first three steps) on the parent population:
+ * out[0] = alpha_best = area of the support of argmin err (ties: lowest index; err NULL:
+ * individual 0), out[1] = alpha_all = area of the union of the P supports,
+ * out[2] = alpha_eval = round_half_up((g alpha_best + (G - g) alpha_all) / G), exactly.
+ * out: DEVICE int64[3]. */
+spring_status spring_area_stats(const uint8_t* S, const double* err, int P, int n, int g,
+                                int G, int64_t* out, void* stream);
+
+/* a9 RandomChoice (App. "Crossover"): for each p < P three distinct parents a, b, c, all
+ * != p, from Philox-4x32-10 keyed by seed at counter (g, p, 1 << 24, 0).  abc: DEVICE
+ * int32[P x 3].  Integer draws are floor(u32 * m / 2^32) among the remaining candidates,
+ * then the excluded indices are skipped in increasing order. */
+spring_status spring_random_choice(uint64_t seed, int g, int P, int32_t* abc, void* stream);
+/* a9 CrossoverMap (App. "Crossover", Fig. crossmap) of individual p at generation g:
+ * map: DEVICE uint8[N x N] in DFT order.  tile_max 0 = N/8. */
+spring_status spring_crossover_map(uint64_t seed, int g, int p, int n, int tile_min,
+                                   int tile_max, float cp, uint8_t* map, void* stream);
+
+/* a8 Reshift (App. "Aligning the reconstructions", Eq. crosscorr): align each x[b] (and
+ * S[b]) onto ref[b]: c = F^-1[Xi conj(F x) F ref], c_t = F^-1[Xi F x F ref]; the larger
+ * peak of |c|, |c_t| picks the twin (ties: not twin), its position s the shift (ties:
+ * lowest linear index), its phase phi the global phase;
+ *   x'(r) = e^{i phi} x(r - s)   or   e^{i phi} conj(x(s - r)).
+ * x_out/S_out may be NULL; info: DEVICE int32[batch x 3] = (s_y, s_x, twin) or NULL;
+ * phase: DEVICE float[batch] or NULL.  Scratch: spectra and correlations. */
+spring_status spring_reshift(const void* x, const uint8_t* S, const void* ref, const float* M,
+                             int batch, int n, void* x_out, uint8_t* S_out, int32_t* info,
+                             float* phase, void* stream);
+
+/* a8+a9 Crossover (Alg. crossover) of a population of P at generation g: new individual
+ * p mixes its parents a, b, c aligned onto p, in Fourier space:
+ *   F x_new = F a' + cw (F b' - F c')  on the crossover map,  F x_p elsewhere;
+ *   S_new = S_a' OR (S_b' AND S_c' AND S_p).
+ * parents: DEVICE int32[P x 3] (output) or NULL. */
+spring_status spring_crossover(const void* pop_x, const uint8_t* pop_S, const float* M, int P,
+                               int n, uint64_t seed, int g, float cw, float cp, int tile_min,
+                               int tile_max, void* new_x, uint8_t* new_S, int32_t* parents,
+                               void* stream);
+
+/* a10 Select (Alg. select): for each p with new_err[p] < pop_err[p] (strict) copy the new
+ * density, support and error over the parent's.  replaced: DEVICE uint8[P] or NULL. */
+spring_status spring_select(void* pop_x, uint8_t* pop_S, double* pop_err, const void* new_x,
+                            const uint8_t* new_S, const double* new_err, int P, int n,
+                            uint8_t* replaced, void* stream);
+
+/* a12 Average (Eq. avgrec): every individual aligned onto the best (argmin err, ties:
+ * lowest index) and averaged; the support is the union of the aligned supports.
+ * avg: DEVICE complex64 N x N; S_avg: DEVICE uint8 N x N. */
+spring_status spring_average(const void* pop_x, const uint8_t* pop_S, const double* err,
+                             const float* M, int P, int n, void* avg, uint8_t* S_avg,
+                             void* stream);
+
+/* a11 Initialize (App. "Initialization of the starting densities"): P densities, each a
+ * sum of n_spheres projected spheres (thickness 2 sqrt(R^2 - d^2)) in the bounding square
+ * of S0 with diameters in [0.2, 0.9] of its side and phases in [-phi_max, phi_max]
+ * (Philox counter (0, p, 4 << 24 | sphere, 0)); then |rho|^gamma with the phase kept,
+ * restriction to S0, and the scale sqrt(nu) of Eq. norm.  x: DEVICE complex64 P x N x N. */
+spring_status spring_initialize(uint64_t seed, const uint8_t* S0, const float* M, int n, int P,
+                                int n_spheres, float gamma, float phi_max, void* x,
+                                void* stream);
+
+/* ---------------------------------------------------------------- instrumentation
+ * Per-kernel-class launch counts and (when enabled) CUDA-event durations recorded on the
+ * launching stream.  Used by the benchmark for its roofline figures. */
+typedef struct {
+  uint64_t launches;       /* launches since the last reset */
+  double total_ms;         /* summed event time (timing enabled only) */
+  uint64_t timed;          /* launches that were timed */
+  double bytes_per_launch; /* algorithmic bytes of the last launch */
+} spring_kernel_stat;
+#define SPRING_KC_ROW_ITER 0  /* iteration row pass (inverse row FFT, update, forward row FFT) */
+#define SPRING_KC_COL_PM 1    /* iteration column pass (column FFT, P_M, inverse column FFT) */
+#define SPRING_KC_OTHER 2     /* every other kernel of the library */
+#define SPRING_KC_COUNT 3
+void spring_stats_reset(void);
+void spring_stats_enable_timing(int on);
+void spring_stats_get(int kernel_class, spring_kernel_stat* out);
+/* Total kernel launches of the library since the last reset. */
+uint64_t spring_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPRING_H */

@@ -934,8 +934,9 @@ extern "C" int orc_mpr_run(const double* I_c, const uint8_t* mask_c, const uint8
     for (int p = 0; p < P; p++)
       for (size_t i = 0; i < nn; i++) uni[i] |= pS[p * nn + i];
     long a_all = area(uni.data(), nn);
-    double f = (double)g / (double)G;
-    long a_eval = (long)std::floor(f * a_best + (1.0 - f) * a_all + 0.5);
+    // alpha_eval = (g/G) alpha_best + (1 - g/G) alpha_all, rounded half up; evaluated
+    // exactly in integers so that no floating-point contraction can move a half-way case
+    long a_eval = (2L * ((long)g * a_best + (long)(G - g) * a_all) + G) / (2L * G);
     // Linear parameter schedule over generations (App. "Changing values over generations")
     double t = (G > 1) ? (double)(g - 1) / (double)(G - 1) : 0.0;
     double sigma = pr.sw_sigma + (pr.sw_sigma_end - pr.sw_sigma) * t;

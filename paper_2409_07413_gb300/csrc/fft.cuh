@@ -1,0 +1,295 @@
+// fft.cuh -- register / shared-memory Stockham FFT engine (sm_103a).
+//
+// A length-N transform is done by T = N / E threads; thread t holds E elements in
+// registers, v[m] = x[t + m T] on entry and X[t + m T] on exit (natural order both
+// ways, so global loads and stores of rows stay coalesced and a point-wise operation can
+// sit between a forward and an inverse transform without touching memory).
+//
+// Stage s of radix R (NS = product of the earlier radices) takes, for butterfly
+// j = t + u T (u < E/R), the inputs j + r N/R, multiplies input r by W_{NS R}^{(j mod NS) r},
+// does a radix-R DFT in registers and writes output r to (j / NS) NS R + (j mod NS) + r NS
+// (Stockham autosort).  Between stages the data goes through shared memory.  With
+// PAD the exchange layout of the stage that produced groups of L = NS R is
+// p(i) = i + (i / L) NS, which makes both the strided writes and the unit-stride reads of
+// a half-warp hit distinct banks (64-bit accesses) for power-of-two radices.
+//
+// Unnormalised: DIR = -1 computes sum x e^{-2 pi i k n / N}, DIR = +1 the conjugate sum.
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace spring {
+
+// cos(2 pi k / 32) for k = 0..8 (mathematical constants).
+__host__ __device__ constexpr double cos32_tab(int k) {
+  return k == 0 ? 1.0 : k == 1 ? 0.98078528040323044913 : k == 2 ? 0.92387953251128675613
+       : k == 3 ? 0.83146961230254523708 : k == 4 ? 0.70710678118654752440
+       : k == 5 ? 0.55557023301960222474 : k == 6 ? 0.38268343236508977173
+       : k == 7 ? 0.19509032201612826785 : 0.0;
+}
+__host__ __device__ constexpr double cos32(int k) {
+  return (k & 31) <= 8 ? cos32_tab(k & 31)
+       : (k & 31) <= 16 ? -cos32_tab(16 - (k & 31))
+       : (k & 31) <= 24 ? -cos32_tab((k & 31) - 16)
+       : cos32_tab(32 - (k & 31));
+}
+__host__ __device__ constexpr double sin32(int k) { return cos32(k - 8); }
+
+// a * (DIR i)
+template <int DIR>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// a * W_R^k with W_R = e^{DIR 2 pi i / R}, R | 32, constant-folded special cases.
+template <int R, int K, int DIR>
+__device__ __forceinline__ float2 twc(float2 a) {
+  constexpr int k = (K * (32 / R)) & 31;  // angle in units of 2 pi / 32
+  if constexpr (k == 0) {
+    return a;
+  } else if constexpr (k == 8) {
+    return rot90<DIR>(a);
+  } else if constexpr (k == 16) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (k == 24) {
+    return rot90<-DIR>(a);
+  } else if constexpr (k == 4 || k == 12 || k == 20 || k == 28) {
+    constexpr float h = 0.70710678118654752440f;
+    constexpr float c = (float)(cos32(k) > 0 ? 1 : -1), s = (float)(sin32(k) > 0 ? 1 : -1) * DIR;
+    // (a.x + i a.y)(c + i s) / sqrt 2
+    return make_float2((c * a.x - s * a.y) * h, (c * a.y + s * a.x) * h);
+  } else {
+    constexpr float c = (float)cos32(k), s = (float)(DIR * sin32(k));
+    return make_float2(c * a.x - s * a.y, c * a.y + s * a.x);
+  }
+}
+
+// In-place radix-R DFT of v[0..R), natural order in and out.
+template <int R, int DIR>
+struct DFT {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      e[k] = v[2 * k];
+      o[k] = v[2 * k + 1];
+    }
+    DFT<R / 2, DIR>::run(e);
+    DFT<R / 2, DIR>::run(o);
+    combine(v, e, o, std::integral_constant<int, 0>());
+  }
+  template <int K>
+  __device__ __forceinline__ static void combine(float2* v, const float2* e, const float2* o,
+                                                 std::integral_constant<int, K>) {
+    if constexpr (K < R / 2) {
+      float2 t = twc<R, K, DIR>(o[K]);
+      v[K] = cadd(e[K], t);
+      v[K + R / 2] = csub(e[K], t);
+      combine(v, e, o, std::integral_constant<int, K + 1>());
+    }
+  }
+};
+template <int DIR>
+struct DFT<1, DIR> {
+  __device__ __forceinline__ static void run(float2*) {}
+};
+template <int DIR>
+struct DFT<2, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  }
+};
+template <int DIR>
+struct DFT<4, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = rot90<DIR>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+template <int DIR>
+struct DFT<3, DIR> {
+  __device__ __forceinline__ static void run(float2* v) {
+    constexpr float h3 = 0.86602540378443864676f;  // sqrt(3) / 2
+    float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+    float2 m = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+    float2 r = cscale(rot90<DIR>(t2), h3);
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+  }
+};
+
+// ------------------------------------------------------------------ sync policies
+struct WarpSync {  // a transform owned by a lane group inside one warp
+  unsigned mask;
+  __device__ __forceinline__ void operator()() const { __syncwarp(mask); }
+};
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// ------------------------------------------------------------------ plans
+// Elements per thread and radices for each supported N.
+template <int N> struct Plan;
+template <> struct Plan<64>   { static constexpr int E = 8,  R0 = 8,  R1 = 8,  R2 = 0; };
+template <> struct Plan<128>  { static constexpr int E = 16, R0 = 8,  R1 = 16, R2 = 0; };
+template <> struct Plan<192>  { static constexpr int E = 24, R0 = 8,  R1 = 8,  R2 = 3; };
+template <> struct Plan<256>  { static constexpr int E = 16, R0 = 16, R1 = 16, R2 = 0; };
+template <> struct Plan<512>  { static constexpr int E = 16, R0 = 8,  R1 = 8,  R2 = 8; };
+template <> struct Plan<1024> { static constexpr int E = 32, R0 = 32, R1 = 32, R2 = 0; };
+
+// shared-memory elements of one transform's padded exchange buffer
+template <int N>
+__host__ __device__ constexpr int pad_elems() {
+  using P = Plan<N>;
+  int a = N + N / P::R0;
+  int b = P::R2 ? N + N / P::R1 : 0;
+  return a > b ? a : b;
+}
+
+// ------------------------------------------------------------------ stage helpers
+// twiddle multiplications of a stage: input r of butterfly u times W_{NS R}^{(j mod NS) r}
+template <int N, int E, int R, int NS, int DIR>
+__device__ __forceinline__ void stage_twiddle(float2 (&b)[E], int t, const float2* __restrict__ tw) {
+  constexpr int T = N / E;
+  constexpr int STEP = N / (NS * R);  // table index of W_{NS R}^{1}
+#pragma unroll
+  for (int u = 0; u < E / R; ++u) {
+    const int j = t + u * T;
+    const int k1 = (j % NS) * STEP;
+    // powers by binary decomposition from table entries W^1, W^2, W^4, ...
+    float2 pw[6];
+    int np = 0;
+#pragma unroll
+    for (int q = 1; q < R; q <<= 1) {
+      float2 w = __ldg(&tw[(k1 * q) % N]);
+      pw[np++] = DIR < 0 ? w : cconj(w);
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w;
+      bool have = false;
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if ((r >> q) & 1) {
+          w = have ? cmul(w, pw[q]) : pw[q];
+          have = true;
+        }
+      b[u * R + r] = cmul(b[u * R + r], w);
+    }
+  }
+}
+
+// radix-3 stages (N = 192 only) use direct table loads
+template <int N, int E, int NS, int DIR>
+__device__ __forceinline__ void stage_twiddle3(float2 (&b)[E], int t, const float2* __restrict__ tw) {
+  constexpr int T = N / E, R = 3, STEP = N / (NS * R);
+#pragma unroll
+  for (int u = 0; u < E / R; ++u) {
+    const int j = t + u * T;
+    const int k1 = (j % NS) * STEP;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = __ldg(&tw[(k1 * r) % N]);
+      b[u * R + r] = cmul(b[u * R + r], DIR < 0 ? w : cconj(w));
+    }
+  }
+}
+
+template <int L, int PADN, bool PAD>
+__device__ __forceinline__ int xlayout(int i) {
+  return PAD ? i + (i / L) * PADN : i;
+}
+
+// write the outputs of a stage (radix R, NS) in the exchange layout
+template <int N, int E, int R, int NS, bool PAD, int STRIDE>
+__device__ __forceinline__ void stage_store(const float2 (&b)[E], float2* sm, int t) {
+  constexpr int T = N / E;
+#pragma unroll
+  for (int u = 0; u < E / R; ++u) {
+    const int j = t + u * T;
+    const int base = PAD ? (j / NS) * (NS * R + NS) + (j % NS) : (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[(base + r * NS) * STRIDE] = b[u * R + r];
+  }
+}
+
+// read the inputs of a stage of radix R from the layout of the previous stage (groups L,
+// padding PADN)
+template <int N, int E, int R, int L, int PADN, bool PAD, int STRIDE>
+__device__ __forceinline__ void stage_load(float2 (&b)[E], const float2* sm, int t) {
+  constexpr int T = N / E;
+#pragma unroll
+  for (int u = 0; u < E / R; ++u) {
+    const int j = t + u * T;
+#pragma unroll
+    for (int r = 0; r < R; ++r) b[u * R + r] = sm[xlayout<L, PADN, PAD>(j + r * (N / R)) * STRIDE];
+  }
+}
+
+template <int N, int E, int R, int DIR>
+__device__ __forceinline__ void stage_dft(float2 (&b)[E]) {
+#pragma unroll
+  for (int u = 0; u < E / R; ++u) DFT<R, DIR>::run(&b[u * R]);
+}
+
+template <int N, int E, int R, int NS, int DIR>
+__device__ __forceinline__ void stage_tw(float2 (&b)[E], int t, const float2* __restrict__ tw) {
+  if constexpr (NS > 1) {
+    if constexpr (R == 3)
+      stage_twiddle3<N, E, NS, DIR>(b, t, tw);
+    else
+      stage_twiddle<N, E, R, NS, DIR>(b, t, tw);
+  }
+}
+
+// ------------------------------------------------------------------ the transform
+// v: E registers of thread t (element t + m T).  sm: this transform's exchange buffer
+// (with STRIDE between consecutive elements).  tw: table of e^{-2 pi i k / N}.
+template <int N, int DIR, bool PAD, int STRIDE, class Sync>
+__device__ __forceinline__ void fft_regs(float2 (&v)[Plan<N>::E], float2* sm, int t,
+                                         const float2* __restrict__ tw, const Sync& sync) {
+  using P = Plan<N>;
+  constexpr int E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2;
+  float2 b[E];
+  // stage 0 (NS = 1): inputs j + r N/R0 are the registers u + r E/R0
+#pragma unroll
+  for (int u = 0; u < E / R0; ++u)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) b[u * R0 + r] = v[u + r * (E / R0)];
+  stage_dft<N, E, R0, DIR>(b);
+  stage_store<N, E, R0, 1, PAD, STRIDE>(b, sm, t);
+  sync();
+  // stage 1 (NS = R0)
+  stage_load<N, E, R1, R0, 1, PAD, STRIDE>(b, sm, t);
+  sync();
+  stage_tw<N, E, R1, R0, DIR>(b, t, tw);
+  stage_dft<N, E, R1, DIR>(b);
+  if constexpr (R2 == 0) {
+#pragma unroll
+    for (int u = 0; u < E / R1; ++u)
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[u + r * (E / R1)] = b[u * R1 + r];
+  } else {
+    stage_store<N, E, R1, R0, PAD, STRIDE>(b, sm, t);
+    sync();
+    stage_load<N, E, R2, R0 * R1, R0, PAD, STRIDE>(b, sm, t);
+    sync();
+    stage_tw<N, E, R2, R0 * R1, DIR>(b, t, tw);
+    stage_dft<N, E, R2, DIR>(b);
+#pragma unroll
+    for (int u = 0; u < E / R2; ++u)
+#pragma unroll
+      for (int r = 0; r < R2; ++r) v[u + r * (E / R2)] = b[u * R2 + r];
+  }
+}
+
+}  // namespace spring

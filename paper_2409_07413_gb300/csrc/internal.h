@@ -1,0 +1,113 @@
+// internal.h -- launchers shared by the translation units of libspring.
+// All pointers are device pointers; every launcher is asynchronous on stream s.
+#pragma once
+
+#include "common.cuh"
+
+namespace spring {
+
+// ---------------------------------------------------------------- k_fft.cu
+// iteration row pass: w (column-pass output) -> P_M x -> update -> x, rowFFT(x) -> w
+spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint8_t* S,
+                              long long batch, float beta, float chi, bool zout, cudaStream_t s);
+// iteration column pass: colFFT, masked modulus projection, colIFFT, in place on w
+spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s);
+// plain row transform (dir -1 forward, +1 inverse), unnormalised times `scale`;
+// Smul (forward only, may be null) multiplies the input by the support first
+spring_status launch_row_fft(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,
+                             long long batch, float scale, cudaStream_t s);
+// plain column transform in place, times `scale`
+spring_status launch_col_fft(int n, int dir, float2* data, int batch, float scale, cudaStream_t s);
+// column forward transform + per-block FP64 partial sums of the Fourier error
+int err_strips(int n);
+spring_status launch_col_err(int n, float2* w, const float* M, int batch, double* partials,
+                             cudaStream_t s);
+spring_status launch_err_finalize(int n, const double* partials, int batch, double* err,
+                                  int* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- composite transforms
+// unitary 2D transform of `batch` images: out = F x (dir -1) or F^-1 x (dir +1); in may
+// equal out.  Smul (forward only): transform S x instead of x.
+spring_status fft2_unitary(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,
+                           int batch, cudaStream_t s);
+
+// ---------------------------------------------------------------- k_sw.cu
+constexpr int SW_MAX_RADIUS = 256;
+spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int batch, float sigma,
+                            unsigned* img_max, cudaStream_t s);
+spring_status launch_threshold(int n, const float* sm, const unsigned* img_max, float tau,
+                               uint8_t* S, int batch, cudaStream_t s);
+spring_status launch_select_area(int n, const float* sm, const int64_t* alpha, int alpha_stride,
+                                 uint8_t* S, int batch, cudaStream_t s);
+
+// ---------------------------------------------------------------- k_ga.cu
+spring_status launch_random_choice(uint64_t seed, int g, int P, int32_t* abc, cudaStream_t s);
+spring_status launch_crossover_map(uint64_t seed, int g, int p, int n, int tmin, int tmax, float cp,
+                                   uint8_t* map, cudaStream_t s);
+// cross-correlation spectra of pairs q = (x index ix[q], ref index ir[q]) from unitary
+// spectra X:  A[q] = Xi conj(X[ix]) X[ir]   and   B[q] = Xi X[ix] X[ir]  (twin)
+spring_status launch_xcorr_spectra(int n, const float2* X, const int32_t* ix, const int32_t* ir,
+                                   int npairs, const float* M, float2* A, float2* B, cudaStream_t s);
+// peak search over the correlation images A[q], B[q] -> info[3q..] = (s_y, s_x, twin),
+// phasor[q] = c(s) / |c(s)|
+size_t peaks_scratch_bytes(int n, int npairs);
+spring_status launch_peaks(int n, const float2* A, const float2* B, int npairs, int32_t* info,
+                           float2* phasor, void* scratch, cudaStream_t s);
+// real-space alignment: out[q] = phasor[q] x[ix[q]](r - s)   (or phasor conj(x(s - r)))
+spring_status launch_apply_shift(int n, const float2* x, const uint8_t* S, const int32_t* ix,
+                                 int npairs, const int32_t* info, const float2* phasor,
+                                 float2* x_out, uint8_t* S_out, cudaStream_t s);
+// crossover mix in Fourier space (parents' alignment applied by the shift theorem)
+spring_status launch_crossover_mix(int n, const float2* Xpop, const int32_t* abc,
+                                   const int32_t* info, const float2* phasor, int P, uint64_t seed,
+                                   int g, float cw, float cp, int tmin, int tmax, float2* Xnew,
+                                   cudaStream_t s);
+spring_status launch_crossover_support(int n, const uint8_t* Spop, const int32_t* abc,
+                                       const int32_t* info, int P, uint8_t* Snew, cudaStream_t s);
+spring_status launch_pairs_crossover(int P, const int32_t* abc, int32_t* ix, int32_t* ir,
+                                     cudaStream_t s);
+spring_status launch_select(int n, float2* pop_x, uint8_t* pop_S, double* pop_err,
+                            const float2* new_x, const uint8_t* new_S, const double* new_err,
+                            int P, uint8_t* replaced, cudaStream_t s);
+// argmin of err (ties: lowest index); err null -> 0
+spring_status launch_argmin(const double* err, int P, int32_t* best, cudaStream_t s);
+spring_status launch_pairs_onto_best(int P, const int32_t* best, int32_t* ix, int32_t* ir,
+                                     cudaStream_t s);
+spring_status launch_average(int n, const float2* x, const uint8_t* S, const int32_t* info,
+                             const float2* phasor, const int32_t* best, int P, float2* avg,
+                             uint8_t* S_avg, cudaStream_t s);
+spring_status launch_area_stats(int n, const uint8_t* S, const int32_t* best, int P, int g, int G,
+                                int64_t* out3, cudaStream_t s);
+size_t init_scratch_bytes(int P, int n_spheres);
+spring_status launch_init_spheres(int n, uint64_t seed, const uint8_t* S0, int P, int n_spheres,
+                                  float gamma, float phi_max, float2* x, void* scratch,
+                                  cudaStream_t s);
+size_t normalise_scratch_bytes(int P);
+spring_status launch_normalise(int n, const float2* X, const float* M, int P, float2* x,
+                               double* partials, cudaStream_t s);
+size_t density_scratch_bytes(int P);
+spring_status launch_density_sums(int n, const float2* x, int P, double* partials, double* out,
+                                  cudaStream_t s);
+spring_status launch_gen_stats(int n, const double* err, const uint8_t* S, const uint8_t* replaced,
+                               const double* dens, int P, double* row, cudaStream_t s);
+spring_status launch_make_modulus(int n, const float* I_centred, const uint8_t* mask_centred,
+                                  float* M, cudaStream_t s);
+spring_status launch_broadcast_support(int n, const uint8_t* S0, int P, uint8_t* S, cudaStream_t s);
+
+// ---------------------------------------------------------------- scratch
+// stream-ordered device scratch (cudaMallocAsync on the current device's pool)
+struct Scratch {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  Scratch() = default;
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  spring_status alloc(size_t bytes, cudaStream_t stream);
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+}  // namespace spring

@@ -1,0 +1,230 @@
+// k_sw.cu -- shrink-wrap support updates (Sec. "The phase problem and conventional
+// approaches", Eq. shrinkwrap; App. "The modified Shrink-wrap").
+//
+//   rho_sigma = G_sigma (*) |x|            separable, periodic, taps d = -r..r, r = ceil(4 sigma)
+//   UpdateSupport:      S = [rho_sigma >= tau max rho_sigma]   (threshold compared in FP64)
+//   UpdateSupportSize:  S = the alpha largest rho_sigma, equal values by lower linear index
+//                       (radix select on the float bit patterns: exact, deterministic)
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace spring {
+
+struct Taps {
+  float w[2 * SW_MAX_RADIUS + 1];
+  int r;
+};
+
+// pass 1: |x| along rows -> tmp
+__global__ void k_smooth_rows(const float2* __restrict__ x, float* __restrict__ tmp, int n,
+                              long long total, const Taps taps) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const long long row0 = (i / n) * n;
+  const int c = (int)(i - row0);
+  float acc = 0.f;
+  for (int d = -taps.r; d <= taps.r; ++d) {
+    int cc = c + d;
+    cc = ((cc % n) + n) % n;
+    const float2 v = __ldg(&x[row0 + cc]);
+    acc = fmaf(taps.w[d + taps.r], sqrtf(v.x * v.x + v.y * v.y), acc);
+  }
+  tmp[i] = acc;
+}
+
+// pass 2: along columns -> out, and the per-image maximum (non-negative floats compare
+// like their bit patterns, so an integer atomicMax is exact and order-independent)
+__global__ void k_smooth_cols(const float* __restrict__ tmp, float* __restrict__ out, int n,
+                              long long total, const Taps taps, unsigned* __restrict__ img_max) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float acc = 0.f;
+  long long img = 0;
+  if (i < total) {
+    const long long nn = (long long)n * n;
+    img = i / nn;
+    const long long off = i - img * nn;
+    const int r = (int)(off / n), c = (int)(off - (long long)r * n);
+    const float* base = tmp + img * nn + c;
+    for (int d = -taps.r; d <= taps.r; ++d) {
+      int rr = r + d;
+      rr = ((rr % n) + n) % n;
+      acc = fmaf(taps.w[d + taps.r], __ldg(&base[(long long)rr * n]), acc);
+    }
+    out[i] = acc;
+  }
+  if (img_max) {
+    // blocks of 256 threads never straddle two images (N^2 is a multiple of 256)
+    unsigned v = (i < total) ? __float_as_uint(fmaxf(acc, 0.f)) : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && i < total) atomicMax(&img_max[img], v);
+  }
+}
+
+__global__ void k_threshold(const float* __restrict__ sm, const unsigned* __restrict__ img_max,
+                            double tau, uint8_t* __restrict__ S, long long nn, long long total) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const double thr = tau * (double)__uint_as_float(img_max[i / nn]);
+  S[i] = ((double)sm[i] >= thr) ? 1 : 0;
+}
+
+static Taps make_taps(float sigma) {
+  Taps t{};
+  if (!(sigma > 0.f)) {
+    t.r = 0;
+    t.w[0] = 1.f;
+    return t;
+  }
+  const double sg = sigma;
+  int r = (int)std::ceil(4.0 * sg);
+  if (r > SW_MAX_RADIUS) r = SW_MAX_RADIUS;
+  std::vector<double> w(2 * r + 1);
+  double s = 0.0;
+  for (int d = -r; d <= r; ++d) s += (w[d + r] = std::exp(-(double)d * d / (2.0 * sg * sg)));
+  for (int d = -r; d <= r; ++d) t.w[d + r] = (float)(w[d + r] / s);
+  t.r = r;
+  return t;
+}
+
+spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int batch, float sigma,
+                            unsigned* img_max, cudaStream_t s) {
+  if (!(sigma >= 0.f) || sigma > 64.f) return invalid("shrink-wrap sigma must be in [0, 64]");
+  const Taps taps = make_taps(sigma);
+  const long long total = (long long)batch * n * n;
+  if (total == 0) return SPRING_OK;
+  if (img_max) SPRING_CUDA(cudaMemsetAsync(img_max, 0, sizeof(unsigned) * batch, s));
+  const int th = 256;
+  launch_begin(SPRING_KC_OTHER, s);
+  k_smooth_rows<<<div_up(total, th), th, 0, s>>>(x, tmp, n, total, taps);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, total * 12.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_smooth_cols<<<div_up(total, th), th, 0, s>>>(tmp, out, n, total, taps, img_max);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, total * 8.0);
+  return SPRING_OK;
+}
+
+spring_status launch_threshold(int n, const float* sm, const unsigned* img_max, float tau,
+                               uint8_t* S, int batch, cudaStream_t s) {
+  const long long nn = (long long)n * n, total = nn * batch;
+  if (total == 0) return SPRING_OK;
+  launch_begin(SPRING_KC_OTHER, s);
+  k_threshold<<<div_up(total, 256), 256, 0, s>>>(sm, img_max, (double)tau, S, nn, total);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, total * 5.0);
+  return SPRING_OK;
+}
+
+// ------------------------------------------------------------------ exact-area select
+// One block per image.  The alpha-th largest bit pattern is found digit by digit
+// (11, 11, 10 bits) from shared-memory histograms; pixels above it are selected, and of
+// the pixels equal to it the first (alpha - #above) in linear order.
+constexpr int SEL_THREADS = 1024;
+
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_tot, unsigned* total) {
+  // exclusive scan over the block in thread order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    unsigned t = lane < nw ? warp_tot[lane] : 0u;
+    unsigned it = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned u = __shfl_up_sync(0xffffffffu, it, o);
+      if (lane >= o) it += u;
+    }
+    if (lane < nw) warp_tot[lane] = it - t;  // exclusive warp offsets
+    if (lane == nw - 1) *total = it;
+  }
+  __syncthreads();
+  const unsigned r = warp_tot[warp] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select_area(const float* __restrict__ sm,
+                                                             const int64_t* __restrict__ alpha,
+                                                             int alpha_stride,
+                                                             uint8_t* __restrict__ S, int n) {
+  __shared__ unsigned hist[2048];
+  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned total;
+  __shared__ unsigned sel_digit, sel_above;
+  const long long nn = (long long)n * n;
+  const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)blockIdx.x * nn;
+  uint8_t* out = S + (long long)blockIdx.x * nn;
+  long long a = alpha[(long long)blockIdx.x * alpha_stride];
+  if (a <= 0 || a >= nn) {
+    const uint8_t fill = a <= 0 ? 0 : 1;
+    for (long long i = threadIdx.x; i < nn; i += blockDim.x) out[i] = fill;
+    return;
+  }
+  unsigned prefix = 0, pmask = 0;
+  unsigned k = (unsigned)a;  // rank still to place within the current prefix
+  const int shifts[3] = {21, 10, 0};
+  const int widths[3] = {11, 11, 10};
+  for (int pass = 0; pass < 3; ++pass) {
+    const int sh = shifts[pass], nb = 1 << widths[pass];
+    for (int b = threadIdx.x; b < 2048; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
+      const unsigned u = v[i];
+      if ((u & pmask) == prefix) atomicAdd(&hist[(u >> sh) & (nb - 1)], 1u);
+    }
+    __syncthreads();
+    // counts above each digit: scan over digits in decreasing order (two per thread)
+    const int d0 = nb - 1 - 2 * threadIdx.x, d1 = d0 - 1;
+    const unsigned c0 = (d0 >= 0) ? hist[d0] : 0u, c1 = (d1 >= 0) ? hist[d1] : 0u;
+    const unsigned above0 = block_excl_scan(c0 + c1, warp_tot, &total);
+    const unsigned above1 = above0 + c0;
+    if (d0 >= 0 && above0 < k && k <= above0 + c0) {
+      sel_digit = (unsigned)d0;
+      sel_above = above0;
+    }
+    if (d1 >= 0 && above1 < k && k <= above1 + c1) {
+      sel_digit = (unsigned)d1;
+      sel_above = above1;
+    }
+    __syncthreads();
+    prefix |= sel_digit << sh;
+    pmask |= (unsigned)(nb - 1) << sh;
+    k -= sel_above;
+    __syncthreads();
+  }
+  // prefix is the alpha-th largest pattern; k pixels equal to it are still to be taken
+  unsigned eq_before = 0;
+  for (long long i0 = 0; i0 < nn; i0 += blockDim.x) {
+    const long long i = i0 + threadIdx.x;
+    const unsigned u = (i < nn) ? v[i] : 0u;
+    const bool eq = (i < nn) && (u == prefix);
+    const int any_eq = __syncthreads_count(eq);
+    unsigned rank = 0;
+    if (any_eq) rank = block_excl_scan(eq ? 1u : 0u, warp_tot, &total);
+    if (i < nn) out[i] = (u > prefix || (eq && eq_before + rank < k)) ? 1 : 0;
+    eq_before += (unsigned)any_eq;
+  }
+}
+
+spring_status launch_select_area(int n, const float* sm, const int64_t* alpha, int alpha_stride,
+                                 uint8_t* S, int batch, cudaStream_t s) {
+  if (batch < 1) return SPRING_OK;
+  launch_begin(SPRING_KC_OTHER, s);
+  k_select_area<<<batch, SEL_THREADS, 0, s>>>(sm, alpha, alpha_stride, S, n);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)batch * n * n * 13.0);
+  return SPRING_OK;
+}
+
+}  // namespace spring

@@ -1,0 +1,866 @@
+// mpr.cu -- the MPR run (Alg. mpr) on one GPU, contexts, problems and serving.
+//
+// A run keeps its whole state resident on the device: two populations of P densities
+// (x), their supports (S), the FFT intermediate (w), the smoothed maps of shrink-wrap and
+// the per-individual errors.  Every decision of the run (best individual, areas, parents,
+// crossover tiles, selection) is taken on the device, so one run is a fixed sequence of
+// kernel launches with no host round trip: it can be enqueued generation by generation
+// (serving) or captured whole in a CUDA graph.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+using namespace spring;
+
+struct spring_problem {
+  spring_ctx* ctx = nullptr;
+  int n = 0;
+  float* M = nullptr;     // device, N x N, DFT order, negative = not measured
+  uint8_t* S0 = nullptr;  // device, N x N, initial support (real space)
+  std::atomic<int> refs{0};
+};
+
+namespace spring {
+
+spring_status prepare_fft_kernels(int n);
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static spring_status validate_params(int n, const spring_params& p) {
+  if (!valid_n(n)) return invalid("unsupported pattern side");
+  if (p.pop < 4) return invalid("pop must be >= 4");
+  if (p.generations < 1) return invalid("generations must be >= 1");
+  if (p.algorithm < 0 || p.algorithm > 2) return invalid("algorithm must be 0, 1 or 2");
+  if (!(p.beta > 0.f && p.beta <= 1.f)) return invalid("beta must be in (0, 1]");
+  if (p.sw_period < 1) return invalid("sw_period must be >= 1");
+  const int R = p.iters_per_gen / p.sw_period;
+  if (R < 2) return invalid("iters_per_gen must be >= 2 * sw_period (R >= 2 repetitions)");
+  const int last = p.iters_per_gen - (R - 1) * p.sw_period;
+  if (p.er_tail < 0 || p.er_tail > last) return invalid("er_tail must be in [0, last block length]");
+  if (!(p.sw_sigma >= 0.f && p.sw_sigma <= 64.f && p.sw_sigma_end >= 0.f && p.sw_sigma_end <= 64.f))
+    return invalid("shrink-wrap sigma must be in [0, 64]");
+  if (!(p.sw_threshold > 0.f && p.sw_threshold <= 1.f && p.sw_threshold_end > 0.f && p.sw_threshold_end <= 1.f))
+    return invalid("shrink-wrap threshold must be in (0, 1]");
+  if (!(p.chi > 0.f)) return invalid("chi must be > 0");
+  if (!(p.cw >= 0.f && p.cw <= 2.f)) return invalid("cw must be in [0, 2]");
+  if (!(p.cp >= 0.f && p.cp <= 1.f)) return invalid("cp must be in [0, 1]");
+  if (p.tile_min < 1) return invalid("tile_min must be >= 1");
+  if (p.init_n_spheres < 1) return invalid("init_n_spheres must be >= 1");
+  if (!(p.init_gamma > 0.f)) return invalid("init_gamma must be > 0");
+  if (p.precision != 0) return invalid("precision 1 (FP16 storage) is not available in this build");
+  return SPRING_OK;
+}
+
+// ------------------------------------------------------------------ device layout of a run
+struct Layout {
+  size_t x, w, S, sm0, sm1, err, abc, ix, ir, info, best, ph, alpha, repl, dens, part_err,
+      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, total;
+};
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static Layout make_layout(int n, const spring_params& p) {
+  const size_t nn = (size_t)n * n, P = p.pop, B = 2 * P, G = p.generations, Q = 3 * P;
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  L.x = take(sizeof(float2) * B * nn);
+  L.w = take(sizeof(float2) * B * nn);
+  L.S = take(B * nn);
+  L.sm0 = take(sizeof(float) * B * nn);
+  L.sm1 = take(sizeof(float) * B * nn);
+  L.err = take(sizeof(double) * B);
+  L.abc = take(sizeof(int32_t) * Q);
+  L.ix = take(sizeof(int32_t) * Q);
+  L.ir = take(sizeof(int32_t) * Q);
+  L.info = take(sizeof(int32_t) * 3 * Q);
+  L.best = take(sizeof(int32_t) * 4);
+  L.ph = take(sizeof(float2) * Q);
+  L.alpha = take(sizeof(int64_t) * 4);
+  L.repl = take(P);
+  L.dens = take(sizeof(double) * 2 * P);
+  L.part_err = take(sizeof(double) * 2 * B * err_strips(n));
+  L.part_norm = take(normalise_scratch_bytes((int)P));
+  L.part_dens = take(density_scratch_bytes((int)P));
+  L.imgmax = take(sizeof(unsigned) * B);
+  L.stats = take(sizeof(double) * 8 * G);
+  L.avg = take(sizeof(float2) * nn);
+  L.Savg = take(nn);
+  L.err_avg = take(sizeof(double) * 2);
+  L.status = take(sizeof(int) * 4);
+  L.peaks = take(peaks_scratch_bytes(n, (int)P));
+  L.init = take(init_scratch_bytes((int)P, p.init_n_spheres) + 128);
+  L.total = o;
+  return L;
+}
+
+class Run {
+ public:
+  int n = 0, P = 0, B = 0, G = 0, R = 0, last = 0;
+  spring_params prm{};
+  const float* M = nullptr;
+  const uint8_t* S0 = nullptr;
+  cudaStream_t s = nullptr;
+  char* mem = nullptr;
+  Layout L{};
+  int next_gen = 1;  // generation to enqueue next (G + 1: finish; G + 2: done)
+
+  float2 *x = nullptr, *w = nullptr, *avg = nullptr;
+  uint8_t *S = nullptr, *repl = nullptr, *Savg = nullptr;
+  float *sm0 = nullptr, *sm1 = nullptr;
+  double *err = nullptr, *dens = nullptr, *part_err = nullptr, *part_norm = nullptr,
+         *part_dens = nullptr, *stats = nullptr, *err_avg = nullptr;
+  int32_t *abc = nullptr, *ix = nullptr, *ir = nullptr, *info = nullptr, *best = nullptr;
+  float2* ph = nullptr;
+  int64_t* alpha = nullptr;
+  unsigned* imgmax = nullptr;
+  int* status = nullptr;
+  void *peaks = nullptr, *init_sc = nullptr;
+  bool z_valid = false;
+
+  ~Run() { release(); }
+
+  void release() {
+    if (mem) {
+      cudaFreeAsync(mem, s);
+      mem = nullptr;
+    }
+  }
+
+  spring_status setup(const spring_problem* prob, const spring_params& p, cudaStream_t stream) {
+    n = prob->n;
+    prm = p;
+    P = p.pop;
+    B = 2 * P;
+    G = p.generations;
+    R = p.iters_per_gen / p.sw_period;
+    last = p.iters_per_gen - (R - 1) * p.sw_period;
+    M = prob->M;
+    S0 = prob->S0;
+    s = stream;
+    L = make_layout(n, p);
+    SPRING_TRY(prepare_fft_kernels(n));
+    DeviceTables tb;
+    SPRING_TRY(device_tables(&tb));
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), L.total, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      mem = nullptr;
+      set_error(std::string("run allocation of ") + std::to_string(L.total) + " bytes failed");
+      return SPRING_E_NOMEM;
+    }
+    x = reinterpret_cast<float2*>(mem + L.x);
+    w = reinterpret_cast<float2*>(mem + L.w);
+    S = reinterpret_cast<uint8_t*>(mem + L.S);
+    sm0 = reinterpret_cast<float*>(mem + L.sm0);
+    sm1 = reinterpret_cast<float*>(mem + L.sm1);
+    err = reinterpret_cast<double*>(mem + L.err);
+    abc = reinterpret_cast<int32_t*>(mem + L.abc);
+    ix = reinterpret_cast<int32_t*>(mem + L.ix);
+    ir = reinterpret_cast<int32_t*>(mem + L.ir);
+    info = reinterpret_cast<int32_t*>(mem + L.info);
+    best = reinterpret_cast<int32_t*>(mem + L.best);
+    ph = reinterpret_cast<float2*>(mem + L.ph);
+    alpha = reinterpret_cast<int64_t*>(mem + L.alpha);
+    repl = reinterpret_cast<uint8_t*>(mem + L.repl);
+    dens = reinterpret_cast<double*>(mem + L.dens);
+    part_err = reinterpret_cast<double*>(mem + L.part_err);
+    part_norm = reinterpret_cast<double*>(mem + L.part_norm);
+    part_dens = reinterpret_cast<double*>(mem + L.part_dens);
+    imgmax = reinterpret_cast<unsigned*>(mem + L.imgmax);
+    stats = reinterpret_cast<double*>(mem + L.stats);
+    avg = reinterpret_cast<float2*>(mem + L.avg);
+    Savg = reinterpret_cast<uint8_t*>(mem + L.Savg);
+    err_avg = reinterpret_cast<double*>(mem + L.err_avg);
+    status = reinterpret_cast<int*>(mem + L.status);
+    peaks = mem + L.peaks;
+    init_sc = mem + L.init;
+    return SPRING_OK;
+  }
+
+  size_t nn() const { return (size_t)n * n; }
+  float2* x_pop() { return x; }
+  float2* x_new() { return x + P * nn(); }
+  float2* w_pop() { return w; }
+  float2* w_new() { return w + P * nn(); }
+  uint8_t* S_pop() { return S; }
+  uint8_t* S_new() { return S + P * nn(); }
+  double* err_pop() { return err; }
+  double* err_new() { return err + P; }
+
+  // Initialize (App. "Initialization of the starting densities")
+  spring_status enqueue_init() {
+    SPRING_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * 4, s));
+    SPRING_TRY(launch_init_spheres(n, prm.seed, S0, P, prm.init_n_spheres, prm.init_gamma,
+                                   prm.init_phi_max, x_pop(), init_sc, s));
+    SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
+    SPRING_TRY(launch_normalise(n, w_pop(), M, P, x_pop(), part_norm, s));
+    SPRING_TRY(launch_broadcast_support(n, S0, P, S_pop(), s));
+    z_valid = false;
+    return SPRING_OK;
+  }
+
+  // alignment of P pairs (ix, ir) given population spectra in w_pop; correlations go to
+  // the free new-population halves of x and w
+  spring_status align(const int32_t* pix, const int32_t* pir, int32_t* pinfo, float2* pph) {
+    SPRING_TRY(launch_xcorr_spectra(n, w_pop(), pix, pir, P, M, x_new(), w_new(), s));
+    SPRING_TRY(fft2_unitary(n, +1, x_new(), x_new(), nullptr, P, s));
+    SPRING_TRY(fft2_unitary(n, +1, w_new(), w_new(), nullptr, P, s));
+    return launch_peaks(n, x_new(), w_new(), P, pinfo, pph, peaks, s);
+  }
+
+  // Crossover (Alg. crossover)
+  spring_status crossover(int g) {
+    SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
+    SPRING_TRY(launch_random_choice(prm.seed, g, P, abc, s));
+    SPRING_TRY(launch_pairs_crossover(P, abc, ix, ir, s));
+    for (int c = 0; c < 3; ++c) SPRING_TRY(align(ix + c * P, ir + c * P, info + 3 * c * P, ph + c * P));
+    SPRING_TRY(launch_crossover_mix(n, w_pop(), abc, info, ph, P, prm.seed, g, prm.cw, prm.cp,
+                                    prm.tile_min, prm.tile_max, x_new(), s));
+    SPRING_TRY(fft2_unitary(n, +1, x_new(), x_new(), nullptr, P, s));
+    SPRING_TRY(launch_crossover_support(n, S_pop(), abc, info, P, S_new(), s));
+    z_valid = false;
+    return SPRING_OK;
+  }
+
+  spring_status iterations(int alg, int k) {
+    if (k <= 0) return SPRING_OK;
+    if (!z_valid) {
+      SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, B, 1.0f, s));
+      z_valid = true;
+    }
+    for (int it = 0; it < k; ++it) {
+      SPRING_TRY(launch_col_pm(n, w, M, B, s));
+      SPRING_TRY(launch_row_iter(n, alg, w, x, S, B, prm.beta, prm.chi, true, s));
+    }
+    return SPRING_OK;
+  }
+
+  spring_status shrinkwrap(float sigma, float tau) {
+    SPRING_TRY(launch_smooth(n, x, sm0, sm1, B, sigma, imgmax, s));
+    return launch_threshold(n, sm1, imgmax, tau, S, B, s);
+  }
+
+  spring_status shrinkwrap_area(float sigma, const int64_t* a) {
+    SPRING_TRY(launch_smooth(n, x, sm0, sm1, B, sigma, nullptr, s));
+    return launch_select_area(n, sm1, a, 0, S, B, s);
+  }
+
+  spring_status errors() {
+    SPRING_TRY(launch_row_fft(n, -1, x, w, S, B, 1.0f, s));
+    SPRING_TRY(launch_col_err(n, w, M, B, part_err, s));
+    SPRING_TRY(launch_err_finalize(n, part_err, B, err, status, s));
+    z_valid = false;
+    return SPRING_OK;
+  }
+
+  // Improve (Alg. improve) of both populations at once
+  spring_status improve(float sigma, float tau) {
+    const int K = prm.sw_period, alg = prm.algorithm;
+    for (int blk = 1; blk <= R; ++blk) {
+      if (blk < R) SPRING_TRY(iterations(alg, K));
+      if (blk <= R - 2) {
+        SPRING_TRY(shrinkwrap(sigma, tau));
+      } else if (blk == R - 1) {
+        SPRING_TRY(shrinkwrap_area(sigma, alpha + 0));  // UpdateSupportSize(alpha_best)
+      } else {
+        SPRING_TRY(iterations(alg, last - prm.er_tail));
+        SPRING_TRY(shrinkwrap_area(sigma, alpha + 2));  // UpdateSupportSize(alpha_eval)
+        SPRING_TRY(iterations(0, prm.er_tail));         // EvalSequence: ER
+        SPRING_TRY(errors());                           // GetError
+        SPRING_TRY(shrinkwrap(sigma, tau));
+      }
+    }
+    return SPRING_OK;
+  }
+
+  spring_status generation(int g) {
+    const double t = G > 1 ? (double)(g - 1) / (double)(G - 1) : 0.0;
+    const float sigma = (float)(prm.sw_sigma + (prm.sw_sigma_end - prm.sw_sigma) * t);
+    const float tau = (float)(prm.sw_threshold + (prm.sw_threshold_end - prm.sw_threshold) * t);
+    SPRING_TRY(crossover(g));
+    SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, best, s));
+    SPRING_TRY(launch_area_stats(n, S_pop(), best, P, g, G, alpha, s));
+    SPRING_TRY(improve(sigma, tau));
+    SPRING_TRY(launch_select(n, x_pop(), S_pop(), err_pop(), x_new(), S_new(), err_new(), P, repl, s));
+    SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
+    SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s));
+    return SPRING_OK;
+  }
+
+  // Average (Eq. avgrec) of the final population and its error
+  spring_status finish() {
+    SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
+    SPRING_TRY(launch_argmin(err_pop(), P, best, s));
+    SPRING_TRY(launch_pairs_onto_best(P, best, ix, ir, s));
+    SPRING_TRY(align(ix, ir, info, ph));
+    SPRING_TRY(launch_average(n, x_pop(), S_pop(), info, ph, best, P, avg, Savg, s));
+    SPRING_TRY(launch_row_fft(n, -1, avg, w_new(), Savg, 1, 1.0f, s));
+    SPRING_TRY(launch_col_err(n, w_new(), M, 1, part_err, s));
+    SPRING_TRY(launch_err_finalize(n, part_err, 1, err_avg, status, s));
+    return SPRING_OK;
+  }
+
+  // enqueue the next chunk of work: init with generation 1, then one generation per call,
+  // then the average; returns true when nothing is left
+  spring_status step(bool* done) {
+    *done = false;
+    if (next_gen == 1) SPRING_TRY(enqueue_init());
+    if (next_gen <= G) {
+      SPRING_TRY(generation(next_gen));
+      ++next_gen;
+      if (next_gen <= G) return SPRING_OK;
+    }
+    if (next_gen == G + 1) {
+      SPRING_TRY(finish());
+      ++next_gen;
+      return SPRING_OK;
+    }
+    *done = true;
+    return SPRING_OK;
+  }
+
+  spring_status enqueue_all() {
+    bool done = false;
+    while (!done) SPRING_TRY(step(&done));
+    return SPRING_OK;
+  }
+
+  // after the stream has completed: copy results to host buffers
+  spring_status collect(spring_result* out) {
+    int st[4] = {0, 0, 0, 0};
+    int32_t b = 0;
+    double ea = 0.0;
+    SPRING_CUDA(cudaMemcpy(st, status, sizeof(st), cudaMemcpyDeviceToHost));
+    SPRING_CUDA(cudaMemcpy(&b, best, sizeof(b), cudaMemcpyDeviceToHost));
+    SPRING_CUDA(cudaMemcpy(&ea, err_avg, sizeof(ea), cudaMemcpyDeviceToHost));
+    double eb = 0.0;
+    SPRING_CUDA(cudaMemcpy(&eb, err_pop() + b, sizeof(eb), cudaMemcpyDeviceToHost));
+    out->final_error_avg = ea;
+    out->final_error_best = eb;
+    if (out->rho_avg) SPRING_CUDA(cudaMemcpy(out->rho_avg, avg, sizeof(float2) * nn(), cudaMemcpyDeviceToHost));
+    if (out->rho_best)
+      SPRING_CUDA(cudaMemcpy(out->rho_best, x_pop() + (size_t)b * nn(), sizeof(float2) * nn(), cudaMemcpyDeviceToHost));
+    if (out->support_avg) SPRING_CUDA(cudaMemcpy(out->support_avg, Savg, nn(), cudaMemcpyDeviceToHost));
+    if (out->gen_stats) {
+      SPRING_CUDA(cudaMemcpy(out->gen_stats, stats, sizeof(double) * 8 * G, cudaMemcpyDeviceToHost));
+      out->gen_stats[8 * (G - 1) + 3] = ea;
+    }
+    if (st[0]) {
+      set_error("non-finite Fourier error in the run");
+      return SPRING_E_NUMERIC;
+    }
+    return SPRING_OK;
+  }
+};
+
+}  // namespace spring
+
+// ------------------------------------------------------------------ context and serving
+namespace {
+
+enum TState { T_QUEUED = 0, T_RUNNING = 1, T_DONE = 2, T_FAILED = 3, T_CANCELLED = 4 };
+
+struct Ticket {
+  uint64_t id = 0;
+  spring_problem* prob = nullptr;
+  spring_params prm{};
+  TState state = T_QUEUED;
+  bool cancel = false;
+  size_t footprint = 0;
+  std::unique_ptr<Run> run;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool ev_pending = false;
+  spring_status status = SPRING_OK;
+  std::string message;
+  // host staging of the results
+  std::vector<float> rho_avg, rho_best;
+  std::vector<uint8_t> support_avg;
+  std::vector<double> gen_stats;
+  double e_avg = 0.0, e_best = 0.0;
+  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+};
+
+}  // namespace
+
+struct spring_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t used = 0;
+  std::mutex mu;
+  std::condition_variable cv;       // scheduler wake-ups
+  std::condition_variable done_cv;  // ticket completions
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
+  uint64_t next_id = 1;
+  bool stop = false;
+  std::thread worker;
+};
+
+namespace spring {
+
+static bool reserve(spring_ctx* c, size_t bytes) {
+  if (c->used + bytes > c->budget) return false;
+  c->used += bytes;
+  return true;
+}
+
+static void finish_ticket(spring_ctx* c, Ticket* t, TState st) {
+  t->state = st;
+  t->t_done = now_s();
+  if (t->run) {
+    t->run->release();
+    t->run.reset();
+  }
+  if (t->stream) {
+    cudaStreamSynchronize(t->stream);
+    cudaStreamDestroy(t->stream);
+    t->stream = nullptr;
+  }
+  if (t->ev) {
+    cudaEventDestroy(t->ev);
+    t->ev = nullptr;
+  }
+  c->used -= t->footprint;
+  t->footprint = 0;
+  t->prob->refs.fetch_sub(1);
+}
+
+// scheduler: admit queued tickets while their footprint fits, then keep every running
+// ticket's stream fed with one generation at a time (continuous batching: requests
+// arriving while others run are admitted as memory frees up, and their kernels overlap
+// on the device through separate streams)
+static void scheduler(spring_ctx* c) {
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(c->mu);
+  while (!c->stop) {
+    bool progress = false;
+    // admission in arrival order
+    while (!c->queue.empty()) {
+      Ticket* t = c->tickets[c->queue.front()].get();
+      if (t->cancel) {
+        c->queue.pop_front();
+        t->state = T_CANCELLED;
+        t->t_done = now_s();
+        t->prob->refs.fetch_sub(1);
+        progress = true;
+        c->done_cv.notify_all();
+        continue;
+      }
+      if (!reserve(c, t->footprint)) break;
+      c->queue.pop_front();
+      t->t_admit = now_s();
+      t->state = T_RUNNING;
+      cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking);
+      cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming);
+      t->run.reset(new Run());
+      spring_status st = t->run->setup(t->prob, t->prm, t->stream);
+      if (st != SPRING_OK) {
+        t->status = st;
+        t->message = spring_last_error();
+        finish_ticket(c, t, T_FAILED);
+        c->done_cv.notify_all();
+      }
+      progress = true;
+    }
+    // feed running tickets
+    for (auto& kv : c->tickets) {
+      Ticket* t = kv.second.get();
+      if (t->state != T_RUNNING) continue;
+      if (t->ev_pending) {
+        cudaError_t q = cudaEventQuery(t->ev);
+        if (q == cudaErrorNotReady) continue;
+        t->ev_pending = false;
+        if (q != cudaSuccess) {
+          t->status = SPRING_E_CUDA;
+          t->message = cudaGetErrorString(q);
+          finish_ticket(c, t, T_FAILED);
+          c->done_cv.notify_all();
+          progress = true;
+          continue;
+        }
+      }
+      if (t->cancel) {
+        finish_ticket(c, t, T_CANCELLED);
+        c->done_cv.notify_all();
+        progress = true;
+        continue;
+      }
+      bool done = false;
+      spring_status st = t->run->step(&done);
+      if (st != SPRING_OK) {
+        t->status = st;
+        t->message = spring_last_error();
+        finish_ticket(c, t, T_FAILED);
+        c->done_cv.notify_all();
+        progress = true;
+        continue;
+      }
+      if (done) {
+        const int n = t->run->n, G = t->run->G;
+        const size_t nn = (size_t)n * n;
+        t->rho_avg.resize(2 * nn);
+        t->rho_best.resize(2 * nn);
+        t->support_avg.resize(nn);
+        t->gen_stats.resize(8 * (size_t)G);
+        spring_result r{};
+        r.rho_avg = t->rho_avg.data();
+        r.rho_best = t->rho_best.data();
+        r.support_avg = t->support_avg.data();
+        r.gen_stats = t->gen_stats.data();
+        st = t->run->collect(&r);
+        t->e_avg = r.final_error_avg;
+        t->e_best = r.final_error_best;
+        if (st != SPRING_OK) {
+          t->status = st;
+          t->message = spring_last_error();
+        }
+        finish_ticket(c, t, st == SPRING_OK ? T_DONE : T_FAILED);
+        c->done_cv.notify_all();
+      } else {
+        cudaEventRecord(t->ev, t->stream);
+        t->ev_pending = true;
+      }
+      progress = true;
+    }
+    if (!progress) c->cv.wait_for(lk, std::chrono::microseconds(200));
+  }
+}
+
+}  // namespace spring
+
+extern "C" {
+
+void spring_params_default(spring_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->pop = 8;
+  p->iters_per_gen = 100;
+  p->generations = 5;
+  p->algorithm = 2;
+  p->beta = 0.9f;
+  p->sw_sigma = 1.5f;
+  p->sw_threshold = 0.2f;
+  p->sw_sigma_end = 1.5f;
+  p->sw_threshold_end = 0.2f;
+  p->sw_period = 20;
+  p->er_tail = 10;
+  p->chi = 0.5f;
+  p->cw = 0.4f;
+  p->cp = 0.6f;
+  p->tile_min = 4;
+  p->tile_max = 0;
+  p->init_n_spheres = 5;
+  p->init_gamma = 1.0f;
+  p->init_phi_max = 0.0f;
+  p->precision = 0;
+  p->use_graph = 0;
+  p->seed = 0;
+}
+
+size_t spring_footprint_bytes(int n, const spring_params* p) {
+  if (!p || !valid_n(n) || p->pop < 1 || p->generations < 1) return 0;
+  return make_layout(n, *p).total;
+}
+
+spring_status spring_init(int device, size_t hbm_budget_bytes, spring_ctx** out) {
+  if (!out) return invalid("null output handle");
+  int count = 0;
+  SPRING_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return invalid("no such CUDA device");
+  SPRING_CUDA(cudaSetDevice(device));
+  size_t fr = 0, tot = 0;
+  SPRING_CUDA(cudaMemGetInfo(&fr, &tot));
+  // keep freed run memory in the device pool for reuse by the next run
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  spring_ctx* c = new spring_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+  c->worker = std::thread(scheduler, c);
+  *out = c;
+  return SPRING_OK;
+}
+
+spring_status spring_shutdown(spring_ctx* c) {
+  if (!c) return invalid("null context");
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto& kv : c->tickets)
+      if (kv.second->state == T_QUEUED || kv.second->state == T_RUNNING) {
+        set_error("context has queued or running tickets");
+        return SPRING_E_BUSY;
+      }
+    c->stop = true;
+  }
+  c->cv.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  delete c;
+  return SPRING_OK;
+}
+
+static spring_status problem_alloc(spring_ctx* ctx, int n, spring_problem** out, spring_problem** p) {
+  if (!ctx || !out) return invalid("null context or output handle");
+  if (!valid_n(n)) return invalid("unsupported pattern side " + std::to_string(n));
+  SPRING_CUDA(cudaSetDevice(ctx->device));
+  std::unique_ptr<spring_problem> pr(new spring_problem());
+  pr->ctx = ctx;
+  pr->n = n;
+  const size_t nn = (size_t)n * n;
+  SPRING_CUDA(cudaMalloc(&pr->M, sizeof(float) * nn));
+  cudaError_t e = cudaMalloc(&pr->S0, nn);
+  if (e != cudaSuccess) {
+    cudaFree(pr->M);
+    return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+  }
+  *p = pr.release();
+  return SPRING_OK;
+}
+
+static spring_status problem_fill(spring_problem* pr, const float* d_I, const uint8_t* d_mask,
+                                  const uint8_t* d_S0, cudaStream_t s) {
+  const int n = pr->n;
+  SPRING_TRY(launch_make_modulus(n, d_I, d_mask, pr->M, s));
+  SPRING_CUDA(cudaMemcpyAsync(pr->S0, d_S0, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+  return SPRING_OK;
+}
+
+spring_status spring_problem_create(spring_ctx* ctx, int ny, int nx, const float* I, const uint8_t* mask,
+                                    const uint8_t* S0, spring_problem** out) {
+  if (ny != nx) return invalid("patterns must be square");
+  if (!I || !mask || !S0) return invalid("null input array");
+  spring_problem* pr = nullptr;
+  SPRING_TRY(problem_alloc(ctx, nx, out, &pr));
+  const size_t nn = (size_t)nx * nx;
+  char* tmp = nullptr;
+  spring_status st = SPRING_OK;
+  cudaError_t e = cudaMalloc(&tmp, nn * (sizeof(float) + 2));
+  if (e == cudaSuccess) e = cudaMemcpy(tmp, I, sizeof(float) * nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(tmp + sizeof(float) * nn, mask, nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(tmp + (sizeof(float) + 1) * nn, S0, nn, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    st = cuda_fail(e, "problem upload", __FILE__, __LINE__);
+  } else {
+    st = problem_fill(pr, reinterpret_cast<float*>(tmp), reinterpret_cast<uint8_t*>(tmp + sizeof(float) * nn),
+                      reinterpret_cast<uint8_t*>(tmp + (sizeof(float) + 1) * nn), nullptr);
+    if (st == SPRING_OK) {
+      e = cudaStreamSynchronize(nullptr);
+      if (e != cudaSuccess) st = cuda_fail(e, "problem set-up", __FILE__, __LINE__);
+    }
+  }
+  if (tmp) cudaFree(tmp);
+  if (st != SPRING_OK) {
+    cudaFree(pr->M);
+    cudaFree(pr->S0);
+    delete pr;
+    return st;
+  }
+  *out = pr;
+  return SPRING_OK;
+}
+
+spring_status spring_problem_create_device(spring_ctx* ctx, int ny, int nx, const float* d_I,
+                                           const uint8_t* d_mask, const uint8_t* d_S0, void* stream,
+                                           spring_problem** out) {
+  if (ny != nx) return invalid("patterns must be square");
+  if (!d_I || !d_mask || !d_S0) return invalid("null input array");
+  spring_problem* pr = nullptr;
+  SPRING_TRY(problem_alloc(ctx, nx, out, &pr));
+  spring_status st = problem_fill(pr, d_I, d_mask, d_S0, reinterpret_cast<cudaStream_t>(stream));
+  if (st != SPRING_OK) {
+    cudaFree(pr->M);
+    cudaFree(pr->S0);
+    delete pr;
+    return st;
+  }
+  *out = pr;
+  return SPRING_OK;
+}
+
+spring_status spring_problem_destroy(spring_problem* pr) {
+  if (!pr) return invalid("null problem");
+  if (pr->refs.load() > 0) {
+    set_error("problem is referenced by an unfinished ticket");
+    return SPRING_E_BUSY;
+  }
+  cudaSetDevice(pr->ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(pr->M);
+  cudaFree(pr->S0);
+  delete pr;
+  return SPRING_OK;
+}
+
+spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_result* out) {
+  if (!pr || !p || !out) return invalid("null argument");
+  SPRING_TRY(validate_params(pr->n, *p));
+  spring_ctx* c = pr->ctx;
+  SPRING_CUDA(cudaSetDevice(c->device));
+  const size_t fp = make_layout(pr->n, *p).total;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!reserve(c, fp)) {
+      set_error("run footprint " + std::to_string(fp) + " B exceeds the context's HBM budget");
+      return SPRING_E_NOMEM;
+    }
+  }
+  cudaStream_t s = nullptr;
+  spring_status st = SPRING_OK;
+  {
+    Run run;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__);
+    if (st == SPRING_OK) st = run.setup(pr, *p, s);
+    if (st == SPRING_OK) {
+      if (p->use_graph) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+        if (st == SPRING_OK) {
+          st = run.enqueue_all();
+          e = cudaStreamEndCapture(s, &graph);
+          if (st == SPRING_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        }
+        if (st == SPRING_OK) {
+          e = cudaGraphInstantiate(&exec, graph, 0);
+          if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        }
+        if (st == SPRING_OK) {
+          e = cudaGraphLaunch(exec, s);
+          if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
+        }
+        if (st == SPRING_OK) {
+          e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) st = cuda_fail(e, "graph execution", __FILE__, __LINE__);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+      } else {
+        st = run.enqueue_all();
+        if (st == SPRING_OK) {
+          e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) st = cuda_fail(e, "run execution", __FILE__, __LINE__);
+        }
+      }
+    }
+    if (st == SPRING_OK) {
+      out->t_submit_s = out->t_admit_s = now_s();
+      st = run.collect(out);
+      out->t_done_s = now_s();
+    }
+    run.release();
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->used -= fp;
+  return st;
+}
+
+spring_status spring_submit(spring_ctx* c, spring_problem* pr, const spring_params* p, uint64_t* ticket) {
+  if (!c || !pr || !p || !ticket) return invalid("null argument");
+  if (pr->ctx != c) return invalid("problem belongs to another context");
+  SPRING_TRY(validate_params(pr->n, *p));
+  std::unique_ptr<Ticket> t(new Ticket());
+  t->prob = pr;
+  t->prm = *p;
+  t->footprint = make_layout(pr->n, *p).total;
+  t->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (t->footprint > c->budget) {
+      set_error("request footprint exceeds the context's HBM budget");
+      return SPRING_E_NOMEM;
+    }
+    t->id = c->next_id++;
+    *ticket = t->id;
+    pr->refs.fetch_add(1);
+    c->queue.push_back(t->id);
+    c->tickets[t->id] = std::move(t);
+  }
+  c->cv.notify_all();
+  return SPRING_OK;
+}
+
+spring_status spring_poll(spring_ctx* c, uint64_t ticket, int timeout_us, spring_result* out) {
+  if (!c) return invalid("null context");
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto it = c->tickets.find(ticket);
+  if (it == c->tickets.end()) {
+    set_error("unknown ticket");
+    return SPRING_E_NOT_FOUND;
+  }
+  Ticket* t = it->second.get();
+  auto finished = [&]() { return t->state >= T_DONE; };
+  if (!finished()) {
+    if (timeout_us < 0)
+      c->done_cv.wait(lk, finished);
+    else if (timeout_us > 0)
+      c->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), finished);
+  }
+  if (!finished()) return SPRING_E_BUSY;
+  spring_status st = SPRING_OK;
+  if (t->state == T_CANCELLED) {
+    st = SPRING_E_CANCELLED;
+    set_error("ticket was cancelled");
+  } else if (t->state == T_FAILED) {
+    st = t->status;
+    set_error(t->message);
+  } else if (out) {
+    const size_t nn = t->support_avg.size();
+    if (out->rho_avg) std::memcpy(out->rho_avg, t->rho_avg.data(), sizeof(float) * 2 * nn);
+    if (out->rho_best) std::memcpy(out->rho_best, t->rho_best.data(), sizeof(float) * 2 * nn);
+    if (out->support_avg) std::memcpy(out->support_avg, t->support_avg.data(), nn);
+    if (out->gen_stats) std::memcpy(out->gen_stats, t->gen_stats.data(), sizeof(double) * t->gen_stats.size());
+    out->final_error_avg = t->e_avg;
+    out->final_error_best = t->e_best;
+    out->t_submit_s = t->t_submit;
+    out->t_admit_s = t->t_admit;
+    out->t_done_s = t->t_done;
+  }
+  c->tickets.erase(it);
+  return st;
+}
+
+spring_status spring_cancel(spring_ctx* c, uint64_t ticket) {
+  if (!c) return invalid("null context");
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->tickets.find(ticket);
+    if (it == c->tickets.end()) {
+      set_error("unknown ticket");
+      return SPRING_E_NOT_FOUND;
+    }
+    it->second->cancel = true;
+  }
+  c->cv.notify_all();
+  return SPRING_OK;
+}
+
+}  // extern "C"
