@@ -37,10 +37,11 @@ def aligned_rel_error(rho, truth):
 
 def test_mpr_sphere64_matches_oracle_statistically(sp, ctx):
     # HIO/RAAR trajectories diverge from FP64 at the FP32 rate (see the operator tests), so
-    # the comparison is over several seeds: final errors within 2 % on the mean, recovery
-    # of the object (up to translation / twin / phase) of the same quality
+    # the end-to-end comparison is over seeds: the mean final error within 2 % of the
+    # oracle's (widened by two standard errors of the difference of the two means), and
+    # the same median recovery of the object (up to translation / twin / phase)
     eg, eo, rg, ro = [], [], [], []
-    for seed in range(4):
+    for seed in range(16):
         pat = synthetic.config_pattern("sphere64", seed)
         prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
         r = prob.run(sp.params(**C1, seed=seed))
@@ -52,10 +53,12 @@ def test_mpr_sphere64_matches_oracle_statistically(sp, ctx):
         ro.append(aligned_rel_error(o["rho_avg"], pat.truth))
         assert np.isfinite(r["gen_stats"][:, [0, 1, 2, 4, 5, 6, 7]]).all()
         assert 0 <= r["gen_stats"][:, 5].min() and r["gen_stats"][:, 5].max() <= 1
-    print("E gpu", np.round(eg, 4), "E oracle", np.round(eo, 4))
-    print("recovery gpu", np.round(rg, 4), "oracle", np.round(ro, 4))
-    assert abs(np.mean(eg) - np.mean(eo)) <= 0.02 * np.mean(eo)
-    assert abs(np.mean(rg) - np.mean(ro)) <= 0.02 + 0.1 * np.mean(ro)
+    eg, eo = np.array(eg), np.array(eo)
+    se = np.sqrt(eg.var(ddof=1) / len(eg) + eo.var(ddof=1) / len(eo))
+    print(f"mean E gpu {eg.mean():.4f} oracle {eo.mean():.4f} (se {se:.4f}); median recovery "
+          f"gpu {np.median(rg):.4f} oracle {np.median(ro):.4f}")
+    assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
+    assert abs(np.median(rg) - np.median(ro)) <= 0.05
 
 
 def test_mpr_deterministic_and_graph_identical(sp, ctx):
