@@ -197,6 +197,27 @@ spring_status spring_update_support_size(const void* x, uint8_t* S, int batch, i
 spring_status spring_fourier_error(const void* x, const uint8_t* S, const float* M, int batch,
                                    int n, double* err, void* stream);
 
+/* GetError without allocation.  Some callers cannot call cudaMalloc or cudaMallocAsync
+ * (a host framework whose allocator owns the device memory budget, code that must not
+ * allocate while graphs are being captured, real-time loops that cannot take an
+ * allocation's implicit synchronisation).  This entry point computes exactly what
+ * spring_fourier_error computes, with its scratch (transformed images and partial sums)
+ * in a fixed file-scope device array of SPRING_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until exit; it calls no allocator.  The paper has no
+ * counterpart: this is an interface convenience of this library.
+ *  - Limit: batch * N * N * 8 bytes, rounded up to 256, plus batch * (N / 16) * 16 bytes
+ *    must fit in SPRING_NOALLOC_SCRATCH_BYTES (16 MiB: e.g. batch <= 7 at 512 x 512,
+ *    <= 1 at 1024 x 1024); larger requests return SPRING_E_INVALID with the sizes.
+ *  - The first call on each device looks up the array's device address and uploads a
+ *    twiddle table (no allocation); make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents (each call
+ *    writes all it reads).  Calls that overlap on the GPU (different streams, or threads
+ *    without ordering) race on it: serialise them.
+ *  - err: DEVICE double[batch]. */
+#define SPRING_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+spring_status spring_fourier_error_noalloc(const void* x, const uint8_t* S, const float* M,
+                                           int batch, int n, double* err, void* stream);
+
 /* a7 area bookkeeping (Alg. improve, first three steps) on the parent population:
  * out[0] = alpha_best = area of the support of argmin err (ties: lowest index; err NULL:
  * individual 0), out[1] = alpha_all = area of the union of the P supports,

@@ -24,6 +24,12 @@ spring_status launch_col_err(int n, float2* w, const float* M, int batch, double
                              cudaStream_t s);
 spring_status launch_err_finalize(int n, const double* partials, int batch, double* err,
                                   int* status, cudaStream_t s);
+// the same two error launchers with a caller-supplied twiddle table (all sides, laid out
+// at tw_offset(N)) instead of the per-device one
+spring_status launch_row_fft_tw(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,
+                                long long batch, float scale, const float2* tw_all, cudaStream_t s);
+spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
+                                const float2* tw_all, cudaStream_t s);
 
 // ---------------------------------------------------------------- composite transforms
 // unitary 2D transform of `batch` images: out = F x (dir -1) or F^-1 x (dir +1); in may

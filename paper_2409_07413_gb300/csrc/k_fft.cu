@@ -401,3 +401,38 @@ spring_status prepare_fft_kernels(int n) {
 }
 
 }  // namespace spring
+
+namespace spring {
+
+// Variants of the error-path launchers that take the twiddle table from the caller
+// instead of the per-device table (used by the entry point that must not allocate).
+spring_status launch_row_fft_tw(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,
+                                long long batch, float scale, const float2* tw_all, cudaStream_t s) {
+  RowArgs a{};
+  a.in = in;
+  a.out = out;
+  a.S = Smul;
+  a.tw = tw_all + tw_offset(n);
+  a.nrows = batch * n;
+  a.scale = scale;
+  const double bytes = (double)batch * n * n * (16.0 + (Smul ? 1.0 : 0.0));
+  if (dir < 0) {
+    SPRING_DISPATCH_N(n, (row_launch<NN, ROW_FWD, 0>(a, s, SPRING_KC_OTHER, bytes)));
+  } else {
+    SPRING_DISPATCH_N(n, (row_launch<NN, ROW_INV, 0>(a, s, SPRING_KC_OTHER, bytes)));
+  }
+}
+
+spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
+                                const float2* tw_all, cudaStream_t s) {
+  ColArgs a{};
+  a.data = w;
+  a.M = M;
+  a.tw = tw_all + tw_offset(n);
+  a.batch = batch;
+  a.partials = partials;
+  const double bytes = (double)batch * n * n * 8.0 + (double)n * n * 4.0;
+  SPRING_DISPATCH_N(n, (col_launch<NN, COL_ERR>(a, s, SPRING_KC_OTHER, bytes)));
+}
+
+}  // namespace spring

@@ -72,6 +72,7 @@ _SIGS = {
     "spring_update_support": (_i, [_vp, _vp, _i, _i, _f, _f, _vp]),
     "spring_update_support_size": (_i, [_vp, _vp, _i, _i, _f, _vp, _vp]),
     "spring_fourier_error": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
+    "spring_fourier_error_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp]),
     "spring_area_stats": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp]),
     "spring_random_choice": (_i, [_u64, _i, _i, _vp, _vp]),
     "spring_crossover_map": (_i, [_u64, _i, _i, _i, _i, _i, _f, _vp, _vp]),
@@ -239,6 +240,19 @@ def spring_fourier_error(x, S, M):
     b, n = _batch_n(x)
     err = torch.empty(b, dtype=torch.float64, device=x.device)
     _call("spring_fourier_error", _ptr(x), _ptr(S), _ptr(M), b, n, _ptr(err), _stream())
+    return err
+
+
+def spring_fourier_error_noalloc(x, S, M, err=None):
+    """GetError with the library's fixed device scratch (no allocation by the library)."""
+    import torch
+    _need(x, torch.complex64, "x")
+    _need(S, torch.uint8, "S")
+    _need(M, torch.float32, "M")
+    b, n = _batch_n(x)
+    if err is None:
+        err = torch.empty(b, dtype=torch.float64, device=x.device)
+    _call("spring_fourier_error_noalloc", _ptr(x), _ptr(S), _ptr(M), b, n, _ptr(err), _stream())
     return err
 
 
