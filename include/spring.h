@@ -279,6 +279,23 @@ spring_status spring_initialize(uint64_t seed, const uint8_t* S0, const float* M
                                 int n_spheres, float gamma, float phi_max, void* x,
                                 void* stream);
 
+/* ---------------------------------------------------------------- kernel variants
+ * The two per-iteration passes (row pass: inverse row FFT, update, forward row FFT;
+ * column pass: column FFT, P_M, inverse column FFT) have launch-shape variants per side N:
+ *   row 0: state loads before the inverse transform, one block per SM of registers;
+ *   row 1 / 2: state loads after it, register budget for two / three blocks per SM;
+ *   col 0: default radix plan, 16-column tiles; col 1: alternative radix plan;
+ *   col 2: 32-column tiles (16 at N = 1024); col 3: 8-column tiles.
+ * Row variants and column variants 0, 2, 3 give bit-identical results; column variant 1
+ * uses other radices and differs by rounding.  A run tunes each side once per process
+ * (spring_autotune on the run's batch) unless the environment sets SPRING_AUTOTUNE=0 or
+ * the variant was set explicitly. */
+spring_status spring_set_kernel_variant(int n, int row_variant, int col_variant); /* -1 = keep */
+spring_status spring_get_kernel_variant(int n, int* row_variant, int* col_variant);
+/* Time every variant on `batch` scratch images of side n on `stream` and keep the
+ * fastest.  Allocates scratch; blocks the host until done; do not call during capture. */
+spring_status spring_autotune(int n, int batch, void* stream);
+
 /* ---------------------------------------------------------------- instrumentation
  * Per-kernel-class launch counts and (when enabled) CUDA-event durations recorded on the
  * launching stream.  Used by the benchmark for its roofline figures. */
@@ -286,7 +303,8 @@ typedef struct {
   uint64_t launches;       /* launches since the last reset */
   double total_ms;         /* summed event time (timing enabled only) */
   uint64_t timed;          /* launches that were timed */
-  double bytes_per_launch; /* algorithmic bytes of the last launch */
+  double bytes_per_launch; /* mean algorithmic bytes of the timed launches (of the last
+                              launch if none was timed) */
 } spring_kernel_stat;
 #define SPRING_KC_ROW_ITER 0  /* iteration row pass (inverse row FFT, update, forward row FFT) */
 #define SPRING_KC_COL_PM 1    /* iteration column pass (column FFT, P_M, inverse column FFT) */

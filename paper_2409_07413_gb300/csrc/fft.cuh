@@ -137,23 +137,32 @@ struct BlockSync {
 };
 
 // ------------------------------------------------------------------ plans
-// Elements per thread and radices for each supported N.
+// A plan: transform length N, elements per thread E (T = N / E threads per transform),
+// radices R0, R1, R2 (R2 = 0: two stages).  E is a multiple of every radix.
+template <int N_, int E_, int R0_, int R1_, int R2_ = 0>
+struct PlanT {
+  static constexpr int N = N_, E = E_, R0 = R0_, R1 = R1_, R2 = R2_, T = N_ / E_;
+  static_assert(R0_ * R1_ * (R2_ ? R2_ : 1) == N_, "radices must multiply to N");
+  static_assert(E_ % R0_ == 0 && E_ % R1_ == 0 && (R2_ == 0 || E_ % R2_ == 0), "E vs radices");
+};
+// default plan for each supported N
 template <int N> struct Plan;
-template <> struct Plan<64>   { static constexpr int E = 8,  R0 = 8,  R1 = 8,  R2 = 0; };
-template <> struct Plan<128>  { static constexpr int E = 16, R0 = 8,  R1 = 16, R2 = 0; };
-template <> struct Plan<192>  { static constexpr int E = 24, R0 = 8,  R1 = 8,  R2 = 3; };
-template <> struct Plan<256>  { static constexpr int E = 16, R0 = 16, R1 = 16, R2 = 0; };
-template <> struct Plan<512>  { static constexpr int E = 16, R0 = 8,  R1 = 8,  R2 = 8; };
-template <> struct Plan<1024> { static constexpr int E = 32, R0 = 32, R1 = 32, R2 = 0; };
+template <> struct Plan<64>   : PlanT<64, 8, 8, 8> {};
+template <> struct Plan<128>  : PlanT<128, 16, 8, 16> {};
+template <> struct Plan<192>  : PlanT<192, 24, 8, 8, 3> {};
+template <> struct Plan<256>  : PlanT<256, 16, 16, 16> {};
+template <> struct Plan<512>  : PlanT<512, 16, 8, 8, 8> {};
+template <> struct Plan<1024> : PlanT<1024, 32, 32, 32> {};
 
 // shared-memory elements of one transform's padded exchange buffer
-template <int N>
-__host__ __device__ constexpr int pad_elems() {
-  using P = Plan<N>;
-  int a = N + N / P::R0;
-  int b = P::R2 ? N + N / P::R1 : 0;
+template <class P>
+__host__ __device__ constexpr int pad_elems_p() {
+  int a = P::N + P::N / P::R0;
+  int b = P::R2 ? P::N + P::N / P::R1 : 0;
   return a > b ? a : b;
 }
+template <int N>
+__host__ __device__ constexpr int pad_elems() { return pad_elems_p<Plan<N>>(); }
 
 // ------------------------------------------------------------------ stage helpers
 // twiddle multiplications of a stage: input r of butterfly u times W_{NS R}^{(j mod NS) r}
@@ -254,11 +263,10 @@ __device__ __forceinline__ void stage_tw(float2 (&b)[E], int t, const float2* __
 // ------------------------------------------------------------------ the transform
 // v: E registers of thread t (element t + m T).  sm: this transform's exchange buffer
 // (with STRIDE between consecutive elements).  tw: table of e^{-2 pi i k / N}.
-template <int N, int DIR, bool PAD, int STRIDE, class Sync>
-__device__ __forceinline__ void fft_regs(float2 (&v)[Plan<N>::E], float2* sm, int t,
+template <class P, int DIR, bool PAD, int STRIDE, class Sync>
+__device__ __forceinline__ void fft_plan(float2 (&v)[P::E], float2* sm, int t,
                                          const float2* __restrict__ tw, const Sync& sync) {
-  using P = Plan<N>;
-  constexpr int E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2;
+  constexpr int N = P::N, E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2;
   float2 b[E];
   // stage 0 (NS = 1): inputs j + r N/R0 are the registers u + r E/R0
 #pragma unroll
@@ -290,6 +298,13 @@ __device__ __forceinline__ void fft_regs(float2 (&v)[Plan<N>::E], float2* sm, in
 #pragma unroll
       for (int r = 0; r < R2; ++r) v[u + r * (E / R2)] = b[u * R2 + r];
   }
+}
+
+// the default plan of side N
+template <int N, int DIR, bool PAD, int STRIDE, class Sync>
+__device__ __forceinline__ void fft_regs(float2 (&v)[Plan<N>::E], float2* sm, int t,
+                                         const float2* __restrict__ tw, const Sync& sync) {
+  fft_plan<Plan<N>, DIR, PAD, STRIDE>(v, sm, t, tw, sync);
 }
 
 }  // namespace spring

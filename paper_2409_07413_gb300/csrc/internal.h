@@ -31,6 +31,10 @@ spring_status launch_row_fft_tw(int n, int dir, const float2* in, float2* out, c
 spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
                                 const float2* tw_all, cudaStream_t s);
 
+// kernel-variant autotuning of side n on `batch` images (once per process and side)
+spring_status ensure_tuned(int n, int batch, cudaStream_t s);
+spring_status prepare_fft_kernels(int n);
+
 // ---------------------------------------------------------------- composite transforms
 // unitary 2D transform of `batch` images: out = F x (dir -1) or F^-1 x (dir +1); in may
 // equal out.  Smul (forward only): transform S x instead of x.

@@ -705,18 +705,20 @@ spring_status launch_normalise(int n, const float2* X, const float* M, int P, fl
 }
 
 // ------------------------------------------------------------------ monitors
-constexpr int DENS_BLOCKS = 16;
+constexpr int DENS_BLOCKS = 64;
 
 __global__ void k_density_partial(const float2* __restrict__ x, long long nn, double* __restrict__ part) {
+  // monitors only: per-thread FP32 sums (a few hundred terms), FP64 across threads
   const int p = blockIdx.y;
-  double sr = 0.0, si = 0.0, sa = 0.0;
+  float fr = 0.f, fi = 0.f, fa = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn;
        i += (long long)gridDim.x * blockDim.x) {
     const float2 v = x[(long long)p * nn + i];
-    sr += v.x;
-    si += v.y;
-    sa += sqrt((double)v.x * v.x + (double)v.y * v.y);
+    fr += v.x;
+    fi += v.y;
+    fa += sqrtf(v.x * v.x + v.y * v.y);
   }
+  double sr = fr, si = fi, sa = fa;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     sr += __shfl_down_sync(0xffffffffu, sr, o);

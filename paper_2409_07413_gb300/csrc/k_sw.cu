@@ -17,58 +17,88 @@ struct Taps {
   int r;
 };
 
-// pass 1: |x| along rows -> tmp
-__global__ void k_smooth_rows(const float2* __restrict__ x, float* __restrict__ tmp, int n,
-                              long long total, const Taps taps) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  const long long row0 = (i / n) * n;
-  const int c = (int)(i - row0);
-  float acc = 0.f;
-  for (int d = -taps.r; d <= taps.r; ++d) {
-    int cc = c + d;
-    cc = ((cc % n) + n) % n;
-    const float2 v = __ldg(&x[row0 + cc]);
-    acc = fmaf(taps.w[d + taps.r], sqrtf(v.x * v.x + v.y * v.y), acc);
+// pass 1: |x| along rows -> tmp.  One block per row: |x| is computed once per pixel into
+// a shared row extended by a periodic halo of r pixels on each side, so each tap is a
+// plain shared-memory read.
+constexpr int SW_ROW_THREADS = 256;
+
+__global__ void __launch_bounds__(SW_ROW_THREADS) k_smooth_rows(const float2* __restrict__ x,
+                                                                float* __restrict__ tmp, int n,
+                                                                const Taps taps) {
+  extern __shared__ float ext[];  // n + 2 r
+  const long long row0 = (long long)blockIdx.x * n;
+  const int r = taps.r, len = n + 2 * r;
+  for (int k = threadIdx.x; k < len; k += blockDim.x) {
+    int c = k - r;
+    c %= n;
+    if (c < 0) c += n;
+    const float2 v = __ldg(&x[row0 + c]);
+    ext[k] = sqrtf(v.x * v.x + v.y * v.y);
   }
-  tmp[i] = acc;
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    float acc = 0.f;
+    for (int d = 0; d <= 2 * r; ++d) acc = fmaf(taps.w[d], ext[c + d], acc);
+    tmp[row0 + c] = acc;
+  }
 }
 
-// pass 2: along columns -> out, and the per-image maximum (non-negative floats compare
-// like their bit patterns, so an integer atomicMax is exact and order-independent)
-__global__ void k_smooth_cols(const float* __restrict__ tmp, float* __restrict__ out, int n,
-                              long long total, const Taps taps, unsigned* __restrict__ img_max) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  float acc = 0.f;
-  long long img = 0;
-  if (i < total) {
-    const long long nn = (long long)n * n;
-    img = i / nn;
-    const long long off = i - img * nn;
-    const int r = (int)(off / n), c = (int)(off - (long long)r * n);
-    const float* base = tmp + img * nn + c;
-    for (int d = -taps.r; d <= taps.r; ++d) {
-      int rr = r + d;
-      rr = ((rr % n) + n) % n;
-      acc = fmaf(taps.w[d + taps.r], __ldg(&base[(long long)rr * n]), acc);
-    }
-    out[i] = acc;
+// pass 2: along columns -> out, and the per-image maximum.  A block smooths a tile of
+// 32 columns x SW_TILE_ROWS rows from a shared copy of those columns with r halo rows
+// above and below (periodic).  Non-negative floats compare like their bit patterns, so an
+// integer atomicMax gives the exact maximum in any order.
+constexpr int SW_TILE_ROWS = 64;
+
+__global__ void __launch_bounds__(256) k_smooth_cols(const float* __restrict__ tmp, float* __restrict__ out,
+                                                     int n, const Taps taps, unsigned* __restrict__ img_max) {
+  extern __shared__ float tile[];  // (SW_TILE_ROWS + 2 r) x 32
+  const int r = taps.r;
+  const int tiles_x = n / 32, tiles_y = (n + SW_TILE_ROWS - 1) / SW_TILE_ROWS;
+  const int img = blockIdx.x / (tiles_x * tiles_y);
+  const int rem = blockIdx.x % (tiles_x * tiles_y);
+  const int c0 = (rem % tiles_x) * 32, r0 = (rem / tiles_x) * SW_TILE_ROWS;
+  const int rows_out = min(SW_TILE_ROWS, n - r0), rows_in = rows_out + 2 * r;
+  const long long base = (long long)img * n * n;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int k = ly; k < rows_in; k += 8) {
+    int rr = r0 - r + k;
+    rr %= n;
+    if (rr < 0) rr += n;
+    tile[k * 32 + lx] = __ldg(&tmp[base + (long long)rr * n + c0 + lx]);
+  }
+  __syncthreads();
+  unsigned vmax = 0u;
+  for (int k = ly; k < rows_out; k += 8) {
+    float acc = 0.f;
+    for (int d = 0; d <= 2 * r; ++d) acc = fmaf(taps.w[d], tile[(k + d) * 32 + lx], acc);
+    out[base + (long long)(r0 + k) * n + c0 + lx] = acc;
+    vmax = max(vmax, __float_as_uint(fmaxf(acc, 0.f)));
   }
   if (img_max) {
-    // blocks of 256 threads never straddle two images (N^2 is a multiple of 256)
-    unsigned v = (i < total) ? __float_as_uint(fmaxf(acc, 0.f)) : 0u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0 && i < total) atomicMax(&img_max[img], v);
+    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    if (lx == 0) atomicMax(&img_max[img], vmax);
   }
 }
 
+// S = [rho_sigma >= tau max].  The comparison is decided exactly as in FP64: with
+// t = tau * max in double, (double)v >= t holds for a float v iff v >= f, f the smallest
+// float not below t; f is formed once per block.
+constexpr int SW_THR_PER_BLOCK = 1024;
+
 __global__ void k_threshold(const float* __restrict__ sm, const unsigned* __restrict__ img_max,
-                            double tau, uint8_t* __restrict__ S, long long nn, long long total) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  const double thr = tau * (double)__uint_as_float(img_max[i / nn]);
-  S[i] = ((double)sm[i] >= thr) ? 1 : 0;
+                            double tau, uint8_t* __restrict__ S, long long nn) {
+  __shared__ float f_s;
+  const long long first = (long long)blockIdx.x * SW_THR_PER_BLOCK;  // blocks never straddle images
+  if (threadIdx.x == 0) {
+    const double t = tau * (double)__uint_as_float(img_max[first / nn]);
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    f_s = f;
+  }
+  __syncthreads();
+  const float f = f_s;
+  for (int k = threadIdx.x; k < SW_THR_PER_BLOCK; k += blockDim.x) S[first + k] = sm[first + k] >= f ? 1 : 0;
 }
 
 static Taps make_taps(float sigma) {
@@ -96,13 +126,17 @@ spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int 
   const long long total = (long long)batch * n * n;
   if (total == 0) return SPRING_OK;
   if (img_max) SPRING_CUDA(cudaMemsetAsync(img_max, 0, sizeof(unsigned) * batch, s));
-  const int th = 256;
+  const size_t row_smem = sizeof(float) * (n + 2 * taps.r);
+  const size_t col_smem = sizeof(float) * 32 * (SW_TILE_ROWS + 2 * taps.r);
+  if (col_smem > 48 * 1024)
+    cudaFuncSetAttribute(k_smooth_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
   launch_begin(SPRING_KC_OTHER, s);
-  k_smooth_rows<<<div_up(total, th), th, 0, s>>>(x, tmp, n, total, taps);
+  k_smooth_rows<<<(int)((long long)batch * n), SW_ROW_THREADS, row_smem, s>>>(x, tmp, n, taps);
   SPRING_CHECK_LAUNCH();
   launch_end(SPRING_KC_OTHER, s, total * 12.0);
+  const int tiles = (n / 32) * ((n + SW_TILE_ROWS - 1) / SW_TILE_ROWS);
   launch_begin(SPRING_KC_OTHER, s);
-  k_smooth_cols<<<div_up(total, th), th, 0, s>>>(tmp, out, n, total, taps, img_max);
+  k_smooth_cols<<<batch * tiles, 256, col_smem, s>>>(tmp, out, n, taps, img_max);
   SPRING_CHECK_LAUNCH();
   launch_end(SPRING_KC_OTHER, s, total * 8.0);
   return SPRING_OK;
@@ -113,7 +147,7 @@ spring_status launch_threshold(int n, const float* sm, const unsigned* img_max, 
   const long long nn = (long long)n * n, total = nn * batch;
   if (total == 0) return SPRING_OK;
   launch_begin(SPRING_KC_OTHER, s);
-  k_threshold<<<div_up(total, 256), 256, 0, s>>>(sm, img_max, (double)tau, S, nn, total);
+  k_threshold<<<(int)(total / SW_THR_PER_BLOCK), 256, 0, s>>>(sm, img_max, (double)tau, S, nn);
   SPRING_CHECK_LAUNCH();
   launch_end(SPRING_KC_OTHER, s, total * 5.0);
   return SPRING_OK;

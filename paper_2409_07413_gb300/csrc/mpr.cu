@@ -33,8 +33,6 @@ struct spring_problem {
 
 namespace spring {
 
-spring_status prepare_fft_kernels(int n);
-
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -157,6 +155,7 @@ class Run {
     s = stream;
     L = make_layout(n, p);
     SPRING_TRY(prepare_fft_kernels(n));
+    SPRING_TRY(ensure_tuned(n, B, s));
     DeviceTables tb;
     SPRING_TRY(device_tables(&tb));
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&mem), L.total, s);

@@ -33,7 +33,8 @@ struct KStat {
   std::atomic<uint64_t> launches{0};
   std::atomic<uint64_t> timed{0};
   double total_ms = 0.0;
-  double bytes = 0.0;
+  double bytes = 0.0;        // algorithmic bytes of the last launch
+  double timed_bytes = 0.0;  // summed over the timed launches
 };
 static KStat g_kstat[SPRING_KC_COUNT];
 static std::atomic<uint64_t> g_launches{0};
@@ -42,6 +43,7 @@ static std::mutex g_tmu;
 struct Pending {
   int kc;
   cudaEvent_t a, b;
+  double bytes;
 };
 static std::vector<Pending> g_pending;
 static std::vector<cudaEvent_t> g_event_pool;
@@ -81,7 +83,7 @@ void launch_end(int kc, cudaStream_t s, double bytes) {
     std::lock_guard<std::mutex> lk(g_tmu);
     cudaEvent_t b = take_event();
     cudaEventRecord(b, s);
-    g_pending.push_back({kc, t_begin_event, b});
+    g_pending.push_back({kc, t_begin_event, b, bytes});
     t_begin_event = nullptr;
   }
 }
@@ -93,6 +95,7 @@ static void drain_pending() {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       g_kstat[p.kc].total_ms += ms;
+      g_kstat[p.kc].timed_bytes += p.bytes;
       g_kstat[p.kc].timed.fetch_add(1);
     }
     g_event_pool.push_back(p.a);
@@ -232,6 +235,7 @@ void spring_stats_reset(void) {
     k.launches = 0;
     k.timed = 0;
     k.total_ms = 0.0;
+    k.timed_bytes = 0.0;
   }
   g_launches = 0;
 }
@@ -247,7 +251,7 @@ void spring_stats_get(int kc, spring_kernel_stat* out) {
   out->launches = g_kstat[kc].launches;
   out->timed = g_kstat[kc].timed;
   out->total_ms = g_kstat[kc].total_ms;
-  out->bytes_per_launch = g_kstat[kc].bytes;
+  out->bytes_per_launch = out->timed ? g_kstat[kc].timed_bytes / (double)out->timed : g_kstat[kc].bytes;
 }
 
 uint64_t spring_launch_count(void) { return g_launches.load(); }

@@ -1,0 +1,83 @@
+"""Micro-benchmark of the per-iteration passes (row pass with the fused update, column
+pass with the fused modulus projection) on random state.
+
+    python -m paper_2409_07413_gb300.iterbench --n 512 --batch 128 --iters 50 --alg 2
+
+Prints one JSON line per side with each pass's average CUDA-event time, algorithmic bytes
+and GB/s (events are recorded on the launching stream around every launch).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def run(n, batch, iters, alg, warm=3):
+    import torch
+
+    from paper_2409_07413_gb300 import spring
+
+    g = torch.Generator(device="cuda").manual_seed(n)
+    x = torch.randn((batch, n, n), dtype=torch.complex64, device="cuda", generator=g)
+    S = (torch.rand((batch, n, n), device="cuda", generator=g) < 0.25).to(torch.uint8)
+    M = torch.rand((n, n), device="cuda", generator=g) + 0.1
+    M[torch.rand((n, n), device="cuda", generator=g) < 0.05] = -1.0
+    spring.spring_iterate(x, S, M, alg, 0.9, 0.5, warm)
+    torch.cuda.synchronize()
+    spring.stats_reset()
+    spring.stats_enable_timing(True)
+    spring.spring_iterate(x, S, M, alg, 0.9, 0.5, iters)
+    torch.cuda.synchronize()
+    spring.stats_enable_timing(False)
+    out = {"n": n, "batch": batch, "iters": iters, "alg": alg}
+    for name, kc in (("row_iter", spring.KC_ROW_ITER), ("col_pm", spring.KC_COL_PM)):
+        st = spring.stats_get(kc)
+        ms = st.total_ms / max(1, st.timed)
+        out[name] = {"avg_ms": ms, "bytes": st.bytes_per_launch,
+                     "GBps": st.bytes_per_launch / (ms / 1e3) / 1e9 if ms > 0 else None}
+    it_ms = out["row_iter"]["avg_ms"] + out["col_pm"]["avg_ms"]
+    out["iteration_ms"] = it_ms
+    out["iteration_px_per_s"] = batch * n * n / (it_ms / 1e3)
+    return out
+
+
+def sweep(n, batch, iters, alg):
+    """Time every (row, column) launch variant of side n; returns the list of results."""
+    from paper_2409_07413_gb300 import spring
+    saved = spring.get_kernel_variant(n)
+    res = []
+    try:
+        for rv in range(3):
+            for cv in range(4):
+                spring.set_kernel_variant(n, rv, cv)
+                r = run(n, batch, iters, alg)
+                r["variant"] = [rv, cv]
+                res.append(r)
+    finally:
+        spring.set_kernel_variant(n, *saved)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, nargs="+", default=[512])
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--alg", type=int, default=2)
+    ap.add_argument("--sweep", action="store_true", help="time every launch variant")
+    a = ap.parse_args()
+    for n in a.n:
+        b = a.batch if a.batch > 0 else max(1, (128 * 512 * 512) // (n * n))
+        if a.sweep:
+            for r in sweep(n, b, a.iters, a.alg):
+                print(json.dumps({"n": n, "variant": r["variant"], "row_ms": r["row_iter"]["avg_ms"],
+                                  "row_GBps": r["row_iter"]["GBps"], "col_ms": r["col_pm"]["avg_ms"],
+                                  "col_GBps": r["col_pm"]["GBps"]}), flush=True)
+        else:
+            print(json.dumps(run(n, b, a.iters, a.alg)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

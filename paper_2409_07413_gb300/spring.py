@@ -81,6 +81,9 @@ _SIGS = {
     "spring_select": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp]),
     "spring_average": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "spring_initialize": (_i, [_u64, _vp, _vp, _i, _i, _i, _f, _f, _vp, _vp]),
+    "spring_set_kernel_variant": (_i, [_i, _i, _i]),
+    "spring_get_kernel_variant": (_i, [_i, C.POINTER(_i), C.POINTER(_i)]),
+    "spring_autotune": (_i, [_i, _i, _vp]),
     "spring_stats_reset": (None, []),
     "spring_stats_enable_timing": (None, [_i]),
     "spring_stats_get": (None, [_i, C.POINTER(KernelStat)]),
@@ -336,6 +339,22 @@ def spring_initialize(seed, S0, M, P, n_spheres=5, gamma=1.0, phi_max=0.0):
     _call("spring_initialize", C.c_uint64(seed), _ptr(S0), _ptr(M), n, int(P), int(n_spheres),
           float(gamma), float(phi_max), _ptr(x), _stream())
     return x
+
+
+# ------------------------------------------------------------------ kernel variants
+def set_kernel_variant(n, row=-1, col=-1):
+    _call("spring_set_kernel_variant", int(n), int(row), int(col))
+
+
+def get_kernel_variant(n):
+    r, c = C.c_int(), C.c_int()
+    _call("spring_get_kernel_variant", int(n), C.byref(r), C.byref(c))
+    return r.value, c.value
+
+
+def autotune(n, batch):
+    _call("spring_autotune", int(n), int(batch), _stream())
+    return get_kernel_variant(n)
 
 
 # ------------------------------------------------------------------ instrumentation

@@ -342,3 +342,40 @@ def test_initialize(sp, n):
     x = host(sp.spring_initialize(5, dev(pat.support0), dev(menc(M, mask)), 6, 5, 0.8, 0.5))
     ref = oracle.initialize(5, pat.support0, M.astype(np.float64) ** 2, mask, 6, 5, 0.8, 0.5)
     assert rel(x, ref) < TOL
+
+
+# ----------------------------------------------------------------------------- launch variants
+@pytest.mark.parametrize("n", [64, 192, 512, 1024])
+def test_kernel_variants_parity(sp, n):
+    """Every launch-shape variant of the two iteration passes matches the oracle; row
+    variants and the same-plan column variants are bit-identical to each other."""
+    B = 2
+    x, S = synthetic.population_state(7 * n, B, n, support_frac=0.3)
+    M, mask = synthetic.random_modulus(7 * n, n, masked_frac=0.1)
+    ref = oracle.iterate(c64(x), S, *as_oracle_M(M, mask), 2, 0.9, 1.0, 1)
+    saved = sp.get_kernel_variant(n)
+    out = {}
+    try:
+        for rv in range(3):
+            for cv in range(4):
+                sp.set_kernel_variant(n, rv, cv)
+                xg = dev(c64(x))
+                sp.spring_iterate(xg, dev(S), dev(menc(M, mask)), 2, 0.9, 1.0, 1)
+                got = host(xg)
+                assert rel(got, ref) < TOL, (rv, cv)
+                out[(rv, cv)] = got
+    finally:
+        sp.set_kernel_variant(n, *saved)
+    for rv in range(3):
+        for cv in (0, 2, 3):
+            assert np.array_equal(out[(rv, cv)], out[(0, 0)]), (rv, cv)
+        assert np.array_equal(out[(rv, 1)], out[(0, 1)]), rv
+
+
+def test_autotune_picks_a_valid_variant(sp):
+    saved = sp.get_kernel_variant(256)
+    try:
+        rv, cv = sp.autotune(256, 8)
+        assert 0 <= rv < 3 and 0 <= cv < 4
+    finally:
+        sp.set_kernel_variant(256, *saved)
