@@ -284,10 +284,14 @@ spring_status spring_initialize(uint64_t seed, const uint8_t* S0, const float* M
  * column pass: column FFT, P_M, inverse column FFT) have launch-shape variants per side N:
  *   row 0: state loads before the inverse transform, one block per SM of registers;
  *   row 1 / 2: state loads after it, register budget for two / three blocks per SM;
+ *   row 3 / 4: x and S rows streamed into shared memory during the inverse transform;
+ *   row 5 / 6: alternative radix plan, register budget for two / four blocks per SM;
  *   col 0: default radix plan, 16-column tiles; col 1: alternative radix plan;
- *   col 2: 32-column tiles (16 at N = 1024); col 3: 8-column tiles.
- * Row variants and column variants 0, 2, 3 give bit-identical results; column variant 1
- * uses other radices and differs by rounding.  A run tunes each side once per process
+ *   col 2: 32-column tiles (16 at N = 1024); col 3: 8-column tiles;
+ *   col 4 / 5: persistent blocks fed by TMA (16 / 8-column tiles, next tile in flight);
+ *   col 6 / 7: transposed tiles, one lane group per column (warp-level synchronisation).
+ * Variants sharing a radix plan give bit-identical results (row 0-4, row 5-6; column 0
+ * and 2-7); the alternative plans (row 5-6, column 1) differ by rounding.  A run tunes each side once per process
  * (spring_autotune on the run's batch) unless the environment sets SPRING_AUTOTUNE=0 or
  * the variant was set explicitly. */
 spring_status spring_set_kernel_variant(int n, int row_variant, int col_variant); /* -1 = keep */

@@ -55,6 +55,7 @@ struct DeviceTables {
   const float2* tw;
   const long long* rot_cos;
   const long long* rot_sin;
+  int* status;  // device status word: bit 2 = a bounded wait in a kernel timed out
 };
 // Tables of the current device (allocated on first use and kept until process exit).
 spring_status device_tables(DeviceTables* out);

@@ -135,6 +135,13 @@ struct WarpSync {  // a transform owned by a lane group inside one warp
 struct BlockSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
+// a transform owned by NT threads (whole warps) of a block: named barrier `id` (1..15)
+struct NamedSync {
+  unsigned id, nt;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nt) : "memory");
+  }
+};
 
 // ------------------------------------------------------------------ plans
 // A plan: transform length N, elements per thread E (T = N / E threads per transform),

@@ -35,6 +35,13 @@ spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, dou
 spring_status ensure_tuned(int n, int batch, cudaStream_t s);
 spring_status prepare_fft_kernels(int n);
 
+// tiled 3-D TMA descriptor of a float32 array (dim0 x dim1 x dim2, dim0 contiguous), box
+// box0 x box1 x 1; the descriptor is encoded on the host (driver entry point)
+spring_status encode_tmap_f32_3d(void* map, const void* base, int dim0, int dim1, int dim2, int box0,
+                                 int box1);
+// read and clear the per-device status word (bit 2: a kernel's bounded wait timed out)
+spring_status take_device_status(int* out);
+
 // ---------------------------------------------------------------- composite transforms
 // unitary 2D transform of `batch` images: out = F x (dir -1) or F^-1 x (dir +1); in may
 // equal out.  Smul (forward only): transform S x instead of x.

@@ -48,8 +48,8 @@ static int side_index(int n) {
 // Launch-shape variants of the two per-iteration passes, per side (see k_fft.cuh); the
 // defaults are the fastest measured on a GB300 at 33.5 M pixels per launch.
 static std::mutex g_var_mu;
-static int g_row_var[6] = {0, 1, 1, 0, 1, 0};
-static int g_col_var[6] = {0, 0, 0, 0, 0, 1};
+static int g_row_var[6] = {0, 5, 1, 0, 6, 0};
+static int g_col_var[6] = {0, 2, 0, 0, 0, 3};
 static bool g_tuned[6] = {false, false, false, false, false, false};
 
 static int row_variant(int n) {

@@ -18,13 +18,22 @@
 //
 // Launch-shape variants (bit-identical results within a plan):
 //   row:    0 = state loads before the inverse transform, 1 block/SM of registers;
-//           1 / 2 = state loads after it, register budget for 2 / 3 blocks per SM
+//           1 / 2 = state loads after it, register budget for 2 / 3 blocks per SM;
+//           3 / 4 = x and S rows streamed into shared memory (cp.async) during the
+//           inverse transform, register budget for 2 / 3 blocks per SM;
+//           5 / 6 = alternative radix plan (results differ by rounding), loads after the
+//           inverse transform, register budget for 2 / 4 blocks per SM
 //   column: 0 = default plan, 16-column tiles; 1 = alternative plan (other radices:
-//           results differ by rounding); 2 = 32-column tiles; 3 = 8-column tiles
+//           results differ by rounding); 2 = 32-column tiles; 3 = 8-column tiles;
+//           4 / 5 = persistent blocks fed by TMA: while a block transforms one tile, the
+//           next tile is already being copied into a second shared buffer (16 / 8 columns);
+//           6 / 7 = transposed tiles, one lane group per column (16 / 32 columns; 8 at
+//           N >= 1024 / 512)
 #pragma once
 
 #include "fft.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace spring {
 
@@ -33,8 +42,8 @@ enum { COL_PM = 0, COL_FWD = 1, COL_INV = 2, COL_ERR = 3 };
 enum { OP_ROW_ITER = 0, OP_ROW_FWD, OP_ROW_INV, OP_COL_PM, OP_COL_FWD, OP_COL_INV, OP_COL_ERR };
 
 constexpr int ROW_THREADS = 256;
-constexpr int ROW_VARIANTS = 3;
-constexpr int COL_VARIANTS = 4;
+constexpr int ROW_VARIANTS = 7;
+constexpr int COL_VARIANTS = 8;
 constexpr int ERR_W = 16;  // column tile of the error pass (layout of its partial sums)
 
 // alternative column-pass plans
@@ -43,8 +52,14 @@ template <> struct AltPlan<64>   : PlanT<64, 16, 16, 4> {};
 template <> struct AltPlan<128>  : PlanT<128, 16, 16, 8> {};
 template <> struct AltPlan<192>  : PlanT<192, 24, 3, 8, 8> {};
 template <> struct AltPlan<256>  : PlanT<256, 32, 32, 8> {};
-template <> struct AltPlan<512>  : PlanT<512, 32, 32, 16> {};
+template <> struct AltPlan<512>  : PlanT<512, 8, 8, 8, 8> {};
 template <> struct AltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
+
+// alternative row-pass plans (one lane group per row: T <= 32)
+template <int N> struct RowAltPlan : Plan<N> {};
+template <> struct RowAltPlan<512> : PlanT<512, 8, 8, 8, 8> {};
+template <> struct RowAltPlan<256> : PlanT<256, 32, 32, 8> {};
+template <> struct RowAltPlan<128> : PlanT<128, 16, 16, 8> {};
 
 struct RowArgs {
   const float2* in;   // ITER: w (column-pass output); FWD/INV: input rows
@@ -73,12 +88,22 @@ struct FftOp {
   ColArgs ca{};
 };
 
+// synchronisation of the T threads that own one row transform: a lane group inside a
+// warp (T <= 32) or a named barrier over T / 32 whole warps (T = 64, 128)
+template <int T, bool WIDE = (T > 32)>
+struct GroupSync;
 template <int T>
-__device__ __forceinline__ WarpSync group_sync() {
-  static_assert(T <= 32, "one transform per lane group of a warp");
-  const unsigned lane = threadIdx.x & 31u;
-  return WarpSync{T == 32 ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(unsigned)(T - 1)))};
-}
+struct GroupSync<T, false> {
+  static __device__ __forceinline__ WarpSync make() {
+    const unsigned lane = threadIdx.x & 31u;
+    return WarpSync{T == 32 ? 0xffffffffu : (((1u << T) - 1u) << (lane & ~(unsigned)(T - 1)))};
+  }
+};
+template <int T>
+struct GroupSync<T, true> {
+  static_assert(T % 32 == 0 && T <= 128, "wide groups are whole warps");
+  static __device__ __forceinline__ NamedSync make() { return NamedSync{1u + threadIdx.x / T, (unsigned)T}; }
+};
 
 __device__ __forceinline__ float2 update_pixel(int alg, float2 xo, float2 pm, bool in_c, float beta) {
   if (in_c) return pm;
@@ -88,17 +113,51 @@ __device__ __forceinline__ float2 update_pixel(int alg, float2 xo, float2 pm, bo
   return make_float2(beta * xo.x + c * pm.x, beta * xo.y + c * pm.y);
 }
 
-template <class P, int MODE, int ALG, bool LATE, int MINB>
+// row-pass staging area of one lane group: x row (N float2) and S row (N bytes)
+template <class P>
+__host__ __device__ constexpr int stage_elems() { return P::N + P::N / 8; }
+
+template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false>
 __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
   constexpr int N = P::N, E = P::E, T = P::T, G = ROW_THREADS / T, SME = pad_elems_p<P>();
   extern __shared__ float2 smem[];
   const int grp = threadIdx.x / T, t = threadIdx.x % T;
   float2* sm = smem + grp * SME;
-  const WarpSync sync = group_sync<T>();
+  float2* xs = smem + G * SME + grp * stage_elems<P>();  // STAGE: x row, then S row
+  uint8_t* ss = reinterpret_cast<uint8_t*>(xs + N);
+  const auto sync = GroupSync<T>::make();
   for (long long row = (long long)blockIdx.x * G + grp; row < a.nrows; row += (long long)gridDim.x * G) {
     const long long base = row * N + t;
     float2 v[E];
-    if constexpr (MODE == ROW_ITER) {
+    if constexpr (MODE == ROW_ITER && STAGE) {
+      // x_n and S of this row stream into shared memory while the row is transformed
+      const float2* xr = a.x + row * N;
+      const uint8_t* sr = a.S + row * N;
+      if (ALG != 0)
+        for (int k = t; k < N / 2; k += T) cp_async16(xs + 2 * k, xr + 2 * k);
+      for (int k = t; k < N / 16; k += T) cp_async16(ss + 16 * k, sr + 16 * k);
+      cp_async_commit();
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = a.in[base + m * T];
+      fft_plan<P, +1, true, 1>(v, sm, t, a.tw, sync);  // m = P_M x_n
+      cp_async_wait_all();
+      sync();
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const float2 pm = v[m];
+        bool in_c = ss[t + m * T] != 0;
+        if (a.chi_on) in_c = in_c && (pm.x >= a.cchi * sqrtf(pm.x * pm.x + pm.y * pm.y));
+        const float2 xn = update_pixel(ALG, ALG ? xs[t + m * T] : pm, pm, in_c, a.beta);
+        v[m] = xn;
+        a.x[base + m * T] = xn;
+      }
+      sync();  // the staging area is reused by the next row
+      if (a.zout) {
+        fft_plan<P, -1, true, 1>(v, sm, t, a.tw, sync);
+#pragma unroll
+        for (int m = 0; m < E; ++m) a.out[base + m * T] = v[m];
+      }
+    } else if constexpr (MODE == ROW_ITER) {
       uint8_t s[E];
       float2 xo[E];
       if constexpr (!LATE) {
@@ -147,7 +206,7 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
 }
 
 template <class P, int W, int MODE>
-__global__ void __launch_bounds__(W * P::T) k_col(ColArgs a) {
+__global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(ColArgs a) {
   constexpr int N = P::N, E = P::E, T = P::T, STRIPS = N / W;
   extern __shared__ float2 smem[];
   const int c = threadIdx.x % W, t = threadIdx.x / W;
@@ -155,6 +214,18 @@ __global__ void __launch_bounds__(W * P::T) k_col(ColArgs a) {
   const int col = strip * W + c;
   float2* base = a.data + (size_t)img * N * N + col;
   const BlockSync sync;
+  // PM / ERR: the strip's modulus values (N x W floats) arrive in shared memory by
+  // cp.async while the tile is read and transformed, so no global latency is exposed
+  // between the forward and the inverse transform
+  float* Ms = reinterpret_cast<float*>(smem + (size_t)N * W);
+  if constexpr (MODE == COL_PM || MODE == COL_ERR) {
+    constexpr int CH = W / 4;  // 16-byte chunks per row
+    for (int k = threadIdx.x; k < N * CH; k += blockDim.x) {
+      const int row = k / CH, q = k % CH;
+      cp_async16(Ms + row * W + 4 * q, a.M + (size_t)row * N + strip * W + 4 * q);
+    }
+    cp_async_commit();
+  }
   float2 v[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = base[(size_t)(t + m * T) * N];
@@ -170,9 +241,11 @@ __global__ void __launch_bounds__(W * P::T) k_col(ColArgs a) {
     for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * N] = cscale(v[m], a.scale);
   } else if constexpr (MODE == COL_PM) {
     constexpr float inv_n = 1.0f / N;
+    cp_async_wait_all();
+    sync();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const float Mv = __ldg(&a.M[(size_t)(t + m * T) * N + col]);
+      const float Mv = Ms[(t + m * T) * W + c];
       const float2 X = v[m];
       if (Mv >= 0.f) {
         const float a2 = X.x * X.x + X.y * X.y;
@@ -187,9 +260,11 @@ __global__ void __launch_bounds__(W * P::T) k_col(ColArgs a) {
   } else {  // COL_ERR: FP64 accumulation of the Fourier error (Eq. error_calc)
     constexpr float inv_n = 1.0f / N;
     double num = 0.0, den = 0.0;
+    cp_async_wait_all();
+    sync();
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const float Mv = __ldg(&a.M[(size_t)(t + m * T) * N + col]);
+      const float Mv = Ms[(t + m * T) * W + c];
       if (Mv >= 0.f) {
         const float amp = sqrtf(v[m].x * v[m].x + v[m].y * v[m].y) * inv_n;
         const double d = (double)amp - (double)Mv;
@@ -223,26 +298,190 @@ __global__ void __launch_bounds__(W * P::T) k_col(ColArgs a) {
   }
 }
 
-// ------------------------------------------------------------------ launch helpers
-template <class K>
-inline void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// Column pass (COL_PM) with transposed tiles.  The block's W columns are read with
+// coalesced row segments and written transposed into shared memory (one region per
+// column, odd stride: conflict-free); each lane group of T threads then transforms one
+// whole column with only warp-level synchronisation, exactly like a row, applies P_M with
+// the transposed modulus strip, and the result leaves through the same regions with
+// coalesced stores.  Two block barriers per tile.
+template <class P>
+__host__ __device__ constexpr int colt_stride() { return pad_elems_p<P>() | 1; }
+
+template <class P, int W>
+__global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_colT(ColArgs a) {
+  constexpr int N = P::N, E = P::E, T = P::T, STRIPS = N / W, RS = colt_stride<P>(), MS = N + 1;
+  extern __shared__ float2 smem[];
+  float2* reg = smem;                                           // W regions of RS
+  float* MsT = reinterpret_cast<float*>(smem + (size_t)W * RS);  // W x MS
+  const int img = blockIdx.x / STRIPS, strip = blockIdx.x % STRIPS;
+  float2* base = a.data + (size_t)img * N * N + strip * W;
+  const float* Mb = a.M + strip * W;
+  // phase A: coalesced loads (lanes along the columns), transposed writes
+  {
+    const int ca = threadIdx.x % W, ra = threadIdx.x / W;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int row = ra + k * T;
+      reg[ca * RS + row] = base[(size_t)row * N + ca];
+      MsT[ca * MS + row] = __ldg(&Mb[(size_t)row * N + ca]);
+    }
+  }
+  __syncthreads();
+  // phase B: one lane group per column
+  {
+    const int cb = threadIdx.x / T, t = threadIdx.x % T;
+    float2* col = reg + cb * RS;
+    const float* mc = MsT + cb * MS;
+    const auto sync = GroupSync<T>::make();
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = col[t + m * T];
+    sync();
+    fft_plan<P, -1, true, 1>(v, col, t, a.tw, sync);
+    constexpr float inv_n = 1.0f / N;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float Mv = mc[t + m * T];
+      const float2 X = v[m];
+      if (Mv >= 0.f) {
+        const float a2 = X.x * X.x + X.y * X.y;
+        v[m] = a2 > 0.f ? cscale(X, Mv * rsqrtf(a2) * inv_n) : make_float2(Mv * inv_n, 0.f);
+      } else {
+        v[m] = cscale(X, inv_n * inv_n);
+      }
+    }
+    fft_plan<P, +1, true, 1>(v, col, t, a.tw, sync);
+#pragma unroll
+    for (int m = 0; m < E; ++m) col[t + m * T] = v[m];
+  }
+  __syncthreads();
+  // phase C: coalesced stores
+  {
+    const int ca = threadIdx.x % W, ra = threadIdx.x / W;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int row = ra + k * T;
+      base[(size_t)row * N + ca] = reg[ca * RS + row];
+    }
+  }
 }
 
-template <class P, int MODE, int ALG, bool LATE, int MINB>
+template <class P, int W>
+inline spring_status colT_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
+  constexpr int N = P::N;
+  const size_t smem = (size_t)W * colt_stride<P>() * sizeof(float2) + (size_t)W * (N + 1) * sizeof(float);
+  if (prepare_only) return allow_smem(k_colT<P, W>, smem);
+  if (op.ca.batch < 1) return SPRING_OK;
+  launch_begin(op.kclass, s);
+  k_colT<P, W><<<op.ca.batch * (N / W), W * P::T, smem, s>>>(op.ca);
+  SPRING_CHECK_LAUNCH();
+  launch_end(op.kclass, s, op.bytes);
+  return SPRING_OK;
+}
+
+// Persistent column pass (COL_PM) fed by TMA.  Tiles (image, 16- or 8-column strip) are
+// taken in a grid-stride sequence; the next tile's bulk tensor copy into the second
+// shared buffer is issued before the current tile is transformed, so HBM reads overlap the
+// transforms.  The tile buffer is also the transform's exchange area.  Waits are bounded;
+// a timeout sets bit 2 of *status and the block returns.
+template <class P, int W>
+__global__ void __launch_bounds__(W * P::T, (W * P::T <= 256 ? 2 : 1))
+    k_col_pm_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap mmap,
+                 ColArgs a, int ntiles, int* status) {
+  constexpr int N = P::N, E = P::E, T = P::T, STRIPS = N / W;
+  constexpr int BOXR = N > 256 ? 256 : N, NBOX = N / BOXR;
+  constexpr uint32_t TILE_BYTES = (uint32_t)N * W * 8 + (uint32_t)N * W * 4;  // w tile + M strip
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // TMA destinations 1024-byte aligned (the launch reserves the slack)
+  float2* const buf0 = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float2* const buf1 = buf0 + N * W;
+  float* const mb0 = reinterpret_cast<float*>(buf1 + N * W);
+  float* const mb1 = mb0 + N * W;
+  __shared__ __align__(8) uint64_t mbar[2];
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int tile, int b) {
+    const int img = tile / STRIPS, strip = tile % STRIPS;
+    float2* dst = b ? buf1 : buf0;
+    float* mdst = b ? mb1 : mb0;
+    mbar_arrive_expect_tx(&mbar[b], TILE_BYTES);
+#pragma unroll
+    for (int k = 0; k < NBOX; ++k) {
+      tma_load_3d(dst + k * BOXR * W, &tmap, strip * 2 * W, k * BOXR, img, &mbar[b]);
+      tma_load_3d(mdst + k * BOXR * W, &mmap, strip * W, k * BOXR, 0, &mbar[b]);
+    }
+  };
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  const BlockSync sync;
+  constexpr float inv_n = 1.0f / N;
+  for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const int nxt = tile + gridDim.x;
+    if (threadIdx.x == 0 && nxt < ntiles) {
+      fence_proxy_async_smem();  // the other buffer's last generic accesses precede the copy
+      issue(nxt, b ^ 1);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&mbar[b], (uint32_t)(it >> 1) & 1u));
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        atomicOr(status, 2);
+        if (nxt < ntiles) mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+      }
+      return;
+    }
+    float2* cur = b ? buf1 : buf0;
+    const float* Mcur = b ? mb1 : mb0;
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = cur[(t + m * T) * W + c];
+    sync();  // every thread has its inputs before the exchange overwrites the tile
+    fft_plan<P, -1, false, W>(v, cur + c, t, a.tw, sync);
+    const int img = tile / STRIPS, col = (tile % STRIPS) * W + c;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float Mv = Mcur[(t + m * T) * W + c];
+      const float2 X = v[m];
+      if (Mv >= 0.f) {
+        const float a2 = X.x * X.x + X.y * X.y;
+        v[m] = a2 > 0.f ? cscale(X, Mv * rsqrtf(a2) * inv_n) : make_float2(Mv * inv_n, 0.f);
+      } else {
+        v[m] = cscale(X, inv_n * inv_n);
+      }
+    }
+    fft_plan<P, +1, false, W>(v, cur + c, t, a.tw, sync);
+    float2* base = a.data + (size_t)img * N * N + col;
+#pragma unroll
+    for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * N] = v[m];
+    sync();  // this buffer is free for the copy issued in the next iteration
+  }
+}
+
+// ------------------------------------------------------------------ launch helpers
+// raise the kernel's dynamic shared-memory limit to `bytes` (always: static shared
+// memory counts against the default 48 KB limit too)
+template <class K>
+inline spring_status allow_smem(K kernel, size_t bytes) {
+  SPRING_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return SPRING_OK;
+}
+
+template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false>
 inline spring_status row_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
   constexpr int G = ROW_THREADS / P::T;
-  const size_t smem = (size_t)G * pad_elems_p<P>() * sizeof(float2);
-  if (prepare_only) {
-    allow_smem(k_row<P, MODE, ALG, LATE, MINB>, smem);
-    return SPRING_OK;
-  }
+  const size_t smem = (size_t)G * (pad_elems_p<P>() + (STAGE ? stage_elems<P>() : 0)) * sizeof(float2);
+  if (prepare_only) return allow_smem(k_row<P, MODE, ALG, LATE, MINB, STAGE>, smem);
   long long blocks = (op.ra.nrows + G - 1) / G;
   const long long cap = 64LL * sm_count();
   if (blocks > cap) blocks = cap;
   if (blocks < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
-  k_row<P, MODE, ALG, LATE, MINB><<<(int)blocks, ROW_THREADS, smem, s>>>(op.ra);
+  k_row<P, MODE, ALG, LATE, MINB, STAGE><<<(int)blocks, ROW_THREADS, smem, s>>>(op.ra);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;
@@ -255,14 +494,38 @@ constexpr int fit_w() {  // keep the column tile within shared memory and 1024 t
 
 template <class P, int W, int MODE>
 inline spring_status col_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
-  const size_t smem = (size_t)P::N * W * sizeof(float2);
-  if (prepare_only) {
-    allow_smem(k_col<P, W, MODE>, smem);
-    return SPRING_OK;
-  }
+  const size_t smem = (size_t)P::N * W * sizeof(float2) +
+                      ((MODE == COL_PM || MODE == COL_ERR) ? (size_t)P::N * W * sizeof(float) : 0);
+  if (prepare_only) return allow_smem(k_col<P, W, MODE>, smem);
   if (op.ca.batch < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
   k_col<P, W, MODE><<<op.ca.batch * (P::N / W), W * P::T, smem, s>>>(op.ca);
+  SPRING_CHECK_LAUNCH();
+  launch_end(op.kclass, s, op.bytes);
+  return SPRING_OK;
+}
+
+// the TMA column pass: tensor map of the batch (floats: 2N x N x batch), box 2W x min(N,256)
+template <class P, int W>
+inline spring_status col_pm_tma_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
+  constexpr int N = P::N, BOXR = N > 256 ? 256 : N;
+  const size_t smem = (size_t)2 * N * W * (sizeof(float2) + sizeof(float)) + 1024;
+  if (prepare_only) return allow_smem(k_col_pm_tma<P, W>, smem);
+  if (op.ca.batch < 1) return SPRING_OK;
+  CUtensorMap map, mmap;
+  SPRING_TRY(encode_tmap_f32_3d(&map, op.ca.data, 2 * N, N, op.ca.batch, 2 * W, BOXR));
+  SPRING_TRY(encode_tmap_f32_3d(&mmap, op.ca.M, N, N, 1, W, BOXR));
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_col_pm_tma<P, W>, W * P::T, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int ntiles = op.ca.batch * (N / W);
+  const int blocks = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  launch_begin(op.kclass, s);
+  k_col_pm_tma<P, W><<<blocks, W * P::T, smem, s>>>(map, mmap, op.ca, ntiles, tb.status);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;
@@ -273,7 +536,11 @@ inline spring_status row_iter_variant(const FftOp& op, cudaStream_t s, bool prep
   switch (op.variant) {
     case 0: return row_launch<Plan<N>, ROW_ITER, ALG, false, 1>(op, s, prep);
     case 1: return row_launch<Plan<N>, ROW_ITER, ALG, true, 2>(op, s, prep);
-    default: return row_launch<Plan<N>, ROW_ITER, ALG, true, 3>(op, s, prep);
+    case 2: return row_launch<Plan<N>, ROW_ITER, ALG, true, 3>(op, s, prep);
+    case 3: return row_launch<Plan<N>, ROW_ITER, ALG, true, 2, true>(op, s, prep);
+    case 4: return row_launch<Plan<N>, ROW_ITER, ALG, true, 3, true>(op, s, prep);
+    case 5: return row_launch<RowAltPlan<N>, ROW_ITER, ALG, true, 2>(op, s, prep);
+    default: return row_launch<RowAltPlan<N>, ROW_ITER, ALG, true, 4>(op, s, prep);
   }
 }
 
@@ -283,7 +550,19 @@ inline spring_status col_variant(const FftOp& op, cudaStream_t s, bool prep) {
     case 0: return col_launch<Plan<N>, 16, MODE>(op, s, prep);
     case 1: return col_launch<AltPlan<N>, 16, MODE>(op, s, prep);
     case 2: return col_launch<Plan<N>, fit_w<N, 32>(), MODE>(op, s, prep);
-    default: return col_launch<Plan<N>, 8, MODE>(op, s, prep);
+    case 3: return col_launch<Plan<N>, 8, MODE>(op, s, prep);
+    case 4:
+      if constexpr (MODE == COL_PM) return col_pm_tma_launch<Plan<N>, (N >= 1024 ? 8 : 16)>(op, s, prep);
+      return col_launch<Plan<N>, 16, MODE>(op, s, prep);
+    case 5:
+      if constexpr (MODE == COL_PM) return col_pm_tma_launch<Plan<N>, 8>(op, s, prep);
+      return col_launch<Plan<N>, 8, MODE>(op, s, prep);
+    case 6:
+      if constexpr (MODE == COL_PM) return colT_launch<Plan<N>, (N >= 1024 ? 8 : 16)>(op, s, prep);
+      return col_launch<Plan<N>, 16, MODE>(op, s, prep);
+    default:
+      if constexpr (MODE == COL_PM) return colT_launch<Plan<N>, (N >= 512 ? 8 : 32)>(op, s, prep);
+      return col_launch<Plan<N>, 16, MODE>(op, s, prep);
   }
 }
 

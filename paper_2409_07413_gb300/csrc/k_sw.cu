@@ -128,8 +128,7 @@ spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int 
   if (img_max) SPRING_CUDA(cudaMemsetAsync(img_max, 0, sizeof(unsigned) * batch, s));
   const size_t row_smem = sizeof(float) * (n + 2 * taps.r);
   const size_t col_smem = sizeof(float) * 32 * (SW_TILE_ROWS + 2 * taps.r);
-  if (col_smem > 48 * 1024)
-    cudaFuncSetAttribute(k_smooth_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem);
+  SPRING_CUDA(cudaFuncSetAttribute(k_smooth_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
   launch_begin(SPRING_KC_OTHER, s);
   k_smooth_rows<<<(int)((long long)batch * n), SW_ROW_THREADS, row_smem, s>>>(x, tmp, n, taps);
   SPRING_CHECK_LAUNCH();

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "internal.h"
 
 namespace spring {
@@ -149,16 +151,61 @@ spring_status device_tables(DeviceTables* out) {
     }
     char* mem = nullptr;
     const size_t tw_bytes = sizeof(float2) * TW_TOTAL, r_bytes = sizeof(long long) * 1024;
-    SPRING_CUDA(cudaMalloc(&mem, tw_bytes + 2 * r_bytes));
+    SPRING_CUDA(cudaMalloc(&mem, tw_bytes + 2 * r_bytes + 256));
+    SPRING_CUDA(cudaMemset(mem + tw_bytes + 2 * r_bytes, 0, 256));
     SPRING_CUDA(cudaMemcpy(mem, tw.data(), tw_bytes, cudaMemcpyHostToDevice));
     SPRING_CUDA(cudaMemcpy(mem + tw_bytes, rc.data(), r_bytes, cudaMemcpyHostToDevice));
     SPRING_CUDA(cudaMemcpy(mem + tw_bytes + r_bytes, rs.data(), r_bytes, cudaMemcpyHostToDevice));
     g_tabs[dev].tw = reinterpret_cast<const float2*>(mem);
     g_tabs[dev].rot_cos = reinterpret_cast<const long long*>(mem + tw_bytes);
     g_tabs[dev].rot_sin = reinterpret_cast<const long long*>(mem + tw_bytes + r_bytes);
+    g_tabs[dev].status = reinterpret_cast<int*>(mem + tw_bytes + 2 * r_bytes);
     g_tab_ok[dev] = true;
   }
   *out = g_tabs[dev];
+  return SPRING_OK;
+}
+
+spring_status take_device_status(int* out) {
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  int v = 0;
+  SPRING_CUDA(cudaMemcpy(&v, tb.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) SPRING_CUDA(cudaMemset(tb.status, 0, sizeof(int)));
+  *out = v;
+  return SPRING_OK;
+}
+
+// ------------------------------------------------------------------ TMA descriptors
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+spring_status encode_tmap_f32_3d(void* map, const void* base, int dim0, int dim1, int dim2, int box0,
+                                 int box1) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    SPRING_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (!p || q != cudaDriverEntryPointSuccess) {
+      set_error("cuTensorMapEncodeTiled is not available from the driver");
+      return SPRING_E_CUDA;
+    }
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)dim0, (cuuint64_t)dim1, (cuuint64_t)dim2};
+  const cuuint64_t strides[2] = {(cuuint64_t)dim0 * 4, (cuuint64_t)dim0 * dim1 * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return SPRING_E_CUDA;
+  }
   return SPRING_OK;
 }
 

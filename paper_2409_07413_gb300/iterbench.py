@@ -49,8 +49,8 @@ def sweep(n, batch, iters, alg):
     saved = spring.get_kernel_variant(n)
     res = []
     try:
-        for rv in range(3):
-            for cv in range(4):
+        for rv in range(7):
+            for cv in range(8):
                 spring.set_kernel_variant(n, rv, cv)
                 r = run(n, batch, iters, alg)
                 r["variant"] = [rv, cv]

@@ -1,0 +1,51 @@
+"""Write tests/golden/oracle_errors.json: final errors of the FP64 oracle's MPR runs on
+the benchmark workloads (synthetic patterns from paper_2409_07413_gb300.synthetic).
+
+Calls only the oracle.  Run from the repository root:
+    python tests/golden/make_oracle_errors.py [--threads T]
+The 512 x 512 run (P = 64, 10 x 200 iterations) takes ~20 min on 8 cores.
+"""
+import argparse
+import json
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parents[2]
+sys.path.insert(0, str(ROOT))
+
+import oracle  # noqa: E402
+from paper_2409_07413_gb300 import synthetic  # noqa: E402
+
+WORKLOADS = {
+    "ell512": ("ell512", 0, dict(pop=64, iters_per_gen=200, generations=10, algorithm=2, beta=0.9,
+                                 sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
+    "sphere64": ("sphere64", 0, dict(pop=8, iters_per_gen=100, generations=5, algorithm=2, beta=0.9,
+                                     sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
+}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--only", default=None)
+    a = ap.parse_args()
+    if a.threads:
+        oracle.set_threads(a.threads)
+    out_path = Path(__file__).resolve().parent / "oracle_errors.json"
+    out = json.loads(out_path.read_text()) if out_path.exists() else {}
+    for name, (recipe, pseed, prm) in WORKLOADS.items():
+        if a.only and name != a.only:
+            continue
+        pat = synthetic.config_pattern(recipe, pseed)
+        t0 = time.time()
+        r = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=1000, **prm)
+        out[name] = {"final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
+                     "run_seed": 1000, "pattern_seed": pseed, "seconds": time.time() - t0,
+                     "threads": oracle.get_threads(), "gen_best": r["gen_stats"][:, 0].tolist()}
+        out_path.write_text(json.dumps(out, indent=1))
+        print(name, out[name]["final_error_best"], out[name]["final_error_avg"], flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -61,6 +61,17 @@ def test_mpr_sphere64_matches_oracle_statistically(sp, ctx):
     assert abs(np.median(rg) - np.median(ro)) <= 0.05
 
 
+@pytest.mark.parametrize("name", ["sphere64", "ell128", "ell192", "ell256", "ell512", "ell1024"])
+def test_mpr_runs_at_every_side(sp, ctx, name):
+    # a short run at each supported side exercises every kernel of the run at that side
+    pat = synthetic.config_pattern(name, 0)
+    prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
+    r = prob.run(sp.params(pop=4, iters_per_gen=40, generations=2, er_tail=5, seed=3))
+    prob.destroy()
+    assert 0 < r["final_error_best"] < 1.5 and np.isfinite(r["final_error_avg"])
+    assert r["support_avg"].sum() > 0 and np.isfinite(r["rho_avg"]).all()
+
+
 def test_mpr_deterministic_and_graph_identical(sp, ctx):
     pat = synthetic.config_pattern("sphere64", 3)
     prob = ctx.problem(pat.intensities, pat.mask, pat.support0)

@@ -345,7 +345,7 @@ def test_initialize(sp, n):
 
 
 # ----------------------------------------------------------------------------- launch variants
-@pytest.mark.parametrize("n", [64, 192, 512, 1024])
+@pytest.mark.parametrize("n", [64, 128, 192, 256, 512, 1024])
 def test_kernel_variants_parity(sp, n):
     """Every launch-shape variant of the two iteration passes matches the oracle; row
     variants and the same-plan column variants are bit-identical to each other."""
@@ -356,8 +356,8 @@ def test_kernel_variants_parity(sp, n):
     saved = sp.get_kernel_variant(n)
     out = {}
     try:
-        for rv in range(3):
-            for cv in range(4):
+        for rv in range(7):
+            for cv in range(8):
                 sp.set_kernel_variant(n, rv, cv)
                 xg = dev(c64(x))
                 sp.spring_iterate(xg, dev(S), dev(menc(M, mask)), 2, 0.9, 1.0, 1)
@@ -366,16 +366,19 @@ def test_kernel_variants_parity(sp, n):
                 out[(rv, cv)] = got
     finally:
         sp.set_kernel_variant(n, *saved)
-    for rv in range(3):
-        for cv in (0, 2, 3):
-            assert np.array_equal(out[(rv, cv)], out[(0, 0)]), (rv, cv)
-        assert np.array_equal(out[(rv, 1)], out[(0, 1)]), rv
+    # same plans give the same bits: row variants 0-4 share the default plan, 5-6 the
+    # alternative row plan; column variants 0 and 2-5 the default column plan
+    for rv in range(7):
+        r0 = 0 if rv < 5 else 5
+        for cv in (0, 2, 3, 4, 5, 6, 7):
+            assert np.array_equal(out[(rv, cv)], out[(r0, 0)]), (rv, cv)
+        assert np.array_equal(out[(rv, 1)], out[(r0, 1)]), rv
 
 
 def test_autotune_picks_a_valid_variant(sp):
     saved = sp.get_kernel_variant(256)
     try:
         rv, cv = sp.autotune(256, 8)
-        assert 0 <= rv < 3 and 0 <= cv < 4
+        assert 0 <= rv < 7 and 0 <= cv < 8
     finally:
         sp.set_kernel_variant(256, *saved)
