@@ -141,9 +141,12 @@ size_t spring_footprint_bytes(int n, const spring_params* p);
  * Errors: INVALID (parameters), NOMEM (budget), CUDA, NUMERIC. */
 spring_status spring_mpr_run(spring_problem* prob, const spring_params* p, spring_result* out);
 
-/* Serving: queue a run; requests are admitted while their footprint fits the HBM budget
- * and advance concurrently on the device (continuous batching).  *ticket identifies the
- * request.  The problem must stay alive until the ticket is polled or cancelled. */
+/* Serving: queue a run; requests are admitted in arrival order while their footprint fits
+ * the HBM budget and fewer than SPRING_MAX_ACTIVE (environment, default 2) are running;
+ * running requests advance concurrently on the device, one generation per scheduler turn,
+ * on streams whose priority is higher for smaller requests (continuous batching).
+ * *ticket identifies the request.  The problem must stay alive until the ticket is polled
+ * or cancelled. */
 spring_status spring_submit(spring_ctx* ctx, spring_problem* prob, const spring_params* p,
                             uint64_t* ticket);
 /* Wait up to timeout_us (0 = do not wait, < 0 = wait forever) for a ticket.  SPRING_OK

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -404,6 +405,8 @@ struct spring_ctx {
   int device = 0;
   size_t budget = 0;
   size_t used = 0;
+  int max_active = 2;             // requests advancing concurrently (SPRING_MAX_ACTIVE)
+  int prio_lo = 0, prio_hi = 0;   // stream priority range of the device
   std::mutex mu;
   std::condition_variable cv;       // scheduler wake-ups
   std::condition_variable done_cv;  // ticket completions
@@ -452,7 +455,9 @@ static void scheduler(spring_ctx* c) {
   std::unique_lock<std::mutex> lk(c->mu);
   while (!c->stop) {
     bool progress = false;
-    // admission in arrival order
+    // admission in arrival order, while memory and the concurrency cap allow
+    int running = 0;
+    for (auto& kv : c->tickets) running += kv.second->state == T_RUNNING ? 1 : 0;
     while (!c->queue.empty()) {
       Ticket* t = c->tickets[c->queue.front()].get();
       if (t->cancel) {
@@ -464,11 +469,15 @@ static void scheduler(spring_ctx* c) {
         c->done_cv.notify_all();
         continue;
       }
-      if (!reserve(c, t->footprint)) break;
+      if (running >= c->max_active || !reserve(c, t->footprint)) break;
       c->queue.pop_front();
+      ++running;
       t->t_admit = now_s();
       t->state = T_RUNNING;
-      cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking);
+      // smaller requests get higher stream priority: short jobs do not queue behind long ones
+      const int prio = t->footprint < (64u << 20) ? c->prio_hi
+                       : t->footprint < (512u << 20) ? (c->prio_hi + c->prio_lo) / 2 : c->prio_lo;
+      cudaStreamCreateWithPriority(&t->stream, cudaStreamNonBlocking, prio);
       cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming);
       t->run.reset(new Run());
       spring_status st = t->run->setup(t->prob, t->prm, t->stream);
@@ -599,6 +608,11 @@ spring_status spring_init(int device, size_t hbm_budget_bytes, spring_ctx** out)
   spring_ctx* c = new spring_ctx();
   c->device = device;
   c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+  if (const char* e = std::getenv("SPRING_MAX_ACTIVE")) {
+    const int v = std::atoi(e);
+    if (v > 0) c->max_active = v;
+  }
+  cudaDeviceGetStreamPriorityRange(&c->prio_lo, &c->prio_hi);
   c->worker = std::thread(scheduler, c);
   *out = c;
   return SPRING_OK;
