@@ -77,7 +77,8 @@ typedef struct {
   int init_n_spheres;      /* spheres per initial density N_init (5) */
   float init_gamma;        /* gamma applied to |rho| at initialisation (1) */
   float init_phi_max;      /* sphere phases uniform in [-phi_max, phi_max] (0) */
-  int precision;           /* 0: complex64 state; 1: FP16 storage, FP32 math (0) */
+  int precision;           /* 0: complex64 state; 1: FP16 storage of the state and FFT
+                              intermediate inside iteration blocks, FP32 math (0) */
   int use_graph;           /* 1: capture the run in a CUDA graph before launching (0) */
   uint64_t seed;           /* key of the counter-based generator (0) */
 } spring_params;
@@ -178,6 +179,14 @@ spring_status spring_project_modulus(const void* x, void* out, const float* M, i
  * S: batch supports.  Scratch: one batch x N x N complex64 work buffer. */
 spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batch, int n,
                              int algorithm, float beta, float chi, int n_iter, void* stream);
+
+/* a1-a4 with a choice of storage precision: precision 0 is spring_iterate; precision 1
+ * keeps x and the FFT intermediate as FP16 (half2) between the passes while every
+ * operation runs in FP32 (x is rounded to FP16 once on entry and returned as complex64).
+ * Scratch: batch x N x N x 8 bytes. */
+spring_status spring_iterate_ex(void* x, const uint8_t* S, const float* M, int batch, int n,
+                                int algorithm, float beta, float chi, int n_iter, int precision,
+                                void* stream);
 
 /* a5 smoothing: out = periodic convolution of |x| with the separable normalised Gaussian
  * of width sigma (taps d = -r..r, r = ceil(4 sigma)); sigma = 0 copies |x|.

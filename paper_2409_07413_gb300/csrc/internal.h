@@ -31,6 +31,17 @@ spring_status launch_row_fft_tw(int n, int dir, const float2* in, float2* out, c
 spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
                                 const float2* tw_all, cudaStream_t s);
 
+// FP16 storage of the iteration buffers (precision 1): wh, xh are half2 arrays; x is kept
+// scaled by the device scalar s16 (a power of two from launch_fp16_scale), w by s16 times a
+// power of two near 1/sqrt(N)
+spring_status launch_fp16_scale(int n, const float* M, float* s16, cudaStream_t s);
+spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint8_t* S, long long batch,
+                                float beta, float chi, const float* s16, cudaStream_t s);
+spring_status launch_col_pm16(int n, void* wh, const float* M, int batch, const float* s16, cudaStream_t s);
+spring_status launch_row_init16(int n, const float2* x, void* xh, void* wh, long long batch, const float* s16,
+                                cudaStream_t s);
+spring_status launch_half_to_float(const void* xh, float2* x, long long total, const float* s16, cudaStream_t s);
+
 // kernel-variant autotuning of side n on `batch` images (once per process and side)
 spring_status ensure_tuned(int n, int batch, cudaStream_t s);
 spring_status prepare_fft_kernels(int n);

@@ -183,16 +183,133 @@ spring_status launch_err_finalize(int n, const double* partials, int batch, doub
   return SPRING_OK;
 }
 
+// ------------------------------------------------------------------ FP16 storage (precision 1)
+// s16 = 2^e with sqrt(N) ||M||_2 w16_scale(N) 2^e in [2^12, 2^13).  For any row r and
+// frequency k, |rowFFT(x)_rk| <= sum_j |x_rj| <= sqrt(N) ||x||_2, and the iterates keep
+// ||x||_2 near ||M||_2 (P_M maps onto the measured norm), so every stored FP16 value stays
+// about 8x below its largest finite value; the same power of two keeps small intensity
+// scales away from the subnormal range.  One block; a fixed-order FP64 sum.
+__global__ void k_fp16_scale(const float* __restrict__ M, int n, float* __restrict__ out) {
+  __shared__ double part[256];
+  double acc = 0.0;
+  const long long nn = (long long)n * n;
+  for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
+    const double m = M[i];
+    if (m > 0.0) acc += m * m;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double v = sqrt((double)n) * sqrt(part[0]) * (double)w16_scale(n);
+    int k = 0;
+    float sc = 1.0f;
+    if (v > 0.0 && isfinite(v)) {
+      frexp(v, &k);  // v = f 2^k, f in [0.5, 1)
+      const int e = max(-120, min(120, 13 - k));
+      sc = ldexpf(1.0f, e);
+    }
+    *out = sc;
+  }
+}
+
+spring_status launch_fp16_scale(int n, const float* M, float* s16, cudaStream_t s) {
+  launch_begin(SPRING_KC_OTHER, s);
+  k_fp16_scale<<<1, 256, 0, s>>>(M, n, s16);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)n * n * 4.0);
+  return SPRING_OK;
+}
+
+spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint8_t* S, long long batch,
+                                float beta, float chi, const float* s16, cudaStream_t s) {
+  if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  FftOp op;
+  op.kind = OP_ROW_ITER16;
+  op.alg = alg;
+  op.kclass = SPRING_KC_ROW_ITER;
+  op.ra.in = static_cast<const float2*>(wh);
+  op.ra.out = static_cast<float2*>(wh);
+  op.ra.x = static_cast<float2*>(xh);
+  op.ra.S = S;
+  op.ra.tw = tb.tw + tw_offset(n);
+  op.ra.nrows = batch * n;
+  op.ra.beta = beta;
+  op.ra.chi_on = chi < 1.0f;
+  op.ra.cchi = (float)((chi == 0.5f) ? 0.0 : std::cos((double)chi * 3.14159265358979323846));
+  op.ra.zout = 1;
+  op.ra.s16 = s16;
+  op.bytes = (double)batch * n * n * (4.0 + (alg ? 4.0 : 0.0) + 4.0 + 4.0 + 1.0);
+  return dispatch(n, op, s);
+}
+
+spring_status launch_col_pm16(int n, void* wh, const float* M, int batch, const float* s16, cudaStream_t s) {
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  FftOp op;
+  op.kind = OP_COL_PM16;
+  op.kclass = SPRING_KC_COL_PM;
+  op.ca.data = static_cast<float2*>(wh);
+  op.ca.M = M;
+  op.ca.tw = tb.tw + tw_offset(n);
+  op.ca.batch = batch;
+  op.ca.s16 = s16;
+  op.bytes = (double)batch * n * n * 8.0 + (double)n * n * 4.0;
+  return dispatch(n, op, s);
+}
+
+spring_status launch_row_init16(int n, const float2* x, void* xh, void* wh, long long batch, const float* s16,
+                                cudaStream_t s) {
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  FftOp op;
+  op.kind = OP_ROW_INIT16;
+  op.ra.in = x;
+  op.ra.out = static_cast<float2*>(wh);
+  op.ra.xh = xh;
+  op.ra.tw = tb.tw + tw_offset(n);
+  op.ra.nrows = batch * n;
+  op.ra.s16 = s16;
+  op.bytes = (double)batch * n * n * 16.0;
+  return dispatch(n, op, s);
+}
+
+__global__ void k_half_to_float(const __half2* __restrict__ xh, float2* __restrict__ x, long long total,
+                                const float* __restrict__ s16) {
+  const float isx = 1.0f / __ldg(s16);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = __half22float2(xh[i]);
+    x[i] = make_float2(v.x * isx, v.y * isx);
+  }
+}
+
+spring_status launch_half_to_float(const void* xh, float2* x, long long total, const float* s16, cudaStream_t s) {
+  if (total < 1) return SPRING_OK;
+  launch_begin(SPRING_KC_OTHER, s);
+  k_half_to_float<<<div_up(total, 256) < 16 * sm_count() ? div_up(total, 256) : 16 * sm_count(), 256, 0, s>>>(
+      static_cast<const __half2*>(xh), x, total, s16);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)total * 12.0);
+  return SPRING_OK;
+}
+
 // Raise the dynamic shared-memory limit of every transform kernel of side N once, before
 // any launch (and so before any stream capture).
 spring_status prepare_fft_kernels(int n) {
   if (side_index(n) < 0) return invalid("unsupported pattern side");
   FftOp op;
-  for (int kind = OP_ROW_ITER; kind <= OP_COL_ERR; ++kind) {
+  for (int kind = OP_ROW_ITER; kind <= OP_ROW_INIT16; ++kind) {
     op.kind = kind;
     const int nv = kind == OP_ROW_ITER ? ROW_VARIANTS : kind == OP_COL_PM ? COL_VARIANTS : 1;
+    const bool algs = kind == OP_ROW_ITER || kind == OP_ROW_ITER16;
     for (int v = 0; v < nv; ++v)
-      for (int alg = 0; alg < (kind == OP_ROW_ITER ? 3 : 1); ++alg) {
+      for (int alg = 0; alg < (algs ? 3 : 1); ++alg) {
         op.variant = v;
         op.alg = alg;
         SPRING_TRY(dispatch(n, op, nullptr, true));

@@ -31,15 +31,20 @@
 //           N >= 1024 / 512)
 #pragma once
 
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "fft.cuh"
 #include "internal.h"
 #include "tma.cuh"
 
 namespace spring {
 
-enum { ROW_ITER = 0, ROW_FWD = 1, ROW_INV = 2 };
+enum { ROW_ITER = 0, ROW_FWD = 1, ROW_INV = 2, ROW_INIT16 = 3 };
 enum { COL_PM = 0, COL_FWD = 1, COL_INV = 2, COL_ERR = 3 };
-enum { OP_ROW_ITER = 0, OP_ROW_FWD, OP_ROW_INV, OP_COL_PM, OP_COL_FWD, OP_COL_INV, OP_COL_ERR };
+enum { OP_ROW_ITER = 0, OP_ROW_FWD, OP_ROW_INV, OP_COL_PM, OP_COL_FWD, OP_COL_INV, OP_COL_ERR,
+       OP_ROW_ITER16, OP_COL_PM16, OP_ROW_INIT16 };
 
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_VARIANTS = 7;
@@ -61,6 +66,33 @@ template <> struct RowAltPlan<512> : PlanT<512, 8, 8, 8, 8> {};
 template <> struct RowAltPlan<256> : PlanT<256, 32, 32, 8> {};
 template <> struct RowAltPlan<128> : PlanT<128, 16, 16, 8> {};
 
+// FP16 storage of the iteration buffers (precision 1): x as half2 scaled by the problem's
+// power of two s16 (chosen from ||M||_2 so that every stored value stays well inside the
+// FP16 range, see k_fp16_scale), w as half2 scaled by s16 times a power of two near
+// 1/sqrt(N) that absorbs the growth of the unnormalised row transforms.  Power-of-two
+// scales are exact, so only the FP16 rounding of each stored value remains.  All
+// arithmetic stays FP32.
+__host__ __device__ constexpr float w16_scale(int n) {
+  return n >= 512 ? 1.0f / 32 : n >= 128 ? 1.0f / 16 : 1.0f / 8;
+}
+template <class ST>
+__device__ __forceinline__ float2 ld_st(const ST* p, long long i, float inv) {
+  if constexpr (std::is_same<ST, __half2>::value) {
+    const float2 v = __half22float2(p[i]);
+    return make_float2(v.x * inv, v.y * inv);
+  } else {
+    return p[i];
+  }
+}
+template <class ST>
+__device__ __forceinline__ void st_st(ST* p, long long i, float2 v, float sc) {
+  if constexpr (std::is_same<ST, __half2>::value) {
+    p[i] = __float22half2_rn(make_float2(v.x * sc, v.y * sc));
+  } else {
+    p[i] = v;
+  }
+}
+
 struct RowArgs {
   const float2* in;   // ITER: w (column-pass output); FWD/INV: input rows
   float2* out;        // ITER: w (forward row FFT of x_{n+1}); FWD/INV: output rows
@@ -70,6 +102,8 @@ struct RowArgs {
   long long nrows;
   float beta, cchi, scale;
   int chi_on, zout;
+  void* xh;           // INIT16: FP16 copy of x (out)
+  const float* s16;   // FP16 storage: device scalar s16 (power of two)
 };
 
 struct ColArgs {
@@ -79,6 +113,7 @@ struct ColArgs {
   int batch;
   float scale;        // FWD / INV output scale
   double* partials;   // ERR: [batch][N / ERR_W][2] (sum Xi (|X| - M)^2, sum Xi M^2)
+  const float* s16;   // FP16 storage: device scalar s16 (power of two)
 };
 
 struct FftOp {
@@ -117,7 +152,7 @@ __device__ __forceinline__ float2 update_pixel(int alg, float2 xo, float2 pm, bo
 template <class P>
 __host__ __device__ constexpr int stage_elems() { return P::N + P::N / 8; }
 
-template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false>
+template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false, class ST = float2>
 __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
   constexpr int N = P::N, E = P::E, T = P::T, G = ROW_THREADS / T, SME = pad_elems_p<P>();
   extern __shared__ float2 smem[];
@@ -158,23 +193,29 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
         for (int m = 0; m < E; ++m) a.out[base + m * T] = v[m];
       }
     } else if constexpr (MODE == ROW_ITER) {
+      const ST* win = reinterpret_cast<const ST*>(a.in);
+      ST* wout = reinterpret_cast<ST*>(a.out);
+      ST* xs_ = reinterpret_cast<ST*>(a.x);
+      constexpr bool H = std::is_same<ST, __half2>::value;
+      const float sx = H ? __ldg(a.s16) : 1.0f, ws = H ? w16_scale(N) * sx : 1.0f;
+      const float isx = 1.0f / sx, iws = 1.0f / ws;  // exact: powers of two
       uint8_t s[E];
       float2 xo[E];
       if constexpr (!LATE) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
           s[m] = a.S[base + m * T];
-          if (ALG != 0) xo[m] = a.x[base + m * T];
+          if (ALG != 0) xo[m] = ld_st(xs_, base + m * T, isx);
         }
       }
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = a.in[base + m * T];
+      for (int m = 0; m < E; ++m) v[m] = ld_st(win, base + m * T, iws);
       fft_plan<P, +1, true, 1>(v, sm, t, a.tw, sync);  // m = P_M x_n
       if constexpr (LATE) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
           s[m] = a.S[base + m * T];
-          if (ALG != 0) xo[m] = a.x[base + m * T];
+          if (ALG != 0) xo[m] = ld_st(xs_, base + m * T, isx);
         }
       }
 #pragma unroll
@@ -184,13 +225,27 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
         if (a.chi_on) in_c = in_c && (pm.x >= a.cchi * sqrtf(pm.x * pm.x + pm.y * pm.y));
         const float2 xn = update_pixel(ALG, ALG ? xo[m] : pm, pm, in_c, a.beta);
         v[m] = xn;
-        a.x[base + m * T] = xn;
+        st_st(xs_, base + m * T, xn, sx);
       }
       if (a.zout) {
         fft_plan<P, -1, true, 1>(v, sm, t, a.tw, sync);
 #pragma unroll
-        for (int m = 0; m < E; ++m) a.out[base + m * T] = v[m];
+        for (int m = 0; m < E; ++m) st_st(wout, base + m * T, v[m], ws);
       }
+    } else if constexpr (MODE == ROW_INIT16) {
+      // FP16 copies of x (xh) and of its scaled forward row transform (out)
+      __half2* xh = reinterpret_cast<__half2*>(a.xh);
+      __half2* wout = reinterpret_cast<__half2*>(a.out);
+      const float sx = __ldg(a.s16), isx = 1.0f / sx;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const float2 q = a.in[base + m * T];
+        xh[base + m * T] = __float22half2_rn(make_float2(q.x * sx, q.y * sx));
+        v[m] = ld_st(xh, base + m * T, isx);  // transform exactly what is stored
+      }
+      fft_plan<P, -1, true, 1>(v, sm, t, a.tw, sync);
+#pragma unroll
+      for (int m = 0; m < E; ++m) st_st(wout, base + m * T, v[m], w16_scale(N) * sx);
     } else {
 #pragma unroll
       for (int m = 0; m < E; ++m) {
@@ -205,14 +260,16 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
   }
 }
 
-template <class P, int W, int MODE>
+template <class P, int W, int MODE, class ST = float2>
 __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(ColArgs a) {
   constexpr int N = P::N, E = P::E, T = P::T, STRIPS = N / W;
+  constexpr bool H = std::is_same<ST, __half2>::value;
+  const float ws = H ? w16_scale(N) * __ldg(a.s16) : 1.0f, iws = 1.0f / ws;
   extern __shared__ float2 smem[];
   const int c = threadIdx.x % W, t = threadIdx.x / W;
   const int img = blockIdx.x / STRIPS, strip = blockIdx.x % STRIPS;
   const int col = strip * W + c;
-  float2* base = a.data + (size_t)img * N * N + col;
+  ST* base = reinterpret_cast<ST*>(a.data) + (size_t)img * N * N + col;
   const BlockSync sync;
   // PM / ERR: the strip's modulus values (N x W floats) arrive in shared memory by
   // cp.async while the tile is read and transformed, so no global latency is exposed
@@ -228,7 +285,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
   }
   float2 v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = base[(size_t)(t + m * T) * N];
+  for (int m = 0; m < E; ++m) v[m] = ld_st(base, (long long)(t + m * T) * N, iws);
   if constexpr (MODE == COL_INV) {
     fft_plan<P, +1, false, W>(v, smem + c, t, a.tw, sync);
 #pragma unroll
@@ -256,7 +313,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
     }
     fft_plan<P, +1, false, W>(v, smem + c, t, a.tw, sync);
 #pragma unroll
-    for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * N] = v[m];
+    for (int m = 0; m < E; ++m) st_st(base, (long long)(t + m * T) * N, v[m], ws);
   } else {  // COL_ERR: FP64 accumulation of the Fourier error (Eq. error_calc)
     constexpr float inv_n = 1.0f / N;
     double num = 0.0, den = 0.0;
@@ -471,17 +528,17 @@ inline spring_status allow_smem(K kernel, size_t bytes) {
   return SPRING_OK;
 }
 
-template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false>
+template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false, class ST = float2>
 inline spring_status row_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
   constexpr int G = ROW_THREADS / P::T;
   const size_t smem = (size_t)G * (pad_elems_p<P>() + (STAGE ? stage_elems<P>() : 0)) * sizeof(float2);
-  if (prepare_only) return allow_smem(k_row<P, MODE, ALG, LATE, MINB, STAGE>, smem);
+  if (prepare_only) return allow_smem(k_row<P, MODE, ALG, LATE, MINB, STAGE, ST>, smem);
   long long blocks = (op.ra.nrows + G - 1) / G;
   const long long cap = 64LL * sm_count();
   if (blocks > cap) blocks = cap;
   if (blocks < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
-  k_row<P, MODE, ALG, LATE, MINB, STAGE><<<(int)blocks, ROW_THREADS, smem, s>>>(op.ra);
+  k_row<P, MODE, ALG, LATE, MINB, STAGE, ST><<<(int)blocks, ROW_THREADS, smem, s>>>(op.ra);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;
@@ -492,14 +549,14 @@ constexpr int fit_w() {  // keep the column tile within shared memory and 1024 t
   return ((size_t)N * W * 8 > 200 * 1024 || W * Plan<N>::T > 1024) ? W / 2 : W;
 }
 
-template <class P, int W, int MODE>
+template <class P, int W, int MODE, class ST = float2>
 inline spring_status col_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
   const size_t smem = (size_t)P::N * W * sizeof(float2) +
                       ((MODE == COL_PM || MODE == COL_ERR) ? (size_t)P::N * W * sizeof(float) : 0);
-  if (prepare_only) return allow_smem(k_col<P, W, MODE>, smem);
+  if (prepare_only) return allow_smem(k_col<P, W, MODE, ST>, smem);
   if (op.ca.batch < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
-  k_col<P, W, MODE><<<op.ca.batch * (P::N / W), W * P::T, smem, s>>>(op.ca);
+  k_col<P, W, MODE, ST><<<op.ca.batch * (P::N / W), W * P::T, smem, s>>>(op.ca);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;
@@ -580,6 +637,12 @@ spring_status run_fft_op(const FftOp& op, cudaStream_t s, bool prep) {
     case OP_COL_FWD: return col_launch<Plan<N>, 16, COL_FWD>(op, s, prep);
     case OP_COL_INV: return col_launch<Plan<N>, 16, COL_INV>(op, s, prep);
     case OP_COL_ERR: return col_launch<Plan<N>, ERR_W, COL_ERR>(op, s, prep);
+    case OP_ROW_ITER16:
+      if (op.alg == 0) return row_launch<Plan<N>, ROW_ITER, 0, true, 2, false, __half2>(op, s, prep);
+      if (op.alg == 1) return row_launch<Plan<N>, ROW_ITER, 1, true, 2, false, __half2>(op, s, prep);
+      return row_launch<Plan<N>, ROW_ITER, 2, true, 2, false, __half2>(op, s, prep);
+    case OP_COL_PM16: return col_launch<Plan<N>, 16, COL_PM, __half2>(op, s, prep);
+    case OP_ROW_INIT16: return row_launch<Plan<N>, ROW_INIT16, 0, false, 1>(op, s, prep);
   }
   return invalid("unknown transform operation");
 }

@@ -28,6 +28,7 @@ struct spring_problem {
   spring_ctx* ctx = nullptr;
   int n = 0;
   float* M = nullptr;     // device, N x N, DFT order, negative = not measured
+  float* s16 = nullptr;   // device scalar in M's allocation (M + N x N): FP16 storage scale
   uint8_t* S0 = nullptr;  // device, N x N, initial support (real space)
   std::atomic<int> refs{0};
 };
@@ -59,7 +60,7 @@ static spring_status validate_params(int n, const spring_params& p) {
   if (p.tile_min < 1) return invalid("tile_min must be >= 1");
   if (p.init_n_spheres < 1) return invalid("init_n_spheres must be >= 1");
   if (!(p.init_gamma > 0.f)) return invalid("init_gamma must be > 0");
-  if (p.precision != 0) return invalid("precision 1 (FP16 storage) is not available in this build");
+  if (p.precision != 0 && p.precision != 1) return invalid("precision must be 0 (FP32) or 1 (FP16 storage)");
   return SPRING_OK;
 }
 
@@ -115,6 +116,7 @@ class Run {
   int n = 0, P = 0, B = 0, G = 0, R = 0, last = 0;
   spring_params prm{};
   const float* M = nullptr;
+  const float* s16 = nullptr;  // FP16 storage scale of the problem (device scalar)
   const uint8_t* S0 = nullptr;
   cudaStream_t s = nullptr;
   char* mem = nullptr;
@@ -133,6 +135,8 @@ class Run {
   int* status = nullptr;
   void *peaks = nullptr, *init_sc = nullptr;
   bool z_valid = false;
+  // precision 1: the iteration blocks keep x and w as half2 inside the w buffer
+  bool fp16 = false, z16_valid = false, x16_newer = false;
 
   ~Run() { release(); }
 
@@ -152,8 +156,10 @@ class Run {
     R = p.iters_per_gen / p.sw_period;
     last = p.iters_per_gen - (R - 1) * p.sw_period;
     M = prob->M;
+    s16 = prob->s16;
     S0 = prob->S0;
     s = stream;
+    fp16 = p.precision == 1;
     L = make_layout(n, p);
     SPRING_TRY(prepare_fft_kernels(n));
     SPRING_TRY(ensure_tuned(n, B, s));
@@ -196,6 +202,17 @@ class Run {
   }
 
   size_t nn() const { return (size_t)n * n; }
+  void* wh() { return w; }                                                    // B x nn half2
+  void* xh() { return reinterpret_cast<char*>(w) + (size_t)B * nn() * 4; }  // B x nn half2
+
+  // bring the FP32 state up to date with the FP16 iteration state
+  spring_status sync_x() {
+    if (x16_newer) {
+      SPRING_TRY(launch_half_to_float(xh(), x, (long long)B * nn(), s16, s));
+      x16_newer = false;
+    }
+    return SPRING_OK;
+  }
   float2* x_pop() { return x; }
   float2* x_new() { return x + P * nn(); }
   float2* w_pop() { return w; }
@@ -213,7 +230,7 @@ class Run {
     SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
     SPRING_TRY(launch_normalise(n, w_pop(), M, P, x_pop(), part_norm, s));
     SPRING_TRY(launch_broadcast_support(n, S0, P, S_pop(), s));
-    z_valid = false;
+    z_valid = z16_valid = x16_newer = false;
     return SPRING_OK;
   }
 
@@ -236,12 +253,24 @@ class Run {
                                     prm.tile_min, prm.tile_max, x_new(), s));
     SPRING_TRY(fft2_unitary(n, +1, x_new(), x_new(), nullptr, P, s));
     SPRING_TRY(launch_crossover_support(n, S_pop(), abc, info, P, S_new(), s));
-    z_valid = false;
+    z_valid = z16_valid = false;
     return SPRING_OK;
   }
 
   spring_status iterations(int alg, int k) {
     if (k <= 0) return SPRING_OK;
+    if (fp16) {
+      if (!z16_valid) {
+        SPRING_TRY(launch_row_init16(n, x, xh(), wh(), B, s16, s));
+        z16_valid = true;
+      }
+      for (int it = 0; it < k; ++it) {
+        SPRING_TRY(launch_col_pm16(n, wh(), M, B, s16, s));
+        SPRING_TRY(launch_row_iter16(n, alg, wh(), xh(), S, B, prm.beta, prm.chi, s16, s));
+      }
+      x16_newer = true;
+      return SPRING_OK;
+    }
     if (!z_valid) {
       SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, B, 1.0f, s));
       z_valid = true;
@@ -254,20 +283,23 @@ class Run {
   }
 
   spring_status shrinkwrap(float sigma, float tau) {
+    SPRING_TRY(sync_x());
     SPRING_TRY(launch_smooth(n, x, sm0, sm1, B, sigma, imgmax, s));
     return launch_threshold(n, sm1, imgmax, tau, S, B, s);
   }
 
   spring_status shrinkwrap_area(float sigma, const int64_t* a) {
+    SPRING_TRY(sync_x());
     SPRING_TRY(launch_smooth(n, x, sm0, sm1, B, sigma, nullptr, s));
     return launch_select_area(n, sm1, a, 0, S, B, s);
   }
 
   spring_status errors() {
+    SPRING_TRY(sync_x());
     SPRING_TRY(launch_row_fft(n, -1, x, w, S, B, 1.0f, s));
     SPRING_TRY(launch_col_err(n, w, M, B, part_err, s));
     SPRING_TRY(launch_err_finalize(n, part_err, B, err, status, s));
-    z_valid = false;
+    z_valid = z16_valid = false;  // w served as scratch
     return SPRING_OK;
   }
 
@@ -288,7 +320,7 @@ class Run {
         SPRING_TRY(shrinkwrap(sigma, tau));
       }
     }
-    return SPRING_OK;
+    return sync_x();
   }
 
   spring_status generation(int g) {
@@ -643,7 +675,8 @@ static spring_status problem_alloc(spring_ctx* ctx, int n, spring_problem** out,
   pr->ctx = ctx;
   pr->n = n;
   const size_t nn = (size_t)n * n;
-  SPRING_CUDA(cudaMalloc(&pr->M, sizeof(float) * nn));
+  SPRING_CUDA(cudaMalloc(&pr->M, sizeof(float) * (nn + 64)));
+  pr->s16 = pr->M + nn;
   cudaError_t e = cudaMalloc(&pr->S0, nn);
   if (e != cudaSuccess) {
     cudaFree(pr->M);
@@ -657,6 +690,7 @@ static spring_status problem_fill(spring_problem* pr, const float* d_I, const ui
                                   const uint8_t* d_S0, cudaStream_t s) {
   const int n = pr->n;
   SPRING_TRY(launch_make_modulus(n, d_I, d_mask, pr->M, s));
+  SPRING_TRY(launch_fp16_scale(n, pr->M, pr->s16, s));
   SPRING_CUDA(cudaMemcpyAsync(pr->S0, d_S0, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
   return SPRING_OK;
 }

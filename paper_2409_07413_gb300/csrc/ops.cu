@@ -342,6 +342,33 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
   return SPRING_OK;
 }
 
+spring_status spring_iterate_ex(void* x, const uint8_t* S, const float* M, int batch, int n,
+                                int algorithm, float beta, float chi, int n_iter, int precision,
+                                void* stream) {
+  if (precision == 0) return spring_iterate(x, S, M, batch, n, algorithm, beta, chi, n_iter, stream);
+  if (precision != 1) return invalid("precision must be 0 or 1");
+  SPRING_TRY(check_n(n, batch));
+  if (algorithm < 0 || algorithm > 2) return invalid("algorithm must be 0, 1 or 2");
+  if (n_iter < 0) return invalid("negative iteration count");
+  if (batch == 0 || n_iter == 0) return SPRING_OK;
+  if (!x || !S || !M) return invalid("null pointer");
+  cudaStream_t s = ST(stream);
+  const long long total = (long long)batch * n * n;
+  Scratch w;
+  SPRING_TRY(w.alloc(sizeof(float2) * total + 256, s));
+  void* wh = w.p;
+  void* xh = static_cast<char*>(w.p) + total * 4;
+  float* s16 = reinterpret_cast<float*>(static_cast<char*>(w.p) + total * 8);
+  float2* xs = static_cast<float2*>(x);
+  SPRING_TRY(launch_fp16_scale(n, M, s16, s));
+  SPRING_TRY(launch_row_init16(n, xs, xh, wh, batch, s16, s));
+  for (int it = 0; it < n_iter; ++it) {
+    SPRING_TRY(launch_col_pm16(n, wh, M, batch, s16, s));
+    SPRING_TRY(launch_row_iter16(n, algorithm, wh, xh, S, batch, beta, chi, s16, s));
+  }
+  return launch_half_to_float(xh, xs, total, s16, s);
+}
+
 spring_status spring_smooth(const void* x, float* out, int batch, int n, float sigma, void* stream) {
   SPRING_TRY(check_n(n, batch));
   if (batch == 0) return SPRING_OK;

@@ -1,7 +1,7 @@
 """Micro-benchmark of the per-iteration passes (row pass with the fused update, column
 pass with the fused modulus projection) on random state.
 
-    python -m paper_2409_07413_gb300.iterbench --n 512 --batch 128 --iters 50 --alg 2
+    python -m paper_2409_07413_gb300.iterbench --n 512 --batch 128 --iters 50 --alg 2 [--precision 1]
 
 Prints one JSON line per side with each pass's average CUDA-event time, algorithmic bytes
 and GB/s (events are recorded on the launching stream around every launch).
@@ -14,7 +14,7 @@ import json
 import numpy as np
 
 
-def run(n, batch, iters, alg, warm=3):
+def run(n, batch, iters, alg, warm=3, precision=0):
     import torch
 
     from paper_2409_07413_gb300 import spring
@@ -24,14 +24,14 @@ def run(n, batch, iters, alg, warm=3):
     S = (torch.rand((batch, n, n), device="cuda", generator=g) < 0.25).to(torch.uint8)
     M = torch.rand((n, n), device="cuda", generator=g) + 0.1
     M[torch.rand((n, n), device="cuda", generator=g) < 0.05] = -1.0
-    spring.spring_iterate(x, S, M, alg, 0.9, 0.5, warm)
+    spring.spring_iterate_ex(x, S, M, alg, 0.9, 0.5, warm, precision)
     torch.cuda.synchronize()
     spring.stats_reset()
     spring.stats_enable_timing(True)
-    spring.spring_iterate(x, S, M, alg, 0.9, 0.5, iters)
+    spring.spring_iterate_ex(x, S, M, alg, 0.9, 0.5, iters, precision)
     torch.cuda.synchronize()
     spring.stats_enable_timing(False)
-    out = {"n": n, "batch": batch, "iters": iters, "alg": alg}
+    out = {"n": n, "batch": batch, "iters": iters, "alg": alg, "precision": precision}
     for name, kc in (("row_iter", spring.KC_ROW_ITER), ("col_pm", spring.KC_COL_PM)):
         st = spring.stats_get(kc)
         ms = st.total_ms / max(1, st.timed)
@@ -66,6 +66,7 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--alg", type=int, default=2)
+    ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: FP16 storage")
     ap.add_argument("--sweep", action="store_true", help="time every launch variant")
     a = ap.parse_args()
     for n in a.n:
@@ -76,7 +77,7 @@ def main():
                                   "row_GBps": r["row_iter"]["GBps"], "col_ms": r["col_pm"]["avg_ms"],
                                   "col_GBps": r["col_pm"]["GBps"]}), flush=True)
         else:
-            print(json.dumps(run(n, b, a.iters, a.alg)), flush=True)
+            print(json.dumps(run(n, b, a.iters, a.alg, precision=a.precision)), flush=True)
 
 
 if __name__ == "__main__":

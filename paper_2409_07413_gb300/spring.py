@@ -68,6 +68,7 @@ _SIGS = {
     "spring_fft2": (_i, [_vp, _i, _i, _i, _vp]),
     "spring_project_modulus": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "spring_iterate": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _f, _i, _vp]),
+    "spring_iterate_ex": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _f, _i, _i, _vp]),
     "spring_smooth": (_i, [_vp, _vp, _i, _i, _f, _vp]),
     "spring_update_support": (_i, [_vp, _vp, _i, _i, _f, _f, _vp]),
     "spring_update_support_size": (_i, [_vp, _vp, _i, _i, _f, _vp, _vp]),
@@ -204,6 +205,17 @@ def spring_iterate(x, S, M, algorithm, beta, chi, n_iter):
     b, n = _batch_n(x)
     _call("spring_iterate", _ptr(x), _ptr(S), _ptr(M), b, n, int(algorithm), float(beta),
           float(chi), int(n_iter), _stream())
+    return x
+
+
+def spring_iterate_ex(x, S, M, algorithm, beta, chi, n_iter, precision):
+    import torch
+    _need(x, torch.complex64, "x")
+    _need(S, torch.uint8, "S")
+    _need(M, torch.float32, "M")
+    b, n = _batch_n(x)
+    _call("spring_iterate_ex", _ptr(x), _ptr(S), _ptr(M), b, n, int(algorithm), float(beta),
+          float(chi), int(n_iter), int(precision), _stream())
     return x
 
 
