@@ -52,6 +52,7 @@ class OrcParams(C.Structure):
         ("tile_min", C.c_int), ("tile_max", C.c_int), ("init_n_spheres", C.c_int),
         ("init_gamma", C.c_double), ("init_phi_max", C.c_double),
         ("seed", C.c_uint64),
+        ("ub_eta", C.c_double), ("ub_max_missing", C.c_double), ("ub_max_saturated", C.c_double),
     ]
 
 
@@ -77,6 +78,11 @@ def lib():
             "orc_fft2": (C.c_int, [_dp, C.c_int, C.c_int, C.c_int]),
             "orc_dft2_naive": (None, [_dp, _dp, C.c_int, C.c_int]),
             "orc_project_modulus": (C.c_int, [_dp, _dp, _dp, _u8p, C.c_int, C.c_int]),
+            "orc_project_modulus_ub": (C.c_int, [_dp, _dp, _dp, _u8p, _dp, C.c_int, C.c_int]),
+            "orc_upper_bounds": (None, [_dp, _u8p, _u8p, C.c_int, C.c_double, C.c_double,
+                                        C.c_double, _dp]),
+            "orc_iterate_ub": (C.c_int, [_dp, _u8p, _dp, _u8p, _dp, C.c_int, C.c_int, C.c_int,
+                                         C.c_double, C.c_double, C.c_int]),
             "orc_iterate": (C.c_int, [_dp, _u8p, _dp, _u8p, C.c_int, C.c_int, C.c_int,
                                       C.c_double, C.c_double, C.c_int]),
             "orc_project_support": (None, [_dp, _u8p, C.c_int]),
@@ -101,6 +107,8 @@ def lib():
                                       C.c_double, C.c_double, _dp]),
             "orc_mpr_run": (C.c_int, [_dp, _u8p, _u8p, C.c_int, C.POINTER(OrcParams),
                                       C.POINTER(OrcResult)]),
+            "orc_mpr_run_sat": (C.c_int, [_dp, _u8p, _u8p, _u8p, C.c_int, C.POINTER(OrcParams),
+                                          C.POINTER(OrcResult)]),
             "orc_improve": (C.c_int, [_dp, _u8p, _dp, _u8p, C.c_int, C.c_int,
                                       C.POINTER(OrcParams), C.c_double, C.c_double, C.c_long,
                                       C.c_long, _dp]),
@@ -176,15 +184,44 @@ def project_modulus(x, M, mask):
     return out[0] if sq else out
 
 
-def iterate(x, S, M, mask, alg, beta, chi, n_iter):
-    """n_iter ER/HIO/RAAR iterations (alg 0/1/2) on each image."""
+def project_modulus_ub(x, M, mask, U):
+    """P_M x with upper bounds on the missing moduli (Eq. pm_bounds); U in DFT order,
+    negative where no bound applies."""
+    x, sq = _batched(x)
+    out = np.empty_like(x)
+    M, mask, U = _f64(M), _u8(mask), _f64(U)
+    lib().orc_project_modulus_ub(_pd(x), _pd(out), _pd(M), _pu8(mask), _pd(U), x.shape[0], x.shape[1])
+    return out[0] if sq else out
+
+
+def upper_bounds(I_centred, mask_centred, saturated=None, eta=1.5, max_missing=0.2, max_saturated=0.05):
+    """Per-pixel amplitude bounds sqrt(mu + eta sigma) of the missing, unsaturated pixels
+    (Eqs. avgint, stdint, upperbound), detector-centred; -1 where no bound applies."""
+    I = _f64(I_centred)
+    mask = _u8(mask_centred)
+    n = I.shape[0]
+    sat = None if saturated is None else _u8(saturated)
+    U = np.empty((n, n), np.float64)
+    lib().orc_upper_bounds(_pd(I), _pu8(mask), None if sat is None else _pu8(sat), n, float(eta),
+                           float(max_missing), float(max_saturated), _pd(U))
+    return U
+
+
+def iterate(x, S, M, mask, alg, beta, chi, n_iter, U=None):
+    """n_iter ER/HIO/RAAR iterations (alg 0/1/2) on each image; with U (DFT order,
+    negative = no bound) the projection is Eq. pm_bounds."""
     x, sq = _batched(x)
     S = _u8(S)
     if S.ndim == 2:
         S = np.broadcast_to(S, x.shape).copy()
     M, mask = _f64(M), _u8(mask)
-    rc = lib().orc_iterate(_pd(x), _pu8(S), _pd(M), _pu8(mask), x.shape[0], x.shape[1],
-                           int(alg), float(beta), float(chi), int(n_iter))
+    if U is None:
+        rc = lib().orc_iterate(_pd(x), _pu8(S), _pd(M), _pu8(mask), x.shape[0], x.shape[1],
+                               int(alg), float(beta), float(chi), int(n_iter))
+    else:
+        U = _f64(U)
+        rc = lib().orc_iterate_ub(_pd(x), _pu8(S), _pd(M), _pu8(mask), _pd(U), x.shape[0],
+                                  x.shape[1], int(alg), float(beta), float(chi), int(n_iter))
     if rc:
         raise ValueError("invalid arguments")
     return x[0] if sq else x
@@ -328,7 +365,8 @@ def initialize(seed, S0, I, mask, P, n_spheres=5, gamma=1.0, phi_max=0.0):
 DEFAULTS = dict(pop=8, iters_per_gen=100, generations=5, algorithm=2, beta=0.9,
                 sw_sigma=1.5, sw_threshold=0.2, sw_sigma_end=None, sw_threshold_end=None,
                 sw_period=20, er_tail=10, chi=0.5, cw=0.4, cp=0.6, tile_min=4, tile_max=0,
-                init_n_spheres=5, init_gamma=1.0, init_phi_max=0.0, seed=0)
+                init_n_spheres=5, init_gamma=1.0, init_phi_max=0.0, seed=0,
+                ub_eta=0.0, ub_max_missing=0.2, ub_max_saturated=0.05)
 
 
 def make_params(**kw) -> OrcParams:
@@ -354,7 +392,7 @@ def improve(x, S, M, mask, params: OrcParams, sigma, tau, a_best, a_eval):
     return x, S, err
 
 
-def mpr_run(I_centred, mask_centred, S0, keep_population=False, **kw):
+def mpr_run(I_centred, mask_centred, S0, keep_population=False, saturated=None, **kw):
     """Full MPR run (Alg. mpr).  Returns a dict with rho_avg, rho_best, support_avg,
     final errors, per-generation stats and (optionally) the final population."""
     I, mask, S0 = _f64(I_centred), _u8(mask_centred), _u8(S0)
@@ -372,7 +410,9 @@ def mpr_run(I_centred, mask_centred, S0, keep_population=False, **kw):
         pS = np.empty((P, n, n), np.uint8)
         pe = np.empty(P, np.float64)
         res.pop_x, res.pop_S, res.pop_err = _pd(px), _pu8(pS), _pd(pe)
-    rc = lib().orc_mpr_run(_pd(I), _pu8(mask), _pu8(S0), n, C.byref(pr), C.byref(res))
+    sat = None if saturated is None else _u8(saturated)
+    rc = lib().orc_mpr_run_sat(_pd(I), _pu8(mask), None if sat is None else _pu8(sat), _pu8(S0), n,
+                               C.byref(pr), C.byref(res))
     if rc:
         raise ValueError("invalid MPR parameters")
     out = dict(rho_avg=avg, rho_best=best, support_avg=Sa, gen_stats=stats,

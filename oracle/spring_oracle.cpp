@@ -205,21 +205,27 @@ extern "C" void orc_dft2_naive(const double* in, double* out, int n, int inverse
 // ------------------------------------------------------------------------------------
 
 // Eq. pm_full on a spectrum: where the mask is 1, replace the modulus by M (a zero
-// modulus takes phase 0); elsewhere leave the value free.
-static void modulus_constraint(cd* X, const double* M, const uint8_t* mask, int n) {
+// modulus takes phase 0); elsewhere leave the value free.  With upper bounds U (may be
+// null; U < 0 = no bound at that pixel) this is Eq. pm_bounds: where the mask is 0 and a
+// bound exists, a modulus above U is brought down to U with the phase kept.
+static void modulus_constraint(cd* X, const double* M, const uint8_t* mask, const double* U, int n) {
   for (size_t i = 0; i < (size_t)n * n; i++) {
-    if (!mask[i]) continue;
     double a = std::abs(X[i]);
-    X[i] = (a > 0.0) ? X[i] * (M[i] / a) : cd(M[i], 0.0);
+    if (mask[i]) {
+      X[i] = (a > 0.0) ? X[i] * (M[i] / a) : cd(M[i], 0.0);
+    } else if (U && U[i] >= 0.0 && a > U[i]) {
+      X[i] = X[i] * (U[i] / a);
+    }
   }
 }
 
-// P_M x = F^-1[ masked modulus constraint (F x) ]   (Eq. pm with Eq. pm_full)
-static void project_modulus(const cd* x, cd* out, const double* M, const uint8_t* mask, int n) {
+// P_M x = F^-1[ masked modulus constraint (F x) ]   (Eq. pm with Eq. pm_full / pm_bounds)
+static void project_modulus(const cd* x, cd* out, const double* M, const uint8_t* mask,
+                            const double* U, int n) {
   size_t nn = (size_t)n * n;
   std::copy(x, x + nn, out);
   fft2_inplace(out, n, 0);
-  modulus_constraint(out, M, mask, n);
+  modulus_constraint(out, M, mask, U, n);
   fft2_inplace(out, n, 1);
 }
 
@@ -228,9 +234,80 @@ extern "C" int orc_project_modulus(const double* x, double* out, const double* M
   if (!valid_side(n)) return 1;
   size_t nn = (size_t)n * n;
   parallel_for(batch, [&](int b) {
-    project_modulus(as_cd(x) + b * nn, as_cd(out) + b * nn, M, mask, n);
+    project_modulus(as_cd(x) + b * nn, as_cd(out) + b * nn, M, mask, nullptr, n);
   });
   return 0;
+}
+
+// P_M with the upper bounds U of Eq. pm_bounds (DFT order, U < 0 = no bound).
+extern "C" int orc_project_modulus_ub(const double* x, double* out, const double* M,
+                                      const uint8_t* mask, const double* U, int batch, int n) {
+  if (!valid_side(n)) return 1;
+  size_t nn = (size_t)n * n;
+  parallel_for(batch, [&](int b) {
+    project_modulus(as_cd(x) + b * nn, as_cd(out) + b * nn, M, mask, U, n);
+  });
+  return 0;
+}
+
+// ------------------------------------------------------------------------------------
+// Upper bounds for missing intensities (App. "Constraining intensities at large
+// scattering angles", Eqs. avgint, stdint, upperbound).  Pixels are grouped by their
+// distance q from the detector centre (pixel (N/2, N/2) of the centred array) rounded to
+// the nearest integer.  Over the measured pixels of each ring:
+//   mu(q) = mean I,  sigma(q)^2 = mean (I - mu)^2  (= mean I^2 - mu^2 of Eq. stdint,
+//   taken as the mean squared deviation so that no cancellation occurs),
+//   U_I(q) = mu + eta sigma.
+// The bound is used at a missing pixel only if it is not saturated, at most max_missing of
+// the ring's pixels are missing, and at most max_saturated of them are saturated.  The
+// projector compares moduli, so the per-pixel bound is the amplitude sqrt(U_I(q)).
+// Input and output are detector-centred; U = -1 where no bound applies.
+// ------------------------------------------------------------------------------------
+extern "C" void orc_upper_bounds(const double* I, const uint8_t* mask, const uint8_t* sat, int n,
+                                 double eta, double max_missing, double max_saturated, double* U) {
+  const int h = n / 2;
+  int nb = (int)std::lround(std::sqrt(2.0 * h * h)) + 1;
+  std::vector<double> s1(nb, 0.0), s2(nb, 0.0), mu(nb, 0.0);
+  std::vector<long> cnt(nb, 0), meas(nb, 0), satc(nb, 0);
+  auto ring = [&](int i, int j) {
+    long dy = i - h, dx = j - h;
+    return (int)std::lround(std::sqrt((double)(dy * dy + dx * dx)));
+  };
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      size_t k = (size_t)i * n + j;
+      int q = ring(i, j);
+      cnt[q]++;
+      if (sat && sat[k]) satc[q]++;
+      if (mask[k]) {
+        meas[q]++;
+        s1[q] += I[k];
+      }
+    }
+  for (int q = 0; q < nb; q++) mu[q] = meas[q] ? s1[q] / meas[q] : 0.0;
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      size_t k = (size_t)i * n + j;
+      if (mask[k]) {
+        int q = ring(i, j);
+        s2[q] += (I[k] - mu[q]) * (I[k] - mu[q]);
+      }
+    }
+  std::vector<double> Uq(nb, -1.0);
+  for (int q = 0; q < nb; q++) {
+    if (cnt[q] == 0 || meas[q] == 0) continue;
+    double missing = (double)(cnt[q] - meas[q]);
+    if (missing > max_missing * (double)cnt[q]) continue;
+    if ((double)satc[q] > max_saturated * (double)cnt[q]) continue;
+    double sd = std::sqrt(s2[q] / meas[q]);
+    Uq[q] = std::sqrt(std::max(0.0, mu[q] + eta * sd));
+  }
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      size_t k = (size_t)i * n + j;
+      bool free_px = !mask[k] && !(sat && sat[k]);
+      U[k] = free_px ? Uq[ring(i, j)] : -1.0;
+    }
 }
 
 // cos(chi*pi) with the positivity case chi = 1/2 made exact (the half-plane Re >= 0).
@@ -255,13 +332,13 @@ static inline cd update_pixel(int alg, cd x, cd m, bool in_c, double beta) {
   }
 }
 
-static void iterate_one(cd* x, const uint8_t* S, const double* M, const uint8_t* mask, int n,
-                        int alg, double beta, double chi, int n_iter) {
+static void iterate_one(cd* x, const uint8_t* S, const double* M, const uint8_t* mask,
+                        const double* U, int n, int alg, double beta, double chi, int n_iter) {
   size_t nn = (size_t)n * n;
   std::vector<cd> m(nn);
   double cchi = chi_cos(chi);
   for (int it = 0; it < n_iter; it++) {
-    project_modulus(x, m.data(), M, mask, n);
+    project_modulus(x, m.data(), M, mask, U, n);
     for (size_t i = 0; i < nn; i++)
       x[i] = update_pixel(alg, x[i], m[i], in_constraint(S[i], m[i], chi, cchi), beta);
   }
@@ -273,7 +350,19 @@ extern "C" int orc_iterate(double* x, const uint8_t* S, const double* M, const u
   if (!valid_side(n) || alg < 0 || alg > 2) return 1;
   size_t nn = (size_t)n * n;
   parallel_for(batch, [&](int b) {
-    iterate_one(as_cd(x) + b * nn, S + b * nn, M, mask, n, alg, beta, chi, n_iter);
+    iterate_one(as_cd(x) + b * nn, S + b * nn, M, mask, nullptr, n, alg, beta, chi, n_iter);
+  });
+  return 0;
+}
+
+// the same with the upper bounds U of Eq. pm_bounds (DFT order, U < 0 = no bound)
+extern "C" int orc_iterate_ub(double* x, const uint8_t* S, const double* M, const uint8_t* mask,
+                              const double* U, int batch, int n, int alg, double beta, double chi,
+                              int n_iter) {
+  if (!valid_side(n) || alg < 0 || alg > 2) return 1;
+  size_t nn = (size_t)n * n;
+  parallel_for(batch, [&](int b) {
+    iterate_one(as_cd(x) + b * nn, S + b * nn, M, mask, U, n, alg, beta, chi, n_iter);
   });
   return 0;
 }
@@ -847,6 +936,7 @@ struct orc_params {
   int tile_min, tile_max, init_n_spheres;
   double init_gamma, init_phi_max;
   uint64_t seed;
+  double ub_eta, ub_max_missing, ub_max_saturated;  // upper bounds (eta <= 0: off)
 };
 
 struct orc_result {
@@ -866,21 +956,21 @@ static long area(const uint8_t* S, size_t nn) {
   return a;
 }
 
-static void improve_one(cd* x, uint8_t* S, const double* M, const uint8_t* mask, int n,
-                        const orc_params& pr, double sigma, double tau, long a_best, long a_eval,
+static void improve_one(cd* x, uint8_t* S, const double* M, const uint8_t* mask, const double* U,
+                        int n, const orc_params& pr, double sigma, double tau, long a_best, long a_eval,
                         double* err) {
   int K = pr.sw_period, R = pr.iters_per_gen / K;
   int last = pr.iters_per_gen - (R - 1) * K;
   int alg = pr.algorithm;
   for (int blk = 1; blk <= R - 2; blk++) {
-    iterate_one(x, S, M, mask, n, alg, pr.beta, pr.chi, K);
+    iterate_one(x, S, M, mask, U, n, alg, pr.beta, pr.chi, K);
     update_support(x, S, n, sigma, tau);
   }
-  iterate_one(x, S, M, mask, n, alg, pr.beta, pr.chi, K);
+  iterate_one(x, S, M, mask, U, n, alg, pr.beta, pr.chi, K);
   update_support_size(x, S, n, sigma, a_best);
-  iterate_one(x, S, M, mask, n, alg, pr.beta, pr.chi, last - pr.er_tail);
+  iterate_one(x, S, M, mask, U, n, alg, pr.beta, pr.chi, last - pr.er_tail);
   update_support_size(x, S, n, sigma, a_eval);
-  iterate_one(x, S, M, mask, n, 0, pr.beta, pr.chi, pr.er_tail);
+  iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, pr.er_tail);
   *err = fourier_error(x, S, M, mask, n);
   update_support(x, S, n, sigma, tau);
 }
@@ -897,8 +987,9 @@ static void ifftshift2(const void* src, void* dst, int n, size_t esz) {
 }
 
 // Returns 0 on success, 1 on invalid parameters.  I, mask: detector-centred; S0 real space.
-extern "C" int orc_mpr_run(const double* I_c, const uint8_t* mask_c, const uint8_t* S0, int n,
-                           const orc_params* prm, orc_result* res) {
+// sat_c: detector-centred saturation map (may be null), used by the upper bounds only
+extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const uint8_t* sat_c,
+                               const uint8_t* S0, int n, const orc_params* prm, orc_result* res) {
   const orc_params& pr = *prm;
   if (!valid_side(n) || pr.pop < 4 || pr.generations < 1 || pr.sw_period < 1) return 1;
   int R = pr.iters_per_gen / pr.sw_period;
@@ -912,6 +1003,16 @@ extern "C" int orc_mpr_run(const double* I_c, const uint8_t* mask_c, const uint8
   ifftshift2(I_c, I.data(), n, sizeof(double));
   ifftshift2(mask_c, mask.data(), n, 1);
   for (size_t i = 0; i < nn; i++) M[i] = std::sqrt(std::max(0.0, I[i]));
+  // upper bounds of the missing intensities (Eq. pm_bounds), in DFT order
+  std::vector<double> U;
+  const double* Up = nullptr;
+  if (pr.ub_eta > 0.0) {
+    std::vector<double> Uc(nn);
+    orc_upper_bounds(I_c, mask_c, sat_c, n, pr.ub_eta, pr.ub_max_missing, pr.ub_max_saturated, Uc.data());
+    U.resize(nn);
+    ifftshift2(Uc.data(), U.data(), n, sizeof(double));
+    Up = U.data();
+  }
 
   std::vector<cd> px(P * nn), nx(P * nn);
   std::vector<uint8_t> pS(P * nn), nS(P * nn);
@@ -948,7 +1049,7 @@ extern "C" int orc_mpr_run(const double* I_c, const uint8_t* mask_c, const uint8
       cd* x = old ? &px[p * nn] : &nx[p * nn];
       uint8_t* S = old ? &pS[p * nn] : &nS[p * nn];
       double* e = old ? &pe[p] : &ne[p];
-      improve_one(x, S, M.data(), mask.data(), n, pr, sigma, tau, a_best, a_eval, e);
+      improve_one(x, S, M.data(), mask.data(), Up, n, pr, sigma, tau, a_best, a_eval, e);
     });
     // Select
     int repl = 0;
@@ -996,6 +1097,11 @@ extern "C" int orc_mpr_run(const double* I_c, const uint8_t* mask_c, const uint8
   return 0;
 }
 
+extern "C" int orc_mpr_run(const double* I_c, const uint8_t* mask_c, const uint8_t* S0, int n,
+                           const orc_params* prm, orc_result* res) {
+  return orc_mpr_run_sat(I_c, mask_c, nullptr, S0, n, prm, res);
+}
+
 // Improve on an explicit batch (used by the CPU-baseline timing and by parity tests of
 // the whole self-improvement step).  x, S: batch images; err: batch errors out.
 extern "C" int orc_improve(double* x, uint8_t* S, const double* M, const uint8_t* mask, int batch,
@@ -1009,7 +1115,8 @@ extern "C" int orc_improve(double* x, uint8_t* S, const double* M, const uint8_t
   if (pr.er_tail < 0 || pr.er_tail > last) return 1;
   size_t nn = (size_t)n * n;
   parallel_for(batch, [&](int b) {
-    improve_one(as_cd(x) + b * nn, S + b * nn, M, mask, n, pr, sigma, tau, a_best, a_eval, &err[b]);
+    improve_one(as_cd(x) + b * nn, S + b * nn, M, mask, nullptr, n, pr, sigma, tau, a_best, a_eval,
+                &err[b]);
   });
   return 0;
 }

@@ -36,6 +36,7 @@ class Pattern:
     support0: np.ndarray     # uint8, n x n, real space
     truth: np.ndarray        # complex128, n x n, the object (real space)
     n: int
+    saturated: np.ndarray | None = None  # uint8, n x n, detector-centred, 1 = saturated (masked)
 
 
 def _sphere_thickness(n, cy, cx, radius):
@@ -109,14 +110,15 @@ def pattern_ellipsoids(seed=0, n=512, extent=120.0, photons=1e7, beamstop=12, ga
         mask[_disc(n, beamstop)] = 0
     if gap_rows > 0:
         mask[n // 2 - gap_rows // 2: n // 2 - gap_rows // 2 + gap_rows, :] = 0
+    sat = np.zeros((n, n), bool)
     if saturate:
         lim = np.percentile(I[mask > 0], 99.9)
-        sat = I > lim
+        sat = (I > lim) & (mask > 0)
         I = np.where(sat, lim, I)
         mask[sat] = 0
     I = np.where(mask > 0, I, 0.0)
     S0 = autocorrelation_support(I, mask)
-    return Pattern(I.astype(np.float32), mask, S0, obj.astype(np.complex128), n)
+    return Pattern(I.astype(np.float32), mask, S0, obj.astype(np.complex128), n, sat.astype(np.uint8))
 
 
 def config_pattern(name: str, seed: int = 0) -> Pattern:
@@ -125,7 +127,8 @@ def config_pattern(name: str, seed: int = 0) -> Pattern:
     ``sphere64``   64x64, 1e5 photons, beamstop r=3.
     ``ell512``     512x512, 120 px extent, 1e7 photons, beamstop r=12, 20-row gap,
                    99.9th-percentile saturation.
-    ``ell1024``    1024x1024, 200 px extent, 1e8 photons, hole r=24, 30-row gap.
+    ``ell1024``    1024x1024, 200 px extent, 1e8 photons, hole r=24, 30-row gap (a split
+                   two-panel detector; no saturation).
     ``ellN``       N in {128, 192, 256, 512}: extent 0.25 N, photons log-uniform in
                    [1e6, 1e7], beamstop r = N/40, gap N/25 rows.
     """
@@ -134,7 +137,7 @@ def config_pattern(name: str, seed: int = 0) -> Pattern:
     if name == "ell512":
         return pattern_ellipsoids(seed, 512, 120.0, 1e7, 12, 20, True)
     if name == "ell1024":
-        return pattern_ellipsoids(seed, 1024, 200.0, 1e8, 24, 30, True)
+        return pattern_ellipsoids(seed, 1024, 200.0, 1e8, 24, 30, False)
     if name.startswith("ell"):
         n = int(name[3:])
         rng = np.random.default_rng(10_000 + seed)
