@@ -18,7 +18,9 @@
  *    starting densities").
  *  - Modulus encoding (operator API): M is N x N float32 in DFT order; an entry >= 0 is
  *    the measured modulus sqrt(I) (mask Xi = 1), an entry < 0 marks a pixel whose
- *    intensity is not measured (Xi = 0: beamstop/hole, detector gap, saturation).
+ *    intensity is not measured (Xi = 0: beamstop/hole, detector gap, saturation).  A
+ *    missing pixel whose modulus is bounded above (Eq. pm_bounds) carries M = -2 - U
+ *    (M <= -2, bound U >= 0); entries in (-2, 0) (the library writes -1) are free.
  *  - Supports and masks are uint8, 0 or 1.
  *  - Sizes: N in {64, 128, 192, 256, 512, 1024} (square patterns; N = 2^a or 3 * 2^a).
  *    Other sizes return SPRING_E_INVALID.
@@ -130,6 +132,27 @@ spring_status spring_problem_create_device(spring_ctx* ctx, int ny, int nx,
                                            const float* d_intensities, const uint8_t* d_mask,
                                            const uint8_t* d_support0, void* stream,
                                            spring_problem** out);
+/* Upper bounds for missing intensities (App. "Constraining intensities at large
+ * scattering angles", Eqs. avgint, stdint, upperbound, enforced by Eq. pm_bounds).
+ * Pixels are grouped in rings by their distance from the detector centre (pixel
+ * (N/2, N/2) of the centred arrays) rounded to the nearest integer.  Over the measured
+ * pixels of a ring, mu = mean I and sigma^2 = mean (I - mu)^2; a missing, unsaturated
+ * pixel of a ring with at most max_missing of its pixels missing and at most
+ * max_saturated of them saturated gets the modulus bound U = sqrt(mu + eta sigma). */
+typedef struct {
+  float eta;            /* <= 0: no bounds (paper: 1.5) */
+  float max_missing;    /* fraction of a ring that may be missing (paper: 0.2) */
+  float max_saturated;  /* fraction of a ring that may be saturated (paper: 0.05) */
+} spring_bounds;
+void spring_bounds_default(spring_bounds* b);
+/* spring_problem_create with upper bounds: `saturated` (host, detector-centred, 1 = the
+ * pixel is saturated; such pixels should also be 0 in `mask`) may be NULL; bounds NULL
+ * or eta <= 0 is spring_problem_create.  Every run of the problem uses the bounds.
+ * Errors: as spring_problem_create. */
+spring_status spring_problem_create_bounded(spring_ctx* ctx, int ny, int nx, const float* intensities,
+                                            const uint8_t* mask, const uint8_t* support0,
+                                            const uint8_t* saturated, const spring_bounds* bounds,
+                                            spring_problem** out);
 /* BUSY if an unfinished ticket still references the problem. */
 spring_status spring_problem_destroy(spring_problem* prob);
 /* Device bytes one run of an N x N problem with parameters p holds (admission). */
@@ -164,8 +187,17 @@ spring_status spring_cancel(spring_ctx* ctx, uint64_t ticket);
 /* a1/a3: unitary 2D DFT of `batch` complex64 images in place (inverse != 0: F^-1). */
 spring_status spring_fft2(void* data, int batch, int n, int inverse, void* stream);
 
+/* The modulus array of the operator API from device arrays: I and mask (and saturated,
+ * may be NULL) detector-centred N x N; M out in DFT order (sqrt(I) where mask = 1, the
+ * bound encoding -2 - U where spring_problem_create_bounded would bound the pixel, -1
+ * elsewhere).  bounds NULL or eta <= 0: no bounds.  Scratch: a few KB. */
+spring_status spring_modulus_encode(const float* I, const uint8_t* mask, const uint8_t* saturated, int n,
+                                    const spring_bounds* bounds, float* M, void* stream);
+
 /* a1-a3: out = P_M x = F^-1[ M F x / |F x| where Xi = 1, F x elsewhere ]
- * (Eq. pm with the masked form Eq. pm_full; a zero modulus takes phase 0).
+ * (Eq. pm with the masked form Eq. pm_full; a zero modulus takes phase 0); with bound
+ * entries in M (see the modulus encoding) the free values follow Eq. pm_bounds:
+ * |F x| > U is brought down to U with its phase kept.
  * x and out: batch images (may alias).  M: one pattern shared by the batch. */
 spring_status spring_project_modulus(const void* x, void* out, const float* M, int batch,
                                      int n, void* stream);

@@ -118,6 +118,12 @@ spring_status launch_density_sums(int n, const float2* x, int P, double* partial
                                   cudaStream_t s);
 spring_status launch_gen_stats(int n, const double* err, const uint8_t* S, const uint8_t* replaced,
                                const double* dens, int P, double* row, cudaStream_t s);
+// M (DFT order) from detector-centred I, mask and optional saturation map, with the upper
+// bounds of Eq. pm_bounds encoded as -2 - U when b enables them; ring_scratch holds
+// ring_count(n) doubles
+int ring_count(int n);
+spring_status launch_modulus_encode(int n, const float* I_c, const uint8_t* mask_c, const uint8_t* sat_c,
+                                    const spring_bounds* b, double* ring_scratch, float* M, cudaStream_t s);
 spring_status launch_make_modulus(int n, const float* I_centred, const uint8_t* mask_centred,
                                   float* M, cudaStream_t s);
 spring_status launch_broadcast_support(int n, const uint8_t* S0, int P, uint8_t* S, cudaStream_t s);

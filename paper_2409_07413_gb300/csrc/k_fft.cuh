@@ -140,6 +140,21 @@ struct GroupSync<T, true> {
   static __device__ __forceinline__ NamedSync make() { return NamedSync{1u + threadIdx.x / T, (unsigned)T}; }
 };
 
+// The modulus projection of one value X of the unnormalised column transform (|X| / N is
+// the unitary modulus), Eq. pm_full with the upper bounds of Eq. pm_bounds, times the 1/N
+// that completes the unitary inverse.  Encoding of M: M >= 0 measured (modulus -> M);
+// M <= -2 missing with bound U = -2 - M (modulus -> min(|X| / N, U)); otherwise missing
+// and free (X unchanged).
+__device__ __forceinline__ float2 pm_value(float2 X, float Mv, float inv_n) {
+  const float a2 = X.x * X.x + X.y * X.y;
+  if (Mv >= 0.f) return a2 > 0.f ? cscale(X, Mv * rsqrtf(a2) * inv_n) : make_float2(Mv * inv_n, 0.f);
+  if (Mv <= -2.f) {
+    const float U = -2.f - Mv;
+    if (a2 * (inv_n * inv_n) > U * U) return cscale(X, U * rsqrtf(a2) * inv_n);
+  }
+  return cscale(X, inv_n * inv_n);
+}
+
 __device__ __forceinline__ float2 update_pixel(int alg, float2 xo, float2 pm, bool in_c, float beta) {
   if (in_c) return pm;
   if (alg == 0) return make_float2(0.f, 0.f);
@@ -304,12 +319,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
     for (int m = 0; m < E; ++m) {
       const float Mv = Ms[(t + m * T) * W + c];
       const float2 X = v[m];
-      if (Mv >= 0.f) {
-        const float a2 = X.x * X.x + X.y * X.y;
-        v[m] = a2 > 0.f ? cscale(X, Mv * rsqrtf(a2) * inv_n) : make_float2(Mv * inv_n, 0.f);
-      } else {
-        v[m] = cscale(X, inv_n * inv_n);
-      }
+      v[m] = pm_value(X, Mv, inv_n);
     }
     fft_plan<P, +1, false, W>(v, smem + c, t, a.tw, sync);
 #pragma unroll
@@ -400,12 +410,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_colT(Co
     for (int m = 0; m < E; ++m) {
       const float Mv = mc[t + m * T];
       const float2 X = v[m];
-      if (Mv >= 0.f) {
-        const float a2 = X.x * X.x + X.y * X.y;
-        v[m] = a2 > 0.f ? cscale(X, Mv * rsqrtf(a2) * inv_n) : make_float2(Mv * inv_n, 0.f);
-      } else {
-        v[m] = cscale(X, inv_n * inv_n);
-      }
+      v[m] = pm_value(X, Mv, inv_n);
     }
     fft_plan<P, +1, true, 1>(v, col, t, a.tw, sync);
 #pragma unroll
@@ -504,12 +509,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 256 ? 2 : 1))
     for (int m = 0; m < E; ++m) {
       const float Mv = Mcur[(t + m * T) * W + c];
       const float2 X = v[m];
-      if (Mv >= 0.f) {
-        const float a2 = X.x * X.x + X.y * X.y;
-        v[m] = a2 > 0.f ? cscale(X, Mv * rsqrtf(a2) * inv_n) : make_float2(Mv * inv_n, 0.f);
-      } else {
-        v[m] = cscale(X, inv_n * inv_n);
-      }
+      v[m] = pm_value(X, Mv, inv_n);
     }
     fft_plan<P, +1, false, W>(v, cur + c, t, a.tw, sync);
     float2* base = a.data + (size_t)img * N * N + col;

@@ -687,32 +687,56 @@ static spring_status problem_alloc(spring_ctx* ctx, int n, spring_problem** out,
 }
 
 static spring_status problem_fill(spring_problem* pr, const float* d_I, const uint8_t* d_mask,
+                                  const uint8_t* d_sat, const spring_bounds* b, double* ring_scratch,
                                   const uint8_t* d_S0, cudaStream_t s) {
   const int n = pr->n;
-  SPRING_TRY(launch_make_modulus(n, d_I, d_mask, pr->M, s));
+  SPRING_TRY(launch_modulus_encode(n, d_I, d_mask, d_sat, b, ring_scratch, pr->M, s));
   SPRING_TRY(launch_fp16_scale(n, pr->M, pr->s16, s));
   SPRING_CUDA(cudaMemcpyAsync(pr->S0, d_S0, (size_t)n * n, cudaMemcpyDeviceToDevice, s));
   return SPRING_OK;
 }
 
+void spring_bounds_default(spring_bounds* b) {
+  if (!b) return;
+  b->eta = 1.5f;
+  b->max_missing = 0.2f;
+  b->max_saturated = 0.05f;
+}
+
 spring_status spring_problem_create(spring_ctx* ctx, int ny, int nx, const float* I, const uint8_t* mask,
                                     const uint8_t* S0, spring_problem** out) {
+  return spring_problem_create_bounded(ctx, ny, nx, I, mask, S0, nullptr, nullptr, out);
+}
+
+spring_status spring_problem_create_bounded(spring_ctx* ctx, int ny, int nx, const float* I,
+                                            const uint8_t* mask, const uint8_t* S0, const uint8_t* sat,
+                                            const spring_bounds* b, spring_problem** out) {
   if (ny != nx) return invalid("patterns must be square");
   if (!I || !mask || !S0) return invalid("null input array");
+  if (b && b->eta > 0.f && !(b->max_missing >= 0.f && b->max_saturated >= 0.f && std::isfinite(b->eta)))
+    return invalid("bounds: eta must be finite and the fractions >= 0");
   spring_problem* pr = nullptr;
   SPRING_TRY(problem_alloc(ctx, nx, out, &pr));
   const size_t nn = (size_t)nx * nx;
+  // device staging: ring scratch (doubles) | I | mask | S0 | saturated
+  const size_t ring_bytes = sizeof(double) * (size_t)ring_count(nx);
   char* tmp = nullptr;
   spring_status st = SPRING_OK;
-  cudaError_t e = cudaMalloc(&tmp, nn * (sizeof(float) + 2));
-  if (e == cudaSuccess) e = cudaMemcpy(tmp, I, sizeof(float) * nn, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(tmp + sizeof(float) * nn, mask, nn, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(tmp + (sizeof(float) + 1) * nn, S0, nn, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc(&tmp, ring_bytes + nn * (sizeof(float) + 3));
+  char* dI = tmp + ring_bytes;
+  char* dmask = dI + sizeof(float) * nn;
+  char* dS0 = dmask + nn;
+  char* dsat = dS0 + nn;
+  if (e == cudaSuccess) e = cudaMemcpy(dI, I, sizeof(float) * nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dmask, mask, nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dS0, S0, nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && sat) e = cudaMemcpy(dsat, sat, nn, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     st = cuda_fail(e, "problem upload", __FILE__, __LINE__);
   } else {
-    st = problem_fill(pr, reinterpret_cast<float*>(tmp), reinterpret_cast<uint8_t*>(tmp + sizeof(float) * nn),
-                      reinterpret_cast<uint8_t*>(tmp + (sizeof(float) + 1) * nn), nullptr);
+    st = problem_fill(pr, reinterpret_cast<float*>(dI), reinterpret_cast<uint8_t*>(dmask),
+                      sat ? reinterpret_cast<uint8_t*>(dsat) : nullptr, b, reinterpret_cast<double*>(tmp),
+                      reinterpret_cast<uint8_t*>(dS0), nullptr);
     if (st == SPRING_OK) {
       e = cudaStreamSynchronize(nullptr);
       if (e != cudaSuccess) st = cuda_fail(e, "problem set-up", __FILE__, __LINE__);
@@ -736,7 +760,8 @@ spring_status spring_problem_create_device(spring_ctx* ctx, int ny, int nx, cons
   if (!d_I || !d_mask || !d_S0) return invalid("null input array");
   spring_problem* pr = nullptr;
   SPRING_TRY(problem_alloc(ctx, nx, out, &pr));
-  spring_status st = problem_fill(pr, d_I, d_mask, d_S0, reinterpret_cast<cudaStream_t>(stream));
+  spring_status st = problem_fill(pr, d_I, d_mask, nullptr, nullptr, nullptr, d_S0,
+                                  reinterpret_cast<cudaStream_t>(stream));
   if (st != SPRING_OK) {
     cudaFree(pr->M);
     cudaFree(pr->S0);

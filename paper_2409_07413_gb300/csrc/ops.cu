@@ -342,6 +342,18 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
   return SPRING_OK;
 }
 
+spring_status spring_modulus_encode(const float* I, const uint8_t* mask, const uint8_t* sat, int n,
+                                    const spring_bounds* b, float* M, void* stream) {
+  SPRING_TRY(check_n(n, 1));
+  if (!I || !mask || !M) return invalid("null pointer");
+  if (b && b->eta > 0.f && !(b->max_missing >= 0.f && b->max_saturated >= 0.f && std::isfinite(b->eta)))
+    return invalid("bounds: eta must be finite and the fractions >= 0");
+  cudaStream_t s = ST(stream);
+  Scratch ring;
+  if (b && b->eta > 0.f) SPRING_TRY(ring.alloc(sizeof(double) * (size_t)ring_count(n), s));
+  return launch_modulus_encode(n, I, mask, sat, b, ring.as<double>(), M, s);
+}
+
 spring_status spring_iterate_ex(void* x, const uint8_t* S, const float* M, int batch, int n,
                                 int algorithm, float beta, float chi, int n_iter, int precision,
                                 void* stream) {

@@ -43,6 +43,10 @@ class Result(C.Structure):
     ]
 
 
+class Bounds(C.Structure):
+    _fields_ = [("eta", C.c_float), ("max_missing", C.c_float), ("max_saturated", C.c_float)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("total_ms", C.c_double), ("timed", C.c_uint64),
                 ("bytes_per_launch", C.c_double)]
@@ -59,6 +63,10 @@ _SIGS = {
     "spring_shutdown": (_i, [_vp]),
     "spring_problem_create": (_i, [_vp, _i, _i, _vp, _vp, _vp, C.POINTER(_vp)]),
     "spring_problem_create_device": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    "spring_problem_create_bounded": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, C.POINTER(Bounds),
+                                           C.POINTER(_vp)]),
+    "spring_bounds_default": (None, [C.POINTER(Bounds)]),
+    "spring_modulus_encode": (_i, [_vp, _vp, _vp, _i, C.POINTER(Bounds), _vp, _vp]),
     "spring_problem_destroy": (_i, [_vp]),
     "spring_footprint_bytes": (C.c_size_t, [_i, C.POINTER(Params)]),
     "spring_mpr_run": (_i, [_vp, C.POINTER(Params), C.POINTER(Result)]),
@@ -172,6 +180,30 @@ def params(**kw) -> Params:
         if e not in kw and s in kw:
             setattr(p, e, kw[s])
     return p
+
+
+def bounds(**kw) -> Bounds:
+    """Upper-bound settings (Eq. pm_bounds); defaults eta 1.5, max_missing 0.2,
+    max_saturated 0.05."""
+    b = Bounds()
+    lib().spring_bounds_default(C.byref(b))
+    for k, v in kw.items():
+        if not hasattr(b, k):
+            raise KeyError(k)
+        setattr(b, k, v)
+    return b
+
+
+def spring_modulus_encode(I, mask, saturated=None, bounds_=None, out=None):
+    """Modulus array (DFT order) of detector-centred device I / mask (/ saturated)."""
+    import torch
+    _need(I, torch.float32, "I")
+    _need(mask, torch.uint8, "mask")
+    n = I.shape[-1]
+    M = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=I.device)
+    _call("spring_modulus_encode", _ptr(I), _ptr(mask), _ptr(saturated) if saturated is not None else None,
+          n, C.byref(bounds_) if bounds_ is not None else None, _ptr(M), _stream())
+    return M
 
 
 def footprint_bytes(n: int, p: Params) -> int:
@@ -408,16 +440,25 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def problem(self, intensities, mask, support0):
-        """Host numpy arrays (detector-centred I and mask, real-space support)."""
+    def problem(self, intensities, mask, support0, saturated=None, bounds=None):
+        """Host numpy arrays (detector-centred I and mask, real-space support); with
+        `bounds` (a Bounds) the missing moduli get the upper bounds of Eq. pm_bounds
+        (`saturated`: detector-centred map of saturated pixels, optional)."""
         import numpy as np
         I = np.ascontiguousarray(intensities, dtype=np.float32)
         m = np.ascontiguousarray(mask, dtype=np.uint8)
         s = np.ascontiguousarray(support0, dtype=np.uint8)
         h = C.c_void_p()
-        _call("spring_problem_create", self.handle, I.shape[0], I.shape[1],
-              I.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
-              s.ctypes.data_as(C.c_void_p), C.byref(h))
+        if bounds is None and saturated is None:
+            _call("spring_problem_create", self.handle, I.shape[0], I.shape[1],
+                  I.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                  s.ctypes.data_as(C.c_void_p), C.byref(h))
+        else:
+            sat = None if saturated is None else np.ascontiguousarray(saturated, dtype=np.uint8)
+            _call("spring_problem_create_bounded", self.handle, I.shape[0], I.shape[1],
+                  I.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                  s.ctypes.data_as(C.c_void_p), None if sat is None else sat.ctypes.data_as(C.c_void_p),
+                  C.byref(bounds) if bounds is not None else None, C.byref(h))
         return Problem(self, h, I.shape[0])
 
     def problem_device(self, I, mask, support0):

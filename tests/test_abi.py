@@ -67,13 +67,15 @@ _LAYOUT_C = r"""
 #include "spring.h"
 #define F(T, m) printf("%s.%s %zu\n", #T, #m, offsetof(T, m));
 int main(void) {
-  printf("spring_params %zu\nspring_result %zu\nspring_kernel_stat %zu\n",
-         sizeof(spring_params), sizeof(spring_result), sizeof(spring_kernel_stat));
+  printf("spring_params %zu\nspring_result %zu\nspring_kernel_stat %zu\nspring_bounds %zu\n",
+         sizeof(spring_params), sizeof(spring_result), sizeof(spring_kernel_stat),
+         sizeof(spring_bounds));
   F(spring_params, pop) F(spring_params, beta) F(spring_params, sw_period) F(spring_params, chi)
   F(spring_params, tile_min) F(spring_params, init_gamma) F(spring_params, precision)
   F(spring_params, use_graph) F(spring_params, seed)
   F(spring_result, gen_stats) F(spring_result, final_error_avg) F(spring_result, t_done_s)
   F(spring_kernel_stat, total_ms) F(spring_kernel_stat, bytes_per_launch)
+  F(spring_bounds, eta) F(spring_bounds, max_missing) F(spring_bounds, max_saturated)
   return 0;
 }
 """
@@ -91,8 +93,9 @@ def test_struct_layouts_match_header(tmp_path):
     assert vals["spring_params"] == C.sizeof(spring.Params)
     assert vals["spring_result"] == C.sizeof(spring.Result)
     assert vals["spring_kernel_stat"] == C.sizeof(spring.KernelStat)
+    assert vals["spring_bounds"] == C.sizeof(spring.Bounds)
     cls = {"spring_params": spring.Params, "spring_result": spring.Result,
-           "spring_kernel_stat": spring.KernelStat}
+           "spring_kernel_stat": spring.KernelStat, "spring_bounds": spring.Bounds}
     for k, v in vals.items():
         if "." in k:
             t, m = k.split(".")
