@@ -10,7 +10,8 @@ Both runs keep the Fourier-error fitness and the shrink-wrap threshold statistic
 on the GPU.  Per result it reports time, reconstructions/s, iteration-pixels/s, the final
 Fourier error (Eq. error_calc) of the average and best individual, and the error of the
 aligned average against the synthetic object (aligned by spring_reshift: translation,
-twin and global phase).
+twin and global phase; then the best real scale, since intensities in photon counts fix the
+object only up to a global factor).
 
     python -m paper_2409_07413_gb300.precbench [--generations 20] [--iters 300] [--pop 128]
 
@@ -34,7 +35,9 @@ def truth_error(spring, rho, truth):
     torch.cuda.synchronize()
     a = al[0].cpu().numpy().astype(np.complex128)
     t = truth.astype(np.complex128)
-    return float(np.linalg.norm(a - t) / np.linalg.norm(t))
+    # the data fix the object only up to a global scale (intensities are photon counts)
+    c = np.real(np.vdot(a, t)) / max(np.vdot(a, a).real, 1e-300)
+    return float(np.linalg.norm(c * a - t) / np.linalg.norm(t))
 
 
 def main():

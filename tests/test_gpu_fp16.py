@@ -200,4 +200,4 @@ def test_mpr_fp16_deterministic_and_graph_identical(sp, ctx):
     b = prob.run(sp.params(**C1, seed=9, precision=1, use_graph=1))
     prob.destroy()
     assert np.array_equal(a["rho_avg"], b["rho_avg"])
-    assert np.array_equal(a["gen_stats"], b["gen_stats"])
+    assert np.array_equal(a["gen_stats"], b["gen_stats"], equal_nan=True)  # E(avg) is NaN before the end
