@@ -212,6 +212,16 @@ spring_status spring_project_modulus(const void* x, void* out, const float* M, i
 spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batch, int n,
                              int algorithm, float beta, float chi, int n_iter, void* stream);
 
+/* a1-a4 on chip (N in {64, 128, 192, 256}): the same n_iter iterations as spring_iterate
+ * with the image of each individual held in the shared memory of a thread-block cluster
+ * of N/32 CTAs for the whole call (distributed shared memory between the row and the
+ * column transforms); HBM is read once and written once per call.  Results equal
+ * spring_iterate's with the default transform plan of side N (row variants 0-4, column
+ * variants 0 and 2-7).  INVALID for other sides or where the device cannot hold such a
+ * cluster.  No scratch. */
+spring_status spring_iterate_fused(void* x, const uint8_t* S, const float* M, int batch, int n,
+                                   int algorithm, float beta, float chi, int n_iter, void* stream);
+
 /* a1-a4 with a choice of storage precision: precision 0 is spring_iterate; precision 1
  * keeps x and the FFT intermediate as FP16 (half2) between the passes while every
  * operation runs in FP32 (x is rounded to FP16 once on entry and returned as complex64).
@@ -343,6 +353,12 @@ spring_status spring_get_kernel_variant(int n, int* row_variant, int* col_varian
 /* Time every variant on `batch` scratch images of side n on `stream` and keep the
  * fastest.  Allocates scratch; blocks the host until done; do not call during capture. */
 spring_status spring_autotune(int n, int batch, void* stream);
+/* How runs iterate at side n: 0 = two passes through HBM per iteration (row pass, column
+ * pass), 1 = the on-chip kernel of spring_iterate_fused (N <= 256; INVALID where the
+ * device cannot hold its clusters).  The autotuner picks the faster one; an explicit
+ * choice is kept. */
+spring_status spring_set_iteration_path(int n, int path);
+spring_status spring_get_iteration_path(int n, int* path);
 
 /* ---------------------------------------------------------------- instrumentation
  * Per-kernel-class launch counts and (when enabled) CUDA-event durations recorded on the
@@ -357,7 +373,8 @@ typedef struct {
 #define SPRING_KC_ROW_ITER 0  /* iteration row pass (inverse row FFT, update, forward row FFT) */
 #define SPRING_KC_COL_PM 1    /* iteration column pass (column FFT, P_M, inverse column FFT) */
 #define SPRING_KC_OTHER 2     /* every other kernel of the library */
-#define SPRING_KC_COUNT 3
+#define SPRING_KC_FUSED 3     /* on-chip whole iterations (spring_iterate_fused, N <= 256) */
+#define SPRING_KC_COUNT 4
 void spring_stats_reset(void);
 void spring_stats_enable_timing(int on);
 void spring_stats_get(int kernel_class, spring_kernel_stat* out);

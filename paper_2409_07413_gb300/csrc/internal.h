@@ -42,6 +42,16 @@ spring_status launch_row_init16(int n, const float2* x, void* xh, void* wh, long
                                 cudaStream_t s);
 spring_status launch_half_to_float(const void* xh, float2* x, long long total, const float* s16, cudaStream_t s);
 
+// the on-chip whole-iteration kernel (k_cluster.cu): n_iter iterations of ER/HIO/RAAR on
+// `batch` images of side n <= 256 in place, one thread-block cluster per image
+bool cluster_side(int n);
+spring_status prepare_cluster_kernels(int n);
+spring_status cluster_supported(int n, bool* ok);
+spring_status launch_cluster_iter(int n, int alg, float2* x, const uint8_t* S, const float* M, long long batch,
+                                  float beta, float chi, int n_iter, cudaStream_t s);
+// 0: two passes through HBM per iteration; 1: the on-chip kernel (set by the autotuner)
+int iteration_path(int n);
+
 // kernel-variant autotuning of side n on `batch` images (once per process and side)
 spring_status ensure_tuned(int n, int batch, cudaStream_t s);
 spring_status prepare_fft_kernels(int n);

@@ -48,9 +48,19 @@ static int side_index(int n) {
 // Launch-shape variants of the two per-iteration passes, per side (see k_fft.cuh); the
 // defaults are the fastest measured on a GB300 at 33.5 M pixels per launch.
 static std::mutex g_var_mu;
-static int g_row_var[6] = {0, 5, 1, 0, 6, 0};
+static int g_row_var[6] = {0, 5, 1, 0, 6, 5};
 static int g_col_var[6] = {0, 2, 0, 0, 0, 3};
 static bool g_tuned[6] = {false, false, false, false, false, false};
+// iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
+// (N <= 256, k_cluster.cu); chosen by the autotuner, the two-pass path until then
+static int g_path[6] = {0, 0, 0, 0, 0, 0};
+
+int iteration_path(int n) {
+  const int si = side_index(n);
+  if (si < 0) return 0;
+  std::lock_guard<std::mutex> lk(g_var_mu);
+  return g_path[si];
+}
 
 static int row_variant(int n) {
   std::lock_guard<std::mutex> lk(g_var_mu);
@@ -315,6 +325,7 @@ spring_status prepare_fft_kernels(int n) {
         SPRING_TRY(dispatch(n, op, nullptr, true));
       }
   }
+  SPRING_TRY(prepare_cluster_kernels(n));
   SPRING_CHECK_LAUNCH();
   return SPRING_OK;
 }
@@ -423,9 +434,44 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
       best_c = v;
     }
   }
+  // the on-chip path against the two passes with the chosen variants, over one block of
+  // 20 iterations
+  int path = 0;
+  bool fused_ok = false;
+  SPRING_TRY(cluster_supported(n, &fused_ok));
+  if (fused_ok) {
+    constexpr int K = 20;
+    op.variant = best_r;
+    cop.variant = best_c;
+    cudaEvent_t e0, e1, e2;
+    SPRING_CUDA(cudaEventCreate(&e0));
+    SPRING_CUDA(cudaEventCreate(&e1));
+    SPRING_CUDA(cudaEventCreate(&e2));
+    spring_status st = launch_cluster_iter(n, 2, x, S, M, batch, 0.9f, 0.5f, K, s);  // warm-up
+    if (st == SPRING_OK) st = dispatch(n, cop, s);
+    if (st == SPRING_OK) st = dispatch(n, op, s);
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < K && st == SPRING_OK; ++k) {
+      st = dispatch(n, cop, s);
+      if (st == SPRING_OK) st = dispatch(n, op, s);
+    }
+    cudaEventRecord(e1, s);
+    if (st == SPRING_OK) st = launch_cluster_iter(n, 2, x, S, M, batch, 0.9f, 0.5f, K, s);
+    cudaEventRecord(e2, s);
+    cudaEventSynchronize(e2);
+    float two = 0.f, one = 0.f;
+    cudaEventElapsedTime(&two, e0, e1);
+    cudaEventElapsedTime(&one, e1, e2);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    SPRING_TRY(st);
+    path = one < two ? 1 : 0;
+  }
   std::lock_guard<std::mutex> lk(g_var_mu);
   g_row_var[si] = best_r;
   g_col_var[si] = best_c;
+  g_path[si] = path;
   g_tuned[si] = true;
   return SPRING_OK;
 }
@@ -474,6 +520,29 @@ spring_status spring_get_kernel_variant(int n, int* row_variant, int* col_varian
 
 spring_status spring_autotune(int n, int batch, void* stream) {
   return autotune_n(n, batch, reinterpret_cast<cudaStream_t>(stream));
+}
+
+spring_status spring_set_iteration_path(int n, int path) {
+  const int si = side_index(n);
+  if (si < 0) return invalid("unsupported pattern side");
+  if (path != 0 && path != 1) return invalid("path must be 0 (two passes) or 1 (on chip)");
+  if (path == 1) {
+    bool ok = false;
+    SPRING_TRY(cluster_supported(n, &ok));
+    if (!ok) return invalid("the on-chip iteration kernel does not cover this side on this device");
+  }
+  std::lock_guard<std::mutex> lk(g_var_mu);
+  g_path[si] = path;
+  g_tuned[si] = true;  // an explicit choice is kept
+  return SPRING_OK;
+}
+
+spring_status spring_get_iteration_path(int n, int* path) {
+  const int si = side_index(n);
+  if (si < 0) return invalid("unsupported pattern side");
+  std::lock_guard<std::mutex> lk(g_var_mu);
+  if (path) *path = g_path[si];
+  return SPRING_OK;
 }
 
 }  // extern "C"

@@ -60,8 +60,9 @@ template <> struct AltPlan<256>  : PlanT<256, 32, 32, 8> {};
 template <> struct AltPlan<512>  : PlanT<512, 8, 8, 8, 8> {};
 template <> struct AltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
-// alternative row-pass plans (one lane group per row: T <= 32)
+// alternative row-pass plans (fewer elements per thread; T = 64 rows sync by named barrier)
 template <int N> struct RowAltPlan : Plan<N> {};
+template <> struct RowAltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 template <> struct RowAltPlan<512> : PlanT<512, 8, 8, 8, 8> {};
 template <> struct RowAltPlan<256> : PlanT<256, 32, 32, 8> {};
 template <> struct RowAltPlan<128> : PlanT<128, 16, 16, 8> {};

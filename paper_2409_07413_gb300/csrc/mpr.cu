@@ -271,6 +271,11 @@ class Run {
       x16_newer = true;
       return SPRING_OK;
     }
+    if (iteration_path(n) == 1) {  // on chip: x in, x out; w is left stale
+      SPRING_TRY(launch_cluster_iter(n, alg, x, S, M, B, prm.beta, prm.chi, k, s));
+      z_valid = false;
+      return SPRING_OK;
+    }
     if (!z_valid) {
       SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, B, 1.0f, s));
       z_valid = true;

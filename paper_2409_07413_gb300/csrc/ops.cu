@@ -342,6 +342,19 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
   return SPRING_OK;
 }
 
+spring_status spring_iterate_fused(void* x, const uint8_t* S, const float* M, int batch, int n,
+                                   int algorithm, float beta, float chi, int n_iter, void* stream) {
+  SPRING_TRY(check_n(n, batch));
+  if (algorithm < 0 || algorithm > 2) return invalid("algorithm must be 0, 1 or 2");
+  if (n_iter < 0) return invalid("negative iteration count");
+  bool ok = false;
+  SPRING_TRY(cluster_supported(n, &ok));
+  if (!ok) return invalid("the on-chip iteration kernel does not cover this side on this device");
+  if (batch == 0 || n_iter == 0) return SPRING_OK;
+  if (!x || !S || !M) return invalid("null pointer");
+  return launch_cluster_iter(n, algorithm, static_cast<float2*>(x), S, M, batch, beta, chi, n_iter, ST(stream));
+}
+
 spring_status spring_modulus_encode(const float* I, const uint8_t* mask, const uint8_t* sat, int n,
                                     const spring_bounds* b, float* M, void* stream) {
   SPRING_TRY(check_n(n, 1));

@@ -43,6 +43,30 @@ def run(n, batch, iters, alg, warm=3, precision=0):
     return out
 
 
+def run_fused(n, batch, iters, alg, warm=3):
+    """The on-chip kernel: one launch of `iters` iterations (N <= 256)."""
+    import torch
+
+    from paper_2409_07413_gb300 import spring
+
+    g = torch.Generator(device="cuda").manual_seed(n)
+    x = torch.randn((batch, n, n), dtype=torch.complex64, device="cuda", generator=g)
+    S = (torch.rand((batch, n, n), device="cuda", generator=g) < 0.25).to(torch.uint8)
+    M = torch.rand((n, n), device="cuda", generator=g) + 0.1
+    M[torch.rand((n, n), device="cuda", generator=g) < 0.05] = -1.0
+    spring.spring_iterate_fused(x, S, M, alg, 0.9, 0.5, warm)
+    torch.cuda.synchronize()
+    spring.stats_reset()
+    spring.stats_enable_timing(True)
+    spring.spring_iterate_fused(x, S, M, alg, 0.9, 0.5, iters)
+    torch.cuda.synchronize()
+    spring.stats_enable_timing(False)
+    st = spring.stats_get(spring.KC_FUSED)
+    ms = st.total_ms / max(1, st.timed)
+    return {"n": n, "batch": batch, "iters": iters, "alg": alg, "path": "on-chip", "launch_ms": ms,
+            "iteration_ms": ms / iters, "iteration_px_per_s": batch * n * n * iters / (ms / 1e3)}
+
+
 def sweep(n, batch, iters, alg):
     """Time every (row, column) launch variant of side n; returns the list of results."""
     from paper_2409_07413_gb300 import spring
@@ -68,6 +92,7 @@ def main():
     ap.add_argument("--alg", type=int, default=2)
     ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: FP16 storage")
     ap.add_argument("--sweep", action="store_true", help="time every launch variant")
+    ap.add_argument("--fused", action="store_true", help="also time the on-chip kernel (N <= 256)")
     a = ap.parse_args()
     for n in a.n:
         b = a.batch if a.batch > 0 else max(1, (128 * 512 * 512) // (n * n))
@@ -78,6 +103,8 @@ def main():
                                   "col_GBps": r["col_pm"]["GBps"]}), flush=True)
         else:
             print(json.dumps(run(n, b, a.iters, a.alg, precision=a.precision)), flush=True)
+        if a.fused and n <= 256:
+            print(json.dumps(run_fused(n, b, a.iters, a.alg)), flush=True)
 
 
 if __name__ == "__main__":

@@ -13,7 +13,7 @@ from pathlib import Path
 _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libspring.so"
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_BUSY, E_TIMEOUT, E_NOT_FOUND, E_NUMERIC, E_CANCELLED = range(9)
-KC_ROW_ITER, KC_COL_PM, KC_OTHER = 0, 1, 2
+KC_ROW_ITER, KC_COL_PM, KC_OTHER, KC_FUSED = 0, 1, 2, 3
 
 
 class SpringError(RuntimeError):
@@ -77,6 +77,7 @@ _SIGS = {
     "spring_project_modulus": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "spring_iterate": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _f, _i, _vp]),
     "spring_iterate_ex": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _f, _i, _i, _vp]),
+    "spring_iterate_fused": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _f, _i, _vp]),
     "spring_smooth": (_i, [_vp, _vp, _i, _i, _f, _vp]),
     "spring_update_support": (_i, [_vp, _vp, _i, _i, _f, _f, _vp]),
     "spring_update_support_size": (_i, [_vp, _vp, _i, _i, _f, _vp, _vp]),
@@ -93,6 +94,8 @@ _SIGS = {
     "spring_set_kernel_variant": (_i, [_i, _i, _i]),
     "spring_get_kernel_variant": (_i, [_i, C.POINTER(_i), C.POINTER(_i)]),
     "spring_autotune": (_i, [_i, _i, _vp]),
+    "spring_set_iteration_path": (_i, [_i, _i]),
+    "spring_get_iteration_path": (_i, [_i, C.POINTER(_i)]),
     "spring_stats_reset": (None, []),
     "spring_stats_enable_timing": (None, [_i]),
     "spring_stats_get": (None, [_i, C.POINTER(KernelStat)]),
@@ -251,6 +254,18 @@ def spring_iterate_ex(x, S, M, algorithm, beta, chi, n_iter, precision):
     return x
 
 
+def spring_iterate_fused(x, S, M, algorithm, beta, chi, n_iter):
+    """spring_iterate on chip (N <= 256): one thread-block cluster per image."""
+    import torch
+    _need(x, torch.complex64, "x")
+    _need(S, torch.uint8, "S")
+    _need(M, torch.float32, "M")
+    b, n = _batch_n(x)
+    _call("spring_iterate_fused", _ptr(x), _ptr(S), _ptr(M), b, n, int(algorithm), float(beta),
+          float(chi), int(n_iter), _stream())
+    return x
+
+
 def spring_smooth(x, sigma, out=None):
     import torch
     _need(x, torch.complex64, "x")
@@ -402,6 +417,17 @@ def autotune(n, batch):
 
 
 # ------------------------------------------------------------------ instrumentation
+def set_iteration_path(n, path):
+    """0: two passes through HBM per iteration; 1: on chip (N <= 256)."""
+    _call("spring_set_iteration_path", int(n), int(path))
+
+
+def get_iteration_path(n) -> int:
+    p = C.c_int()
+    _call("spring_get_iteration_path", int(n), C.byref(p))
+    return p.value
+
+
 def stats_reset():
     lib().spring_stats_reset()
 
