@@ -53,6 +53,8 @@ class OrcParams(C.Structure):
         ("init_gamma", C.c_double), ("init_phi_max", C.c_double),
         ("seed", C.c_uint64),
         ("ub_eta", C.c_double), ("ub_max_missing", C.c_double), ("ub_max_saturated", C.c_double),
+        ("schedule", C.c_int), ("mode", C.c_int), ("seq_ia", C.c_int), ("seq_er", C.c_int),
+        ("seq_eval", C.c_int), ("repetitions", C.c_int), ("ca", C.c_double),
     ]
 
 
@@ -81,6 +83,7 @@ def lib():
             "orc_project_modulus_ub": (C.c_int, [_dp, _dp, _dp, _u8p, _dp, C.c_int, C.c_int]),
             "orc_upper_bounds": (None, [_dp, _u8p, _u8p, C.c_int, C.c_double, C.c_double,
                                         C.c_double, _dp]),
+            "orc_sequence_counts": (None, [C.c_int, C.c_int, C.c_int, C.c_int, _ip]),
             "orc_iterate_ub": (C.c_int, [_dp, _u8p, _dp, _u8p, _dp, C.c_int, C.c_int, C.c_int,
                                          C.c_double, C.c_double, C.c_int]),
             "orc_iterate": (C.c_int, [_dp, _u8p, _dp, _u8p, C.c_int, C.c_int, C.c_int,
@@ -100,6 +103,10 @@ def lib():
             "orc_reshift": (None, [_dp, _u8p, _dp, _u8p, C.c_int, _dp, _u8p, _ip, _dp]),
             "orc_crossover": (None, [_dp, _u8p, _u8p, C.c_int, C.c_int, C.c_uint64, C.c_int,
                                      C.c_double, C.c_double, C.c_int, C.c_int, _dp, _u8p, _ip]),
+            "orc_crossover_ca": (None, [_dp, _u8p, _u8p, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                                        C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, _dp,
+                                        _dp, _u8p, _ip]),
+            "orc_average_moduli": (None, [_dp, _u8p, _u8p, C.c_int, C.c_int, C.c_int, _dp]),
             "orc_select": (C.c_int, [_dp, _dp, C.c_int, _u8p]),
             "orc_average": (None, [_dp, _u8p, _u8p, C.c_int, C.c_int, C.c_int, _dp, _u8p]),
             "orc_complexity": (C.c_double, [_dp, C.c_int, _dp]),
@@ -192,6 +199,13 @@ def project_modulus_ub(x, M, mask, U):
     M, mask, U = _f64(M), _u8(mask), _f64(U)
     lib().orc_project_modulus_ub(_pd(x), _pd(out), _pd(M), _pu8(mask), _pd(U), x.shape[0], x.shape[1])
     return out[0] if sq else out
+
+
+def sequence_counts(seq_ia, seq_er, g, G):
+    """(IA, ER) iteration counts of the paper's Sequence at generation g of G."""
+    out = np.zeros(2, np.int32)
+    lib().orc_sequence_counts(int(seq_ia), int(seq_er), int(g), int(G), out.ctypes.data_as(_ip))
+    return int(out[0]), int(out[1])
 
 
 def upper_bounds(I_centred, mask_centred, saturated=None, eta=1.5, max_missing=0.2, max_saturated=0.05):
@@ -318,16 +332,32 @@ def reshift(x, S, ref, mask):
     return xo, So, tuple(info), ph.value
 
 
-def crossover(pop_x, pop_S, mask, seed, g, cw, cp, tmin, tmax):
+def crossover(pop_x, pop_S, mask, seed, g, cw, cp, tmin, tmax, ca=0.0, Mavg=None):
+    """Alg. crossover; with ca > 0 the parent a's moduli move towards Mavg (Eq. crossavg)."""
     pop_x, pop_S, mask = _c128(pop_x), _u8(pop_S), _u8(mask)
     P, n = pop_x.shape[0], pop_x.shape[1]
     nx = np.empty_like(pop_x)
     nS = np.empty_like(pop_S)
     par = np.empty((P, 3), dtype=np.int32)
-    lib().orc_crossover(_pd(pop_x), _pu8(pop_S), _pu8(mask), P, n, C.c_uint64(seed), g,
-                        float(cw), float(cp), tmin, tmax, _pd(nx), _pu8(nS),
-                        par.ctypes.data_as(_ip))
+    if ca > 0.0:
+        Mavg = _f64(Mavg)
+        lib().orc_crossover_ca(_pd(pop_x), _pu8(pop_S), _pu8(mask), P, n, C.c_uint64(seed), g,
+                               float(cw), float(cp), tmin, tmax, float(ca), _pd(Mavg), _pd(nx),
+                               _pu8(nS), par.ctypes.data_as(_ip))
+    else:
+        lib().orc_crossover(_pd(pop_x), _pu8(pop_S), _pu8(mask), P, n, C.c_uint64(seed), g,
+                            float(cw), float(cp), tmin, tmax, _pd(nx), _pu8(nS),
+                            par.ctypes.data_as(_ip))
     return nx, nS, par
+
+
+def average_moduli(pop_x, pop_S, mask, best):
+    """(|F rho_avg| + mean_p |F rho_p|) / 2 (Eqs. avgint1, avgint2), DFT order."""
+    pop_x, pop_S, mask = _c128(pop_x), _u8(pop_S), _u8(mask)
+    P, n = pop_x.shape[0], pop_x.shape[1]
+    out = np.empty((n, n), np.float64)
+    lib().orc_average_moduli(_pd(pop_x), _pu8(pop_S), _pu8(mask), P, n, int(best), _pd(out))
+    return out
 
 
 def select(e_old, e_new):
@@ -366,7 +396,8 @@ DEFAULTS = dict(pop=8, iters_per_gen=100, generations=5, algorithm=2, beta=0.9,
                 sw_sigma=1.5, sw_threshold=0.2, sw_sigma_end=None, sw_threshold_end=None,
                 sw_period=20, er_tail=10, chi=0.5, cw=0.4, cp=0.6, tile_min=4, tile_max=0,
                 init_n_spheres=5, init_gamma=1.0, init_phi_max=0.0, seed=0,
-                ub_eta=0.0, ub_max_missing=0.2, ub_max_saturated=0.05)
+                ub_eta=0.0, ub_max_missing=0.2, ub_max_saturated=0.05,
+                schedule=0, mode=0, seq_ia=40, seq_er=40, seq_eval=40, repetitions=3, ca=0.0)
 
 
 def make_params(**kw) -> OrcParams:

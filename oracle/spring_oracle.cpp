@@ -721,6 +721,8 @@ extern "C" void orc_reshift(const double* x, const uint8_t* S, const double* ref
 struct CrossCfg {
   double cw, cp;
   int tmin, tmax;
+  double ca = 0.0;              // crossover averaging C_a
+  const double* Mavg = nullptr;  // (M-dot + M-double-dot) / 2, DFT order (C_a > 0)
 };
 
 static void crossover_one(const cd* pop_x, const uint8_t* pop_S, const uint8_t* mask, int P,
@@ -745,6 +747,15 @@ static void crossover_one(const cd* pop_x, const uint8_t* pop_S, const uint8_t* 
   std::vector<cd> Xp(xp, xp + nn);
   fft2_inplace(Xp.data(), n, 0);
   for (int k = 0; k < 3; k++) fft2_inplace(xs[k], n, 0);
+  // crossover averaging (Eq. crossavg): parent a's moduli move towards the population's
+  // average moduli by C_a, its phases are kept (a zero modulus takes phase 0)
+  if (cf.ca > 0.0) {
+    for (size_t i = 0; i < nn; i++) {
+      double a = std::abs(xa[i]);
+      double m = cf.ca * cf.Mavg[i] + (1.0 - cf.ca) * a;
+      xa[i] = (a > 0.0) ? xa[i] * (m / a) : cd(m, 0.0);
+    }
+  }
   std::vector<uint8_t> map(nn);
   crossover_map(seed, g, p, n, cf.tmin, cf.tmax, cf.cp, map.data());
   cd* out = new_x + (size_t)p * nn;
@@ -760,6 +771,18 @@ extern "C" void orc_crossover(const double* pop_x, const uint8_t* pop_S, const u
                               int P, int n, uint64_t seed, int g, double cw, double cp, int tmin,
                               int tmax, double* new_x, uint8_t* new_S, int* parents) {
   CrossCfg cf{cw, cp, tmin, tmax};
+  parallel_for(P, [&](int p) {
+    crossover_one(as_cd(pop_x), pop_S, mask, P, n, seed, g, p, cf, as_cd(new_x), new_S,
+                  parents ? parents + 3 * p : nullptr);
+  });
+}
+
+// the same with crossover averaging: Mavg = (M-dot + M-double-dot) / 2 in DFT order
+extern "C" void orc_crossover_ca(const double* pop_x, const uint8_t* pop_S, const uint8_t* mask,
+                                 int P, int n, uint64_t seed, int g, double cw, double cp, int tmin,
+                                 int tmax, double ca, const double* Mavg, double* new_x,
+                                 uint8_t* new_S, int* parents) {
+  CrossCfg cf{cw, cp, tmin, tmax, ca, Mavg};
   parallel_for(P, [&](int p) {
     crossover_one(as_cd(pop_x), pop_S, mask, P, n, seed, g, p, cf, as_cd(new_x), new_S,
                   parents ? parents + 3 * p : nullptr);
@@ -825,6 +848,26 @@ extern "C" void orc_average(const double* pop_x, const uint8_t* pop_S, const uin
 }
 
 // Complexity Gamma (Eq. complexity) and density sum |sum rho|.
+// Average moduli for crossover averaging (App. "Crossover averaging"): M-dot = |F rho_avg|
+// of the average reconstruction (Eq. avgint1; rho_avg aligned onto individual `best` as in
+// Eq. avgrec), M-double-dot = mean_p |F rho_p| (Eq. avgint2); out = (M-dot + M-double-dot) / 2.
+extern "C" void orc_average_moduli(const double* pop_x, const uint8_t* pop_S, const uint8_t* mask,
+                                   int P, int n, int best, double* out) {
+  size_t nn = (size_t)n * n;
+  std::vector<cd> avg(nn);
+  std::vector<uint8_t> Savg(nn);
+  average(as_cd(pop_x), pop_S, mask, P, n, best, avg.data(), Savg.data());
+  fft2_inplace(avg.data(), n, 0);
+  std::vector<double> mdd(nn, 0.0);
+  std::vector<cd> X(nn);
+  for (int p = 0; p < P; p++) {
+    std::copy(as_cd(pop_x) + p * nn, as_cd(pop_x) + (p + 1) * nn, X.begin());
+    fft2_inplace(X.data(), n, 0);
+    for (size_t i = 0; i < nn; i++) mdd[i] += std::abs(X[i]);
+  }
+  for (size_t i = 0; i < nn; i++) out[i] = 0.5 * (std::abs(avg[i]) + mdd[i] / P);
+}
+
 static double complexity(const cd* x, int n, double* sum_abs) {
   cd s = 0;
   double a = 0.0;
@@ -937,6 +980,14 @@ struct orc_params {
   double init_gamma, init_phi_max;
   uint64_t seed;
   double ub_eta, ub_max_missing, ub_max_saturated;  // upper bounds (eta <= 0: off)
+  // schedule 0: the configs' blocks (iters_per_gen, sw_period, er_tail); schedule 1: the
+  // paper's Sequence of seq_ia IA + seq_er ER iterations repeated `repetitions` times, with
+  // seq_eval ER iterations of EvalSequence (App. "The algorithms sequence")
+  int schedule;
+  // mode 0: MPR (Alg. mpr); mode 1: independent reconstructions (Alg. randomsearch)
+  int mode;
+  int seq_ia, seq_er, seq_eval, repetitions;
+  double ca;  // crossover averaging C_a (App. "Crossover averaging"), 0 = off
 };
 
 struct orc_result {
@@ -956,9 +1007,54 @@ static long area(const uint8_t* S, size_t nn) {
   return a;
 }
 
+// Sequence lengths of generation g (App. "Changing values over generations", "The
+// algorithms sequence"): the IA count falls linearly from seq_ia to 0 and the ER count rises
+// from seq_er to seq_ia + seq_er over g = 1..G, each rounded to the nearest integer (halves
+// up), evaluated exactly in integers.
+static void sequence_counts(const orc_params& pr, int g, int G, int* ia, int* er) {
+  if (G <= 1) {
+    *ia = pr.seq_ia;
+    *er = pr.seq_er;
+    return;
+  }
+  const long den = 2L * (G - 1);
+  *ia = (int)((2L * pr.seq_ia * (G - g) + (G - 1)) / den);
+  *er = pr.seq_er + (int)((2L * pr.seq_ia * (g - 1) + (G - 1)) / den);
+}
+
+extern "C" void orc_sequence_counts(int seq_ia, int seq_er, int g, int G, int* out) {
+  orc_params pr{};
+  pr.seq_ia = seq_ia;
+  pr.seq_er = seq_er;
+  sequence_counts(pr, g, G, &out[0], &out[1]);
+}
+
+// Sequence (Eq. sequence): ia iterations of the IA (HIO or RAAR), then er of ER
+static void sequence(cd* x, const uint8_t* S, const double* M, const uint8_t* mask, const double* U,
+                     int n, const orc_params& pr, int ia, int er) {
+  iterate_one(x, S, M, mask, U, n, pr.algorithm, pr.beta, pr.chi, ia);
+  iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, er);
+}
+
 static void improve_one(cd* x, uint8_t* S, const double* M, const uint8_t* mask, const double* U,
                         int n, const orc_params& pr, double sigma, double tau, long a_best, long a_eval,
-                        double* err) {
+                        double* err, int g, int G) {
+  if (pr.schedule == 1) {  // Alg. improve with the paper's Sequence
+    int ia, er;
+    sequence_counts(pr, g, G, &ia, &er);
+    for (int r = 1; r <= pr.repetitions - 2; r++) {
+      sequence(x, S, M, mask, U, n, pr, ia, er);
+      update_support(x, S, n, sigma, tau);
+    }
+    sequence(x, S, M, mask, U, n, pr, ia, er);
+    update_support_size(x, S, n, sigma, a_best);
+    sequence(x, S, M, mask, U, n, pr, ia, er);
+    update_support_size(x, S, n, sigma, a_eval);
+    iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, pr.seq_eval);  // EvalSequence
+    *err = fourier_error(x, S, M, mask, n);
+    update_support(x, S, n, sigma, tau);
+    return;
+  }
   int K = pr.sw_period, R = pr.iters_per_gen / K;
   int last = pr.iters_per_gen - (R - 1) * K;
   int alg = pr.algorithm;
@@ -971,6 +1067,30 @@ static void improve_one(cd* x, uint8_t* S, const double* M, const uint8_t* mask,
   iterate_one(x, S, M, mask, U, n, alg, pr.beta, pr.chi, last - pr.er_tail);
   update_support_size(x, S, n, sigma, a_eval);
   iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, pr.er_tail);
+  *err = fourier_error(x, S, M, mask, n);
+  update_support(x, S, n, sigma, tau);
+}
+
+// Improve of the independent reconstructions (Alg. normalimprove): a Sequence and an
+// UpdateSupport per generation.  Schedule 0 splits the generation's iterations into blocks
+// of sw_period, each followed by UpdateSupport, the last er_tail iterations being ER.  The
+// error (Eq. error_calc) is taken after the last Sequence, before the last UpdateSupport.
+static void improve_independent(cd* x, uint8_t* S, const double* M, const uint8_t* mask,
+                                const double* U, int n, const orc_params& pr, double sigma,
+                                double tau, double* err, int g, int G) {
+  if (pr.schedule == 1) {
+    int ia, er;
+    sequence_counts(pr, g, G, &ia, &er);
+    sequence(x, S, M, mask, U, n, pr, ia, er);
+  } else {
+    int K = pr.sw_period, R = pr.iters_per_gen / K;
+    int last = pr.iters_per_gen - (R - 1) * K;
+    for (int blk = 1; blk < R; blk++) {
+      iterate_one(x, S, M, mask, U, n, pr.algorithm, pr.beta, pr.chi, K);
+      update_support(x, S, n, sigma, tau);
+    }
+    sequence(x, S, M, mask, U, n, pr, last - pr.er_tail, pr.er_tail);
+  }
   *err = fourier_error(x, S, M, mask, n);
   update_support(x, S, n, sigma, tau);
 }
@@ -991,11 +1111,20 @@ static void ifftshift2(const void* src, void* dst, int n, size_t esz) {
 extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const uint8_t* sat_c,
                                const uint8_t* S0, int n, const orc_params* prm, orc_result* res) {
   const orc_params& pr = *prm;
-  if (!valid_side(n) || pr.pop < 4 || pr.generations < 1 || pr.sw_period < 1) return 1;
-  int R = pr.iters_per_gen / pr.sw_period;
-  if (R < 2) return 1;
-  int last = pr.iters_per_gen - (R - 1) * pr.sw_period;
-  if (pr.er_tail < 0 || pr.er_tail > last) return 1;
+  if (!valid_side(n) || pr.pop < 4 || pr.generations < 1) return 1;
+  if (pr.mode != 0 && pr.mode != 1) return 1;
+  if (pr.schedule == 0) {
+    if (pr.sw_period < 1) return 1;
+    int R = pr.iters_per_gen / pr.sw_period;
+    if (R < 2) return 1;
+    int last = pr.iters_per_gen - (R - 1) * pr.sw_period;
+    if (pr.er_tail < 0 || pr.er_tail > last) return 1;
+  } else if (pr.schedule == 1) {
+    if (pr.repetitions < 2 || pr.seq_ia < 0 || pr.seq_er < 0 || pr.seq_eval < 0) return 1;
+    if (pr.seq_ia + pr.seq_er < 1) return 1;
+  } else {
+    return 1;
+  }
   size_t nn = (size_t)n * n;
   int P = pr.pop, G = pr.generations;
   std::vector<double> I(nn), M(nn);
@@ -1021,8 +1150,49 @@ extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const u
                  pr.init_phi_max, reinterpret_cast<double*>(px.data()));
   for (int p = 0; p < P; p++) std::copy(S0, S0 + nn, pS.begin() + p * nn);
   CrossCfg cf{pr.cw, pr.cp, pr.tile_min, pr.tile_max};
+  // per-generation monitors (Sec. "Monitoring the reconstruction process")
+  auto monitors = [&](int g, int repl) {
+    if (!res->gen_stats) return;
+    double* st = res->gen_stats + (size_t)(g - 1) * 8;
+    int b = argmin_first(pe);
+    double mn = 0.0, mx = pe[0], gam = 0.0, sm = 0.0;
+    for (int p = 0; p < P; p++) {
+      mn += pe[p];
+      mx = std::max(mx, pe[p]);
+      double s1;
+      gam += complexity(&px[p * nn], n, &s1);
+      sm += s1;
+    }
+    st[0] = pe[b];
+    st[1] = mn / P;
+    st[2] = mx;
+    st[3] = std::numeric_limits<double>::quiet_NaN();  // E(avg): final generation only
+    st[4] = (double)nn / (double)std::max(1L, area(&pS[b * nn], nn));
+    st[5] = (double)repl / P;
+    st[6] = gam / P;
+    st[7] = sm / P;
+  };
 
-  for (int g = 1; g <= G; g++) {
+  for (int g = 1; g <= G && pr.mode == 1; g++) {
+    // independent reconstructions (Alg. randomsearch): Improve only
+    double t = (G > 1) ? (double)(g - 1) / (double)(G - 1) : 0.0;
+    double sigma = pr.sw_sigma + (pr.sw_sigma_end - pr.sw_sigma) * t;
+    double tau = pr.sw_threshold + (pr.sw_threshold_end - pr.sw_threshold) * t;
+    parallel_for(P, [&](int p) {
+      improve_independent(&px[p * nn], &pS[p * nn], M.data(), mask.data(), Up, n, pr, sigma, tau, &pe[p], g, G);
+    });
+    monitors(g, 0);
+  }
+
+  std::vector<double> Mavg;
+  for (int g = 1; g <= G && pr.mode == 0; g++) {
+    if (pr.ca > 0.0) {  // the parents' average moduli for crossover averaging
+      Mavg.resize(nn);
+      orc_average_moduli(reinterpret_cast<const double*>(px.data()), pS.data(), mask.data(), P, n,
+                         argmin_first(pe), Mavg.data());
+      cf.ca = pr.ca;
+      cf.Mavg = Mavg.data();
+    }
     // Crossover (Alg. mpr): new population from the parents
     parallel_for(P, [&](int p) {
       crossover_one(px.data(), pS.data(), mask.data(), P, n, pr.seed, g, p, cf, nx.data(),
@@ -1049,7 +1219,7 @@ extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const u
       cd* x = old ? &px[p * nn] : &nx[p * nn];
       uint8_t* S = old ? &pS[p * nn] : &nS[p * nn];
       double* e = old ? &pe[p] : &ne[p];
-      improve_one(x, S, M.data(), mask.data(), Up, n, pr, sigma, tau, a_best, a_eval, e);
+      improve_one(x, S, M.data(), mask.data(), Up, n, pr, sigma, tau, a_best, a_eval, e, g, G);
     });
     // Select
     int repl = 0;
@@ -1060,26 +1230,7 @@ extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const u
         pe[p] = ne[p];
         repl++;
       }
-    if (res->gen_stats) {
-      double* st = res->gen_stats + (size_t)(g - 1) * 8;
-      int b = argmin_first(pe);
-      double mn = 0.0, mx = pe[0], gam = 0.0, sm = 0.0;
-      for (int p = 0; p < P; p++) {
-        mn += pe[p];
-        mx = std::max(mx, pe[p]);
-        double s;
-        gam += complexity(&px[p * nn], n, &s);
-        sm += s;
-      }
-      st[0] = pe[b];
-      st[1] = mn / P;
-      st[2] = mx;
-      st[3] = std::numeric_limits<double>::quiet_NaN();  // E(avg): final generation only
-      st[4] = (double)nn / (double)std::max(1L, area(&pS[b * nn], nn));
-      st[5] = (double)repl / P;
-      st[6] = gam / P;
-      st[7] = sm / P;
-    }
+    monitors(g, repl);
   }
   int b = argmin_first(pe);
   std::vector<cd> avg(nn);
@@ -1116,7 +1267,7 @@ extern "C" int orc_improve(double* x, uint8_t* S, const double* M, const uint8_t
   size_t nn = (size_t)n * n;
   parallel_for(batch, [&](int b) {
     improve_one(as_cd(x) + b * nn, S + b * nn, M, mask, nullptr, n, pr, sigma, tau, a_best, a_eval,
-                &err[b]);
+                &err[b], 1, 1);
   });
   return 0;
 }
