@@ -82,6 +82,20 @@ typedef struct {
   int precision;           /* 0: complex64 state; 1: FP16 storage of the state and FFT
                               intermediate inside iteration blocks, FP32 math (0) */
   int use_graph;           /* 1: capture the run in a CUDA graph before launching (0) */
+  int schedule;            /* 0: the blocks above (iters_per_gen, sw_period, er_tail);
+                              1: the paper's Sequence (App. "The algorithms sequence"): R
+                              repetitions of seq_ia IA + seq_er ER iterations, the IA count
+                              linear to 0 and the ER count to seq_ia + seq_er over the
+                              generations (halves rounded up), then seq_eval ER (0) */
+  int mode;                /* 0: MPR (Alg. mpr); 1: P independent reconstructions
+                              (Alg. randomsearch: Improve only, no crossover or selection;
+                              the result is the best and the aligned average) (0) */
+  int seq_ia;              /* schedule 1: starting IA iterations of a Sequence (40) */
+  int seq_er;              /* schedule 1: starting ER iterations of a Sequence (40) */
+  int seq_eval;            /* schedule 1: ER iterations of EvalSequence (40) */
+  int repetitions;         /* schedule 1: R >= 2 (3) */
+  float ca;                /* crossover averaging C_a in [0, 1] (App. "Crossover averaging",
+                              Eq. crossavg) (0) */
   uint64_t seed;           /* key of the counter-based generator (0) */
 } spring_params;
 
@@ -306,6 +320,21 @@ spring_status spring_reshift(const void* x, const uint8_t* S, const void* ref, c
  *   F x_new = F a' + cw (F b' - F c')  on the crossover map,  F x_p elsewhere;
  *   S_new = S_a' OR (S_b' AND S_c' AND S_p).
  * parents: DEVICE int32[P x 3] (output) or NULL. */
+/* a9 with crossover averaging (App. "Crossover averaging", Eq. crossavg): before the mix,
+ * parent a's Fourier moduli become ca * mavg + (1 - ca) |F a| with its phases kept (a zero
+ * modulus takes phase 0).  mavg: N x N float, DFT order, unitary scale (spring_average_moduli);
+ * ca in [0, 1]; ca = 0 is spring_crossover (mavg may then be NULL).  Scratch and errors as
+ * spring_crossover. */
+spring_status spring_crossover_ca(const void* pop_x, const uint8_t* pop_S, const float* M, int P, int n,
+                                  uint64_t seed, int g, float cw, float cp, int tile_min, int tile_max,
+                                  float ca, const float* mavg, void* new_x, uint8_t* new_S,
+                                  int32_t* parents, void* stream);
+/* The average moduli of crossover averaging: mavg = (|F rho_avg| + mean_p |F rho_p|) / 2
+ * (Eqs. avgint1, avgint2), rho_avg the population aligned onto its best individual
+ * (argmin of err; err NULL: individual 0) and averaged as in spring_average.  mavg: N x N
+ * float out, DFT order.  Scratch: (3P + 1) N^2 complex64. */
+spring_status spring_average_moduli(const void* pop_x, const uint8_t* pop_S, const double* err, const float* M,
+                                    int P, int n, float* mavg, void* stream);
 spring_status spring_crossover(const void* pop_x, const uint8_t* pop_S, const float* M, int P,
                                int n, uint64_t seed, int g, float cw, float cp, int tile_min,
                                int tile_max, void* new_x, uint8_t* new_S, int32_t* parents,

@@ -95,11 +95,15 @@ spring_status launch_peaks(int n, const float2* A, const float2* B, int npairs, 
 spring_status launch_apply_shift(int n, const float2* x, const uint8_t* S, const int32_t* ix,
                                  int npairs, const int32_t* info, const float2* phasor,
                                  float2* x_out, uint8_t* S_out, cudaStream_t s);
-// crossover mix in Fourier space (parents' alignment applied by the shift theorem)
+// crossover mix in Fourier space (parents' alignment applied by the shift theorem); with
+// ca > 0 parent a's moduli are blended towards mavg (Eq. crossavg)
 spring_status launch_crossover_mix(int n, const float2* Xpop, const int32_t* abc,
                                    const int32_t* info, const float2* phasor, int P, uint64_t seed,
-                                   int g, float cw, float cp, int tmin, int tmax, float2* Xnew,
-                                   cudaStream_t s);
+                                   int g, float cw, float cp, int tmin, int tmax, float ca,
+                                   const float* mavg, float2* Xnew, cudaStream_t s);
+// mavg = (|avg_spec| + mean_p |Xpop_p|) / 2 (Eqs. avgint1, avgint2; unitary spectra)
+spring_status launch_average_moduli(int n, const float2* Xpop, const float2* avg_spec, int P, float* mavg,
+                                    cudaStream_t s);
 spring_status launch_crossover_support(int n, const uint8_t* Spop, const int32_t* abc,
                                        const int32_t* info, int P, uint8_t* Snew, cudaStream_t s);
 spring_status launch_pairs_crossover(int P, const int32_t* abc, int32_t* ix, int32_t* ir,

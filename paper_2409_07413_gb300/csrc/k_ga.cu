@@ -298,7 +298,7 @@ __global__ void k_crossover_mix(const float2* __restrict__ X, const int32_t* __r
                                 const int32_t* __restrict__ info, const float2* __restrict__ phasor,
                                 MapCfg c, float cw, const long long* __restrict__ rc,
                                 const long long* __restrict__ rs, const float2* __restrict__ tw,
-                                float2* __restrict__ Xnew) {
+                                float ca, const float* __restrict__ mavg, float2* __restrict__ Xnew) {
   const int p = blockIdx.y, n = c.n;
   const long long nn = (long long)n * n;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -307,7 +307,12 @@ __global__ void k_crossover_mix(const float2* __restrict__ X, const int32_t* __r
   const MapGeom m = map_geometry(c, p);
   float2 out;
   if (map_elected(c, p, m, rc[m.k], rs[m.k], kr, kc)) {
-    const float2 A = aligned_spectrum(X, nn, n, abc[3 * p + 0], info + 9 * p + 0, phasor[3 * p + 0], tw, kr, kc, i);
+    float2 A = aligned_spectrum(X, nn, n, abc[3 * p + 0], info + 9 * p + 0, phasor[3 * p + 0], tw, kr, kc, i);
+    if (ca > 0.f) {  // Eq. crossavg: moduli towards the average ones, phases kept
+      const float a = sqrtf(A.x * A.x + A.y * A.y);
+      const float m = ca * mavg[i] + (1.f - ca) * a;
+      A = a > 0.f ? make_float2(A.x * (m / a), A.y * (m / a)) : make_float2(m, 0.f);
+    }
     const float2 B = aligned_spectrum(X, nn, n, abc[3 * p + 1], info + 9 * p + 3, phasor[3 * p + 1], tw, kr, kc, i);
     const float2 Cc = aligned_spectrum(X, nn, n, abc[3 * p + 2], info + 9 * p + 6, phasor[3 * p + 2], tw, kr, kc, i);
     out = make_float2(A.x + cw * (B.x - Cc.x), A.y + cw * (B.y - Cc.y));
@@ -319,8 +324,9 @@ __global__ void k_crossover_mix(const float2* __restrict__ X, const int32_t* __r
 
 spring_status launch_crossover_mix(int n, const float2* Xpop, const int32_t* abc,
                                    const int32_t* info, const float2* phasor, int P, uint64_t seed,
-                                   int g, float cw, float cp, int tmin, int tmax, float2* Xnew,
-                                   cudaStream_t s) {
+                                   int g, float cw, float cp, int tmin, int tmax, float ca,
+                                   const float* mavg, float2* Xnew, cudaStream_t s) {
+  if (ca > 0.f && !mavg) return invalid("crossover averaging needs the average moduli");
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
   if (tmin < 1) return invalid("tile_min must be >= 1");
@@ -328,9 +334,36 @@ spring_status launch_crossover_mix(int n, const float2* Xpop, const int32_t* abc
   const long long nn = (long long)n * n;
   launch_begin(SPRING_KC_OTHER, s);
   k_crossover_mix<<<dim3(div_up(nn, 256), P), 256, 0, s>>>(Xpop, abc, info, phasor, c, cw, tb.rot_cos,
-                                                           tb.rot_sin, tb.tw + tw_offset(n), Xnew);
+                                                           tb.rot_sin, tb.tw + tw_offset(n), ca, mavg,
+                                                           Xnew);
   SPRING_CHECK_LAUNCH();
   launch_end(SPRING_KC_OTHER, s, (double)P * nn * 40.0);
+  return SPRING_OK;
+}
+
+// per pixel: (|avg_spec| + mean_p |Xpop_p|) / 2, the sum over p in increasing order in FP32
+__global__ void k_average_moduli(const float2* __restrict__ X, const float2* __restrict__ avg, int P,
+                                 long long nn, float* __restrict__ mavg) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int p = 0; p < P; ++p) {
+      const float2 v = X[(long long)p * nn + i];
+      acc += sqrtf(v.x * v.x + v.y * v.y);
+    }
+    const float2 a = avg[i];
+    mavg[i] = 0.5f * (sqrtf(a.x * a.x + a.y * a.y) + acc / (float)P);
+  }
+}
+
+spring_status launch_average_moduli(int n, const float2* Xpop, const float2* avg_spec, int P, float* mavg,
+                                    cudaStream_t s) {
+  const long long nn = (long long)n * n;
+  launch_begin(SPRING_KC_OTHER, s);
+  k_average_moduli<<<(int)std::min<long long>(div_up(nn, 256), 8LL * sm_count()), 256, 0, s>>>(
+      Xpop, avg_spec, P, nn, mavg);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)nn * (8.0 * P + 12.0));
   return SPRING_OK;
 }
 

@@ -45,11 +45,21 @@ static spring_status validate_params(int n, const spring_params& p) {
   if (p.generations < 1) return invalid("generations must be >= 1");
   if (p.algorithm < 0 || p.algorithm > 2) return invalid("algorithm must be 0, 1 or 2");
   if (!(p.beta > 0.f && p.beta <= 1.f)) return invalid("beta must be in (0, 1]");
-  if (p.sw_period < 1) return invalid("sw_period must be >= 1");
-  const int R = p.iters_per_gen / p.sw_period;
-  if (R < 2) return invalid("iters_per_gen must be >= 2 * sw_period (R >= 2 repetitions)");
-  const int last = p.iters_per_gen - (R - 1) * p.sw_period;
-  if (p.er_tail < 0 || p.er_tail > last) return invalid("er_tail must be in [0, last block length]");
+  if (p.mode != 0 && p.mode != 1) return invalid("mode must be 0 (MPR) or 1 (independent reconstructions)");
+  if (p.schedule == 0) {
+    if (p.sw_period < 1) return invalid("sw_period must be >= 1");
+    const int R = p.iters_per_gen / p.sw_period;
+    if (R < 2) return invalid("iters_per_gen must be >= 2 * sw_period (R >= 2 repetitions)");
+    const int last = p.iters_per_gen - (R - 1) * p.sw_period;
+    if (p.er_tail < 0 || p.er_tail > last) return invalid("er_tail must be in [0, last block length]");
+  } else if (p.schedule == 1) {
+    if (p.repetitions < 2) return invalid("repetitions must be >= 2");
+    if (p.seq_ia < 0 || p.seq_er < 0 || p.seq_eval < 0) return invalid("sequence lengths must be >= 0");
+    if (p.seq_ia + p.seq_er < 1) return invalid("a Sequence needs at least one iteration");
+  } else {
+    return invalid("schedule must be 0 (blocks) or 1 (the paper's Sequence)");
+  }
+  if (!(p.ca >= 0.f && p.ca <= 1.f)) return invalid("ca must be in [0, 1]");
   if (!(p.sw_sigma >= 0.f && p.sw_sigma <= 64.f && p.sw_sigma_end >= 0.f && p.sw_sigma_end <= 64.f))
     return invalid("shrink-wrap sigma must be in [0, 64]");
   if (!(p.sw_threshold > 0.f && p.sw_threshold <= 1.f && p.sw_threshold_end > 0.f && p.sw_threshold_end <= 1.f))
@@ -67,7 +77,7 @@ static spring_status validate_params(int n, const spring_params& p) {
 // ------------------------------------------------------------------ device layout of a run
 struct Layout {
   size_t x, w, S, sm0, sm1, err, abc, ix, ir, info, best, ph, alpha, repl, dens, part_err,
-      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, total;
+      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, total;
 };
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -107,13 +117,16 @@ static Layout make_layout(int n, const spring_params& p) {
   L.status = take(sizeof(int) * 4);
   L.peaks = take(peaks_scratch_bytes(n, (int)P));
   L.init = take(init_scratch_bytes((int)P, p.init_n_spheres) + 128);
+  L.mavg = take(p.ca > 0.f ? sizeof(float) * nn : 0);
   L.total = o;
   return L;
 }
 
 class Run {
  public:
-  int n = 0, P = 0, B = 0, G = 0, R = 0, last = 0;
+  // B: image slots (both populations); NB: individuals improved per generation (B for MPR,
+  // P for independent reconstructions, which use the second half as scratch)
+  int n = 0, P = 0, B = 0, NB = 0, G = 0, R = 0, last = 0;
   spring_params prm{};
   const float* M = nullptr;
   const float* s16 = nullptr;  // FP16 storage scale of the problem (device scalar)
@@ -133,6 +146,7 @@ class Run {
   int64_t* alpha = nullptr;
   unsigned* imgmax = nullptr;
   int* status = nullptr;
+  float* mavg = nullptr;  // crossover averaging: (M-dot + M-double-dot) / 2
   void *peaks = nullptr, *init_sc = nullptr;
   bool z_valid = false;
   // precision 1: the iteration blocks keep x and w as half2 inside the w buffer
@@ -152,9 +166,14 @@ class Run {
     prm = p;
     P = p.pop;
     B = 2 * P;
+    NB = p.mode == 1 ? P : B;
     G = p.generations;
-    R = p.iters_per_gen / p.sw_period;
-    last = p.iters_per_gen - (R - 1) * p.sw_period;
+    if (p.schedule == 1) {
+      R = p.repetitions;
+    } else {
+      R = p.iters_per_gen / p.sw_period;
+      last = p.iters_per_gen - (R - 1) * p.sw_period;
+    }
     M = prob->M;
     s16 = prob->s16;
     S0 = prob->S0;
@@ -198,6 +217,7 @@ class Run {
     status = reinterpret_cast<int*>(mem + L.status);
     peaks = mem + L.peaks;
     init_sc = mem + L.init;
+    mavg = p.ca > 0.f ? reinterpret_cast<float*>(mem + L.mavg) : nullptr;
     return SPRING_OK;
   }
 
@@ -208,7 +228,7 @@ class Run {
   // bring the FP32 state up to date with the FP16 iteration state
   spring_status sync_x() {
     if (x16_newer) {
-      SPRING_TRY(launch_half_to_float(xh(), x, (long long)B * nn(), s16, s));
+      SPRING_TRY(launch_half_to_float(xh(), x, (long long)NB * nn(), s16, s));
       x16_newer = false;
     }
     return SPRING_OK;
@@ -243,14 +263,27 @@ class Run {
     return launch_peaks(n, x_new(), w_new(), P, pinfo, pph, peaks, s);
   }
 
+  // Crossover averaging (App. "Crossover averaging"): the parents' average moduli
+  // (|F rho_avg| + mean_p |F rho_p|) / 2 into mavg, with rho_avg the population aligned onto
+  // its best individual (Eq. avgrec).  Needs the population spectra in w_pop.
+  spring_status average_moduli(int g) {
+    SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, best, s));
+    SPRING_TRY(launch_pairs_onto_best(P, best, ix, ir, s));
+    SPRING_TRY(align(ix, ir, info, ph));
+    SPRING_TRY(launch_average(n, x_pop(), S_pop(), info, ph, best, P, avg, Savg, s));
+    SPRING_TRY(fft2_unitary(n, -1, avg, avg, nullptr, 1, s));
+    return launch_average_moduli(n, w_pop(), avg, P, mavg, s);
+  }
+
   // Crossover (Alg. crossover)
   spring_status crossover(int g) {
     SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
+    if (prm.ca > 0.f) SPRING_TRY(average_moduli(g));
     SPRING_TRY(launch_random_choice(prm.seed, g, P, abc, s));
     SPRING_TRY(launch_pairs_crossover(P, abc, ix, ir, s));
     for (int c = 0; c < 3; ++c) SPRING_TRY(align(ix + c * P, ir + c * P, info + 3 * c * P, ph + c * P));
     SPRING_TRY(launch_crossover_mix(n, w_pop(), abc, info, ph, P, prm.seed, g, prm.cw, prm.cp,
-                                    prm.tile_min, prm.tile_max, x_new(), s));
+                                    prm.tile_min, prm.tile_max, prm.ca, mavg, x_new(), s));
     SPRING_TRY(fft2_unitary(n, +1, x_new(), x_new(), nullptr, P, s));
     SPRING_TRY(launch_crossover_support(n, S_pop(), abc, info, P, S_new(), s));
     z_valid = z16_valid = false;
@@ -261,51 +294,110 @@ class Run {
     if (k <= 0) return SPRING_OK;
     if (fp16) {
       if (!z16_valid) {
-        SPRING_TRY(launch_row_init16(n, x, xh(), wh(), B, s16, s));
+        SPRING_TRY(launch_row_init16(n, x, xh(), wh(), NB, s16, s));
         z16_valid = true;
       }
       for (int it = 0; it < k; ++it) {
-        SPRING_TRY(launch_col_pm16(n, wh(), M, B, s16, s));
-        SPRING_TRY(launch_row_iter16(n, alg, wh(), xh(), S, B, prm.beta, prm.chi, s16, s));
+        SPRING_TRY(launch_col_pm16(n, wh(), M, NB, s16, s));
+        SPRING_TRY(launch_row_iter16(n, alg, wh(), xh(), S, NB, prm.beta, prm.chi, s16, s));
       }
       x16_newer = true;
       return SPRING_OK;
     }
     if (iteration_path(n) == 1) {  // on chip: x in, x out; w is left stale
-      SPRING_TRY(launch_cluster_iter(n, alg, x, S, M, B, prm.beta, prm.chi, k, s));
+      SPRING_TRY(launch_cluster_iter(n, alg, x, S, M, NB, prm.beta, prm.chi, k, s));
       z_valid = false;
       return SPRING_OK;
     }
     if (!z_valid) {
-      SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, B, 1.0f, s));
+      SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, NB, 1.0f, s));
       z_valid = true;
     }
     for (int it = 0; it < k; ++it) {
-      SPRING_TRY(launch_col_pm(n, w, M, B, s));
-      SPRING_TRY(launch_row_iter(n, alg, w, x, S, B, prm.beta, prm.chi, true, s));
+      SPRING_TRY(launch_col_pm(n, w, M, NB, s));
+      SPRING_TRY(launch_row_iter(n, alg, w, x, S, NB, prm.beta, prm.chi, true, s));
     }
     return SPRING_OK;
   }
 
   spring_status shrinkwrap(float sigma, float tau) {
     SPRING_TRY(sync_x());
-    SPRING_TRY(launch_smooth(n, x, sm0, sm1, B, sigma, imgmax, s));
-    return launch_threshold(n, sm1, imgmax, tau, S, B, s);
+    SPRING_TRY(launch_smooth(n, x, sm0, sm1, NB, sigma, imgmax, s));
+    return launch_threshold(n, sm1, imgmax, tau, S, NB, s);
   }
 
   spring_status shrinkwrap_area(float sigma, const int64_t* a) {
     SPRING_TRY(sync_x());
-    SPRING_TRY(launch_smooth(n, x, sm0, sm1, B, sigma, nullptr, s));
-    return launch_select_area(n, sm1, a, 0, S, B, s);
+    SPRING_TRY(launch_smooth(n, x, sm0, sm1, NB, sigma, nullptr, s));
+    return launch_select_area(n, sm1, a, 0, S, NB, s);
   }
 
   spring_status errors() {
     SPRING_TRY(sync_x());
-    SPRING_TRY(launch_row_fft(n, -1, x, w, S, B, 1.0f, s));
-    SPRING_TRY(launch_col_err(n, w, M, B, part_err, s));
-    SPRING_TRY(launch_err_finalize(n, part_err, B, err, status, s));
+    SPRING_TRY(launch_row_fft(n, -1, x, w, S, NB, 1.0f, s));
+    SPRING_TRY(launch_col_err(n, w, M, NB, part_err, s));
+    SPRING_TRY(launch_err_finalize(n, part_err, NB, err, status, s));
     z_valid = z16_valid = false;  // w served as scratch
     return SPRING_OK;
+  }
+
+  // Sequence lengths of generation g for schedule 1 (App. "Changing values over
+  // generations"): IA count linear from seq_ia to 0, ER count from seq_er to
+  // seq_ia + seq_er, each rounded to the nearest integer with halves up (exact integers)
+  void sequence_counts(int g, int* ia, int* er) const {
+    if (G <= 1) {
+      *ia = prm.seq_ia;
+      *er = prm.seq_er;
+      return;
+    }
+    const long long den = 2LL * (G - 1);
+    *ia = (int)((2LL * prm.seq_ia * (G - g) + (G - 1)) / den);
+    *er = prm.seq_er + (int)((2LL * prm.seq_ia * (g - 1) + (G - 1)) / den);
+  }
+
+  // Sequence (Eq. sequence): ia iterations of the IA, then er of ER
+  spring_status sequence(int ia, int er) {
+    SPRING_TRY(iterations(prm.algorithm, ia));
+    return iterations(0, er);
+  }
+
+  // Improve (Alg. improve) of both populations with the paper's Sequence
+  spring_status improve_paper(int g, float sigma, float tau) {
+    int ia = 0, er = 0;
+    sequence_counts(g, &ia, &er);
+    for (int r = 1; r <= R - 2; ++r) {
+      SPRING_TRY(sequence(ia, er));
+      SPRING_TRY(shrinkwrap(sigma, tau));
+    }
+    SPRING_TRY(sequence(ia, er));
+    SPRING_TRY(shrinkwrap_area(sigma, alpha + 0));  // UpdateSupportSize(alpha_best)
+    SPRING_TRY(sequence(ia, er));
+    SPRING_TRY(shrinkwrap_area(sigma, alpha + 2));  // UpdateSupportSize(alpha_eval)
+    SPRING_TRY(iterations(0, prm.seq_eval));        // EvalSequence: ER
+    SPRING_TRY(errors());                           // GetError
+    SPRING_TRY(shrinkwrap(sigma, tau));
+    return sync_x();
+  }
+
+  // Improve of independent reconstructions (Alg. normalimprove): one Sequence and one
+  // UpdateSupport per generation (schedule 0: blocks of sw_period, each followed by
+  // UpdateSupport, the last er_tail iterations ER); the error is taken before the last
+  // UpdateSupport
+  spring_status improve_independent(int g, float sigma, float tau) {
+    if (prm.schedule == 1) {
+      int ia = 0, er = 0;
+      sequence_counts(g, &ia, &er);
+      SPRING_TRY(sequence(ia, er));
+    } else {
+      for (int blk = 1; blk < R; ++blk) {
+        SPRING_TRY(iterations(prm.algorithm, prm.sw_period));
+        SPRING_TRY(shrinkwrap(sigma, tau));
+      }
+      SPRING_TRY(sequence(last - prm.er_tail, prm.er_tail));
+    }
+    SPRING_TRY(errors());
+    SPRING_TRY(shrinkwrap(sigma, tau));
+    return sync_x();
   }
 
   // Improve (Alg. improve) of both populations at once
@@ -332,10 +424,19 @@ class Run {
     const double t = G > 1 ? (double)(g - 1) / (double)(G - 1) : 0.0;
     const float sigma = (float)(prm.sw_sigma + (prm.sw_sigma_end - prm.sw_sigma) * t);
     const float tau = (float)(prm.sw_threshold + (prm.sw_threshold_end - prm.sw_threshold) * t);
+    if (prm.mode == 1) {  // independent reconstructions (Alg. randomsearch)
+      SPRING_TRY(improve_independent(g, sigma, tau));
+      SPRING_CUDA(cudaMemsetAsync(repl, 0, P, s));
+      SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
+      return launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s);
+    }
     SPRING_TRY(crossover(g));
     SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, best, s));
     SPRING_TRY(launch_area_stats(n, S_pop(), best, P, g, G, alpha, s));
-    SPRING_TRY(improve(sigma, tau));
+    if (prm.schedule == 1)
+      SPRING_TRY(improve_paper(g, sigma, tau));
+    else
+      SPRING_TRY(improve(sigma, tau));
     SPRING_TRY(launch_select(n, x_pop(), S_pop(), err_pop(), x_new(), S_new(), err_new(), P, repl, s));
     SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
     SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s));
@@ -618,6 +719,13 @@ void spring_params_default(spring_params* p) {
   p->init_phi_max = 0.0f;
   p->precision = 0;
   p->use_graph = 0;
+  p->schedule = 0;
+  p->mode = 0;
+  p->seq_ia = 40;
+  p->seq_er = 40;
+  p->seq_eval = 40;
+  p->repetitions = 3;
+  p->ca = 0.0f;
   p->seed = 0;
 }
 

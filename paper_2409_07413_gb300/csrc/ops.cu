@@ -546,9 +546,19 @@ spring_status spring_reshift(const void* x, const uint8_t* S, const void* ref, c
 spring_status spring_crossover(const void* pop_x, const uint8_t* pop_S, const float* M, int P, int n,
                                uint64_t seed, int g, float cw, float cp, int tile_min, int tile_max,
                                void* new_x, uint8_t* new_S, int32_t* parents, void* stream) {
+  return spring_crossover_ca(pop_x, pop_S, M, P, n, seed, g, cw, cp, tile_min, tile_max, 0.0f, nullptr,
+                             new_x, new_S, parents, stream);
+}
+
+spring_status spring_crossover_ca(const void* pop_x, const uint8_t* pop_S, const float* M, int P, int n,
+                                  uint64_t seed, int g, float cw, float cp, int tile_min, int tile_max,
+                                  float ca, const float* mavg, void* new_x, uint8_t* new_S, int32_t* parents,
+                                  void* stream) {
   SPRING_TRY(check_n(n, P));
   if (P < 4) return invalid("population must be >= 4");
   if (!pop_x || !pop_S || !M || !new_x || !new_S) return invalid("null pointer");
+  if (!(ca >= 0.f && ca <= 1.f)) return invalid("ca must be in [0, 1]");
+  if (ca > 0.f && !mavg) return invalid("crossover averaging needs the average moduli");
   cudaStream_t s = ST(stream);
   const size_t nn = (size_t)n * n;
   Scratch w;
@@ -569,7 +579,7 @@ spring_status spring_crossover(const void* pop_x, const uint8_t* pop_S, const fl
   for (int c = 0; c < 3; ++c)
     SPRING_TRY(align_pairs(n, X, ix + c * P, ir + c * P, P, M, A, B, inf + 3 * c * P, ph + c * P, s));
   float2* nx = static_cast<float2*>(new_x);
-  SPRING_TRY(launch_crossover_mix(n, X, abc, inf, ph, P, seed, g, cw, cp, tile_min, tile_max, nx, s));
+  SPRING_TRY(launch_crossover_mix(n, X, abc, inf, ph, P, seed, g, cw, cp, tile_min, tile_max, ca, mavg, nx, s));
   SPRING_TRY(fft2_unitary(n, +1, nx, nx, nullptr, P, s));
   SPRING_TRY(launch_crossover_support(n, pop_S, abc, inf, P, new_S, s));
   if (parents) SPRING_CUDA(cudaMemcpyAsync(parents, abc, sizeof(int32_t) * Q, cudaMemcpyDeviceToDevice, s));
@@ -584,6 +594,34 @@ spring_status spring_select(void* pop_x, uint8_t* pop_S, double* pop_err, const 
   if (!pop_x || !pop_S || !pop_err || !new_x || !new_S || !new_err) return invalid("null pointer");
   return launch_select(n, static_cast<float2*>(pop_x), pop_S, pop_err, static_cast<const float2*>(new_x),
                        new_S, new_err, P, replaced, ST(stream));
+}
+
+spring_status spring_average_moduli(const void* pop_x, const uint8_t* pop_S, const double* err, const float* M,
+                                    int P, int n, float* mavg, void* stream) {
+  SPRING_TRY(check_n(n, P));
+  if (P < 1 || !pop_x || !pop_S || !M || !mavg) return invalid("null pointer or empty population");
+  cudaStream_t s = ST(stream);
+  const size_t nn = (size_t)n * n;
+  Scratch w;
+  SPRING_TRY(w.alloc(sizeof(float2) * nn * (3 * (size_t)P + 1) + nn + sizeof(int32_t) * (6 * P + 4) +
+                         sizeof(float2) * P + 64, s));
+  float2* X = w.as<float2>();
+  float2* A = X + P * nn;
+  float2* B = A + P * nn;
+  float2* avg = B + P * nn;
+  uint8_t* Savg = reinterpret_cast<uint8_t*>(avg + nn);
+  int32_t* ix = reinterpret_cast<int32_t*>(Savg + nn + (4 - nn % 4) % 4);
+  int32_t* ir = ix + P;
+  int32_t* inf = ir + P;
+  int32_t* best = inf + 3 * P;
+  float2* ph = reinterpret_cast<float2*>(best + 2 + (P & 1));
+  SPRING_TRY(fft2_unitary(n, -1, static_cast<const float2*>(pop_x), X, nullptr, P, s));
+  SPRING_TRY(launch_argmin(err, P, best, s));
+  SPRING_TRY(launch_pairs_onto_best(P, best, ix, ir, s));
+  SPRING_TRY(align_pairs(n, X, ix, ir, P, M, A, B, inf, ph, s));
+  SPRING_TRY(launch_average(n, static_cast<const float2*>(pop_x), pop_S, inf, ph, best, P, avg, Savg, s));
+  SPRING_TRY(fft2_unitary(n, -1, avg, avg, nullptr, 1, s));
+  return launch_average_moduli(n, X, avg, P, mavg, s);
 }
 
 spring_status spring_average(const void* pop_x, const uint8_t* pop_S, const double* err, const float* M,

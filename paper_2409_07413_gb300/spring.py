@@ -30,7 +30,9 @@ class Params(C.Structure):
         ("sw_period", C.c_int), ("er_tail", C.c_int), ("chi", C.c_float), ("cw", C.c_float),
         ("cp", C.c_float), ("tile_min", C.c_int), ("tile_max", C.c_int),
         ("init_n_spheres", C.c_int), ("init_gamma", C.c_float), ("init_phi_max", C.c_float),
-        ("precision", C.c_int), ("use_graph", C.c_int), ("seed", C.c_uint64),
+        ("precision", C.c_int), ("use_graph", C.c_int), ("schedule", C.c_int), ("mode", C.c_int),
+        ("seq_ia", C.c_int), ("seq_er", C.c_int), ("seq_eval", C.c_int), ("repetitions", C.c_int),
+        ("ca", C.c_float), ("seed", C.c_uint64),
     ]
 
 
@@ -88,6 +90,8 @@ _SIGS = {
     "spring_crossover_map": (_i, [_u64, _i, _i, _i, _i, _i, _f, _vp, _vp]),
     "spring_reshift": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "spring_crossover": (_i, [_vp, _vp, _vp, _i, _i, _u64, _i, _f, _f, _i, _i, _vp, _vp, _vp, _vp]),
+    "spring_crossover_ca": (_i, [_vp, _vp, _vp, _i, _i, _u64, _i, _f, _f, _i, _i, _f, _vp, _vp, _vp, _vp, _vp]),
+    "spring_average_moduli": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp]),
     "spring_select": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp]),
     "spring_average": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "spring_initialize": (_i, [_u64, _vp, _vp, _i, _i, _i, _f, _f, _vp, _vp]),
@@ -370,6 +374,30 @@ def spring_crossover(pop_x, pop_S, M, seed, g, cw=0.4, cp=0.6, tile_min=4, tile_
           float(cw), float(cp), int(tile_min), int(tile_max), _ptr(nx), _ptr(nS), _ptr(par),
           _stream())
     return nx, nS, par
+
+
+def spring_crossover_ca(pop_x, pop_S, M, seed, g, ca, mavg, cw=0.4, cp=0.6, tile_min=4, tile_max=0):
+    import torch
+    _need(pop_x, torch.complex64, "pop_x")
+    _need(pop_S, torch.uint8, "pop_S")
+    P, n = pop_x.shape[0], pop_x.shape[-1]
+    nx = torch.empty_like(pop_x)
+    nS = torch.empty_like(pop_S)
+    par = torch.empty((P, 3), dtype=torch.int32, device=pop_x.device)
+    _call("spring_crossover_ca", _ptr(pop_x), _ptr(pop_S), _ptr(M), P, n, C.c_uint64(seed), int(g),
+          float(cw), float(cp), int(tile_min), int(tile_max), float(ca),
+          _ptr(mavg) if mavg is not None else None, _ptr(nx), _ptr(nS), _ptr(par), _stream())
+    return nx, nS, par
+
+
+def spring_average_moduli(pop_x, pop_S, err, M):
+    import torch
+    _need(pop_x, torch.complex64, "pop_x")
+    P, n = pop_x.shape[0], pop_x.shape[-1]
+    out = torch.empty((n, n), dtype=torch.float32, device=pop_x.device)
+    _call("spring_average_moduli", _ptr(pop_x), _ptr(pop_S), _ptr(err) if err is not None else None,
+          _ptr(M), P, n, _ptr(out), _stream())
+    return out
 
 
 def spring_select(pop_x, pop_S, pop_err, new_x, new_S, new_err):
