@@ -96,6 +96,8 @@ typedef struct {
   int repetitions;         /* schedule 1: R >= 2 (3) */
   float ca;                /* crossover averaging C_a in [0, 1] (App. "Crossover averaging",
                               Eq. crossavg) (0) */
+  int monitor_avg;         /* 1: the average reconstruction and its error E(avg) every
+                              generation (gen_stats column 3), not only at the end (0) */
   uint64_t seed;           /* key of the counter-based generator (0) */
 } spring_params;
 
@@ -178,6 +180,27 @@ size_t spring_footprint_bytes(int n, const spring_params* p);
  * Average.  Results go to the caller's buffers in *out.
  * Errors: INVALID (parameters), NOMEM (budget), CUDA, NUMERIC. */
 spring_status spring_mpr_run(spring_problem* prob, const spring_params* p, spring_result* out);
+
+/* Checkpoint / resume.  The population state of a run after `generation` completed
+ * generations: P images (caller-owned host buffers, P x N x N complex64, P x N x N uint8,
+ * P doubles; errors are +inf before the first generation's evaluation). */
+typedef struct {
+  int generation;
+  float* pop_x;
+  uint8_t* pop_S;
+  double* pop_err;
+} spring_population;
+/* Initialize and run generations 1..g_stop (1 <= g_stop <= p->generations) of the run that
+ * spring_mpr_run would make with the same parameters, then copy its population to *save
+ * (save->generation = g_stop).  Blocking.  Errors: as spring_mpr_run. */
+spring_status spring_mpr_run_until(spring_problem* prob, const spring_params* p, int g_stop,
+                                   spring_population* save);
+/* Continue a run from a saved population: generations from->generation + 1 .. G, then the
+ * average, into *out (gen_stats rows of the skipped generations are NaN).  With the same
+ * problem and parameters the result equals spring_mpr_run's bit for bit (every random
+ * draw is keyed by the generation).  INVALID if from->generation is not in [0, G). */
+spring_status spring_mpr_resume(spring_problem* prob, const spring_params* p, const spring_population* from,
+                                spring_result* out);
 
 /* Serving: queue a run; requests are admitted in arrival order while their footprint fits
  * the HBM budget and fewer than SPRING_MAX_ACTIVE (environment, default 2) are running;

@@ -55,6 +55,7 @@ class OrcParams(C.Structure):
         ("ub_eta", C.c_double), ("ub_max_missing", C.c_double), ("ub_max_saturated", C.c_double),
         ("schedule", C.c_int), ("mode", C.c_int), ("seq_ia", C.c_int), ("seq_er", C.c_int),
         ("seq_eval", C.c_int), ("repetitions", C.c_int), ("ca", C.c_double),
+        ("monitor_avg", C.c_int),
     ]
 
 
@@ -397,7 +398,8 @@ DEFAULTS = dict(pop=8, iters_per_gen=100, generations=5, algorithm=2, beta=0.9,
                 sw_period=20, er_tail=10, chi=0.5, cw=0.4, cp=0.6, tile_min=4, tile_max=0,
                 init_n_spheres=5, init_gamma=1.0, init_phi_max=0.0, seed=0,
                 ub_eta=0.0, ub_max_missing=0.2, ub_max_saturated=0.05,
-                schedule=0, mode=0, seq_ia=40, seq_er=40, seq_eval=40, repetitions=3, ca=0.0)
+                schedule=0, mode=0, seq_ia=40, seq_er=40, seq_eval=40, repetitions=3, ca=0.0,
+                monitor_avg=0)
 
 
 def make_params(**kw) -> OrcParams:

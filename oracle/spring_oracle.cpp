@@ -988,6 +988,7 @@ struct orc_params {
   int mode;
   int seq_ia, seq_er, seq_eval, repetitions;
   double ca;  // crossover averaging C_a (App. "Crossover averaging"), 0 = off
+  int monitor_avg;  // 1: the average reconstruction's error every generation
 };
 
 struct orc_result {
@@ -1166,7 +1167,13 @@ extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const u
     st[0] = pe[b];
     st[1] = mn / P;
     st[2] = mx;
-    st[3] = std::numeric_limits<double>::quiet_NaN();  // E(avg): final generation only
+    st[3] = std::numeric_limits<double>::quiet_NaN();  // E(avg): final generation (below)
+    if (pr.monitor_avg && g < G) {  // Sec. "Monitoring the reconstruction process"
+      std::vector<cd> av(nn);
+      std::vector<uint8_t> Sv(nn);
+      average(px.data(), pS.data(), mask.data(), P, n, b, av.data(), Sv.data());
+      st[3] = fourier_error(av.data(), Sv.data(), M.data(), mask.data(), n);
+    }
     st[4] = (double)nn / (double)std::max(1L, area(&pS[b * nn], nn));
     st[5] = (double)repl / P;
     st[6] = gam / P;

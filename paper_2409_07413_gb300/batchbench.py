@@ -1,0 +1,85 @@
+"""Batched uneven workload: many patterns of different sides reconstructed together.
+
+    python -m paper_2409_07413_gb300.batchbench [--patterns 256] [--generations 5]
+
+Patterns: sides drawn uniformly from {128, 192, 256, 512}; objects, masks and noise as the
+`ellN` recipe (extent 0.25 N, 1e6-1e7 photons, beamstop, gap, saturation); P = 32 each,
+G generations x 200 RAAR iterations.  Two ways to run the same set:
+
+  served: every pattern submitted at once (spring_submit); the scheduler runs several
+          populations of different sides concurrently on prioritised streams, advancing
+          each a generation at a time (continuous batching);
+  plain:  spring_mpr_run one pattern after another.
+
+Reports reconstructions/s and iteration-pixels/s of each (makespan of the whole set) and
+the mean final error; both see identical requests and seeds, so the errors agree exactly.
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+SIDES = (128, 192, 256, 512)
+
+
+def make_set(seed, count, variants=4):
+    from paper_2409_07413_gb300 import synthetic
+    rng = np.random.default_rng(seed)
+    sides = rng.choice(SIDES, size=count)
+    cache = {}
+    out = []
+    for i, n in enumerate(sides):
+        key = (int(n), i % variants)
+        if key not in cache:
+            cache[key] = synthetic.config_pattern(f"ell{int(n)}", key[1])
+        out.append((int(n), cache[key], 500 + i))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--patterns", type=int, default=256)
+    ap.add_argument("--generations", type=int, default=5)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--modes", default="served,plain")
+    a = ap.parse_args()
+    import torch  # noqa: F401  (device selection through the library)
+    from paper_2409_07413_gb300 import spring
+    prm = dict(pop=32, iters_per_gen=200, generations=a.generations, algorithm=2, beta=0.9,
+               sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)
+    jobs = make_set(a.seed, a.patterns)
+    ctx = spring.Context(0)
+    for n in SIDES:  # tune each side once, outside the timed region
+        spring.autotune(n, 2 * prm["pop"])
+    work_px = sum(2 * prm["pop"] * prm["iters_per_gen"] * prm["generations"] * n * n for n, _, _ in jobs)
+    out = {"benchmark": "batched uneven", "patterns": len(jobs),
+           "sides": {str(n): int(sum(1 for j in jobs if j[0] == n)) for n in SIDES}, "params": prm,
+           "iteration_pixels": work_px}
+    for mode in a.modes.split(","):
+        probs = [ctx.problem(p.intensities, p.mask, p.support0) for _, p, _ in jobs]
+        torch.cuda.synchronize()
+        errs = []
+        t0 = time.perf_counter()
+        if mode == "served":
+            tickets = [pr.submit(spring.params(**prm, seed=sd)) for pr, (_, _, sd) in zip(probs, jobs)]
+            for t in tickets:
+                st, r = ctx.poll(t, -1, want_arrays=False)
+                errs.append(r["final_error_best"])
+        else:
+            for pr, (_, _, sd) in zip(probs, jobs):
+                errs.append(pr.run(spring.params(**prm, seed=sd), want_arrays=False)["final_error_best"])
+        span = time.perf_counter() - t0
+        for pr in probs:
+            pr.destroy()
+        out[mode] = {"seconds": span, "reconstructions_per_s": len(jobs) / span,
+                     "iteration_pixels_per_s": work_px / span, "mean_final_error_best": float(np.mean(errs))}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -270,7 +270,9 @@ __device__ __forceinline__ void stage_tw(float2 (&b)[E], int t, const float2* __
 // ------------------------------------------------------------------ the transform
 // v: E registers of thread t (element t + m T).  sm: this transform's exchange buffer
 // (with STRIDE between consecutive elements).  tw: table of e^{-2 pi i k / N}.
-template <class P, int DIR, bool PAD, int STRIDE, class Sync>
+// TAIL = false leaves out the barrier after the last shared-memory read: for callers that
+// synchronise themselves before the buffer is written again, or never write it again.
+template <class P, int DIR, bool PAD, int STRIDE, bool TAIL = true, class Sync>
 __device__ __forceinline__ void fft_plan(float2 (&v)[P::E], float2* sm, int t,
                                          const float2* __restrict__ tw, const Sync& sync) {
   constexpr int N = P::N, E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2;
@@ -285,7 +287,7 @@ __device__ __forceinline__ void fft_plan(float2 (&v)[P::E], float2* sm, int t,
   sync();
   // stage 1 (NS = R0)
   stage_load<N, E, R1, R0, 1, PAD, STRIDE>(b, sm, t);
-  sync();
+  if (TAIL || R2 != 0) sync();
   stage_tw<N, E, R1, R0, DIR>(b, t, tw);
   stage_dft<N, E, R1, DIR>(b);
   if constexpr (R2 == 0) {
@@ -297,7 +299,7 @@ __device__ __forceinline__ void fft_plan(float2 (&v)[P::E], float2* sm, int t,
     stage_store<N, E, R1, R0, PAD, STRIDE>(b, sm, t);
     sync();
     stage_load<N, E, R2, R0 * R1, R0, PAD, STRIDE>(b, sm, t);
-    sync();
+    if (TAIL) sync();
     stage_tw<N, E, R2, R0 * R1, DIR>(b, t, tw);
     stage_dft<N, E, R2, DIR>(b);
 #pragma unroll

@@ -303,12 +303,13 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = ld_st(base, (long long)(t + m * T) * N, iws);
   if constexpr (MODE == COL_INV) {
-    fft_plan<P, +1, false, W>(v, smem + c, t, a.tw, sync);
+    fft_plan<P, +1, false, W, false>(v, smem + c, t, a.tw, sync);  // no shared-memory use after it
 #pragma unroll
     for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * N] = cscale(v[m], a.scale);
     return;
   }
-  fft_plan<P, -1, false, W>(v, smem + c, t, a.tw, sync);
+  // PM / ERR: the barrier after the strip's cp.async wait also ends the transform's reads
+  fft_plan<P, -1, false, W, MODE == COL_FWD>(v, smem + c, t, a.tw, sync);
   if constexpr (MODE == COL_FWD) {
 #pragma unroll
     for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * N] = cscale(v[m], a.scale);
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
       const float2 X = v[m];
       v[m] = pm_value(X, Mv, inv_n);
     }
-    fft_plan<P, +1, false, W>(v, smem + c, t, a.tw, sync);
+    fft_plan<P, +1, false, W, false>(v, smem + c, t, a.tw, sync);  // no shared-memory use after it
 #pragma unroll
     for (int m = 0; m < E; ++m) st_st(base, (long long)(t + m * T) * N, v[m], ws);
   } else {  // COL_ERR: FP64 accumulation of the Fourier error (Eq. error_calc)

@@ -10,6 +10,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <limits>
 #include <condition_variable>
 #include <cstdlib>
 #include <cstring>
@@ -135,6 +136,9 @@ class Run {
   char* mem = nullptr;
   Layout L{};
   int next_gen = 1;  // generation to enqueue next (G + 1: finish; G + 2: done)
+  int stop_after = 0;    // > 0: stop after this generation (no average)
+  bool resumed = false;  // the population was uploaded (checkpoint): no Initialize
+  int first_gen = 1;     // first generation this run executes
 
   float2 *x = nullptr, *w = nullptr, *avg = nullptr;
   uint8_t *S = nullptr, *repl = nullptr, *Savg = nullptr;
@@ -428,7 +432,8 @@ class Run {
       SPRING_TRY(improve_independent(g, sigma, tau));
       SPRING_CUDA(cudaMemsetAsync(repl, 0, P, s));
       SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
-      return launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s);
+      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s));
+      return monitor(g);
     }
     SPRING_TRY(crossover(g));
     SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, best, s));
@@ -440,11 +445,21 @@ class Run {
     SPRING_TRY(launch_select(n, x_pop(), S_pop(), err_pop(), x_new(), S_new(), err_new(), P, repl, s));
     SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
     SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s));
+    return monitor(g);
+  }
+
+  // the average reconstruction's error every generation (gen_stats column 3)
+  spring_status monitor(int g) {
+    if (!prm.monitor_avg || g == G) return SPRING_OK;  // generation G: finish() computes it
+    SPRING_TRY(average_and_error());
+    SPRING_CUDA(cudaMemcpyAsync(stats + 8 * (g - 1) + 3, err_avg, sizeof(double), cudaMemcpyDeviceToDevice, s));
     return SPRING_OK;
   }
 
   // Average (Eq. avgrec) of the final population and its error
-  spring_status finish() {
+  spring_status finish() { return average_and_error(); }
+
+  spring_status average_and_error() {
     SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
     SPRING_TRY(launch_argmin(err_pop(), P, best, s));
     SPRING_TRY(launch_pairs_onto_best(P, best, ix, ir, s));
@@ -456,11 +471,39 @@ class Run {
     return SPRING_OK;
   }
 
+  // checkpoint: the population after generation g0 (host buffers), uploaded before any
+  // other work of the run; the run continues at generation g0 + 1
+  spring_status upload_population(const spring_population& from) {
+    SPRING_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * 4, s));
+    SPRING_CUDA(cudaMemcpyAsync(x_pop(), from.pop_x, sizeof(float2) * P * nn(), cudaMemcpyHostToDevice, s));
+    SPRING_CUDA(cudaMemcpyAsync(S_pop(), from.pop_S, (size_t)P * nn(), cudaMemcpyHostToDevice, s));
+    SPRING_CUDA(cudaMemcpyAsync(err_pop(), from.pop_err, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+    SPRING_CUDA(cudaStreamSynchronize(s));
+    next_gen = from.generation + 1;
+    first_gen = next_gen;
+    resumed = true;
+    z_valid = z16_valid = x16_newer = false;
+    return SPRING_OK;
+  }
+
+  // after the stream has completed: the population to host buffers
+  spring_status download_population(spring_population* to) {
+    SPRING_CUDA(cudaMemcpy(to->pop_x, x_pop(), sizeof(float2) * P * nn(), cudaMemcpyDeviceToHost));
+    SPRING_CUDA(cudaMemcpy(to->pop_S, S_pop(), (size_t)P * nn(), cudaMemcpyDeviceToHost));
+    SPRING_CUDA(cudaMemcpy(to->pop_err, err_pop(), sizeof(double) * P, cudaMemcpyDeviceToHost));
+    to->generation = next_gen - 1;
+    return SPRING_OK;
+  }
+
   // enqueue the next chunk of work: init with generation 1, then one generation per call,
   // then the average; returns true when nothing is left
   spring_status step(bool* done) {
     *done = false;
-    if (next_gen == 1) SPRING_TRY(enqueue_init());
+    if (next_gen == 1 && !resumed) SPRING_TRY(enqueue_init());
+    if (stop_after > 0 && next_gen > stop_after) {
+      *done = true;
+      return SPRING_OK;
+    }
     if (next_gen <= G) {
       SPRING_TRY(generation(next_gen));
       ++next_gen;
@@ -500,6 +543,8 @@ class Run {
     if (out->gen_stats) {
       SPRING_CUDA(cudaMemcpy(out->gen_stats, stats, sizeof(double) * 8 * G, cudaMemcpyDeviceToHost));
       out->gen_stats[8 * (G - 1) + 3] = ea;
+      for (int g = 1; g < first_gen; ++g)  // generations run before a resume
+        for (int k = 0; k < 8; ++k) out->gen_stats[8 * (g - 1) + k] = std::numeric_limits<double>::quiet_NaN();
     }
     if (st[0]) {
       set_error("non-finite Fourier error in the run");
@@ -726,6 +771,7 @@ void spring_params_default(spring_params* p) {
   p->seq_eval = 40;
   p->repetitions = 3;
   p->ca = 0.0f;
+  p->monitor_avg = 0;
   p->seed = 0;
 }
 
@@ -899,8 +945,10 @@ spring_status spring_problem_destroy(spring_problem* pr) {
   return SPRING_OK;
 }
 
-spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_result* out) {
-  if (!pr || !p || !out) return invalid("null argument");
+// A blocking run: from Initialize (from = NULL) or from a saved population, up to
+// generation stop (0 = all, then the average into *out), saving the population if asked.
+static spring_status run_blocking(spring_problem* pr, const spring_params* p, const spring_population* from,
+                                  int stop, spring_population* save, spring_result* out) {
   SPRING_TRY(validate_params(pr->n, *p));
   spring_ctx* c = pr->ctx;
   SPRING_CUDA(cudaSetDevice(c->device));
@@ -919,6 +967,8 @@ spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__);
     if (st == SPRING_OK) st = run.setup(pr, *p, s);
+    if (st == SPRING_OK && from) st = run.upload_population(*from);
+    run.stop_after = stop;
     if (st == SPRING_OK) {
       if (p->use_graph) {
         cudaGraph_t graph = nullptr;
@@ -952,7 +1002,8 @@ spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_
         }
       }
     }
-    if (st == SPRING_OK) {
+    if (st == SPRING_OK && save) st = run.download_population(save);
+    if (st == SPRING_OK && out) {
       out->t_submit_s = out->t_admit_s = now_s();
       st = run.collect(out);
       out->t_done_s = now_s();
@@ -966,6 +1017,27 @@ spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_
   std::lock_guard<std::mutex> lk(c->mu);
   c->used -= fp;
   return st;
+}
+
+spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_result* out) {
+  if (!pr || !p || !out) return invalid("null argument");
+  return run_blocking(pr, p, nullptr, 0, nullptr, out);
+}
+
+spring_status spring_mpr_run_until(spring_problem* pr, const spring_params* p, int g_stop,
+                                   spring_population* save) {
+  if (!pr || !p || !save || !save->pop_x || !save->pop_S || !save->pop_err) return invalid("null argument");
+  if (g_stop < 1 || g_stop > p->generations) return invalid("g_stop must be in [1, generations]");
+  return run_blocking(pr, p, nullptr, g_stop, save, nullptr);
+}
+
+spring_status spring_mpr_resume(spring_problem* pr, const spring_params* p, const spring_population* from,
+                                spring_result* out) {
+  if (!pr || !p || !from || !out || !from->pop_x || !from->pop_S || !from->pop_err)
+    return invalid("null argument");
+  if (from->generation < 0 || from->generation >= p->generations)
+    return invalid("the saved generation must be in [0, generations)");
+  return run_blocking(pr, p, from, 0, nullptr, out);
 }
 
 spring_status spring_submit(spring_ctx* c, spring_problem* pr, const spring_params* p, uint64_t* ticket) {

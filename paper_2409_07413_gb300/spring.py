@@ -32,7 +32,7 @@ class Params(C.Structure):
         ("init_n_spheres", C.c_int), ("init_gamma", C.c_float), ("init_phi_max", C.c_float),
         ("precision", C.c_int), ("use_graph", C.c_int), ("schedule", C.c_int), ("mode", C.c_int),
         ("seq_ia", C.c_int), ("seq_er", C.c_int), ("seq_eval", C.c_int), ("repetitions", C.c_int),
-        ("ca", C.c_float), ("seed", C.c_uint64),
+        ("ca", C.c_float), ("monitor_avg", C.c_int), ("seed", C.c_uint64),
     ]
 
 
@@ -43,6 +43,11 @@ class Result(C.Structure):
         ("final_error_best", C.c_double), ("t_submit_s", C.c_double), ("t_admit_s", C.c_double),
         ("t_done_s", C.c_double),
     ]
+
+
+class Population(C.Structure):
+    _fields_ = [("generation", C.c_int), ("pop_x", C.c_void_p), ("pop_S", C.c_void_p),
+                ("pop_err", C.c_void_p)]
 
 
 class Bounds(C.Structure):
@@ -73,6 +78,8 @@ _SIGS = {
     "spring_footprint_bytes": (C.c_size_t, [_i, C.POINTER(Params)]),
     "spring_mpr_run": (_i, [_vp, C.POINTER(Params), C.POINTER(Result)]),
     "spring_submit": (_i, [_vp, _vp, C.POINTER(Params), C.POINTER(_u64)]),
+    "spring_mpr_run_until": (_i, [_vp, C.POINTER(Params), _i, C.POINTER(Population)]),
+    "spring_mpr_resume": (_i, [_vp, C.POINTER(Params), C.POINTER(Population), C.POINTER(Result)]),
     "spring_poll": (_i, [_vp, _u64, _i, C.POINTER(Result)]),
     "spring_cancel": (_i, [_vp, _u64]),
     "spring_fft2": (_i, [_vp, _i, _i, _i, _vp]),
@@ -559,6 +566,28 @@ class Problem:
         """Blocking MPR run; returns a dict with the result arrays and errors."""
         r, keep = _result_buffers(self.n if want_arrays else None, p.generations)
         _call("spring_mpr_run", self.handle, C.byref(p), C.byref(r))
+        return _result_dict(r, keep)
+
+    def run_until(self, p: Params, g_stop: int):
+        """Checkpoint: Initialize and generations 1..g_stop; returns the population state."""
+        import numpy as np
+        P, n = p.pop, self.n
+        st = {"pop_x": np.empty((P, n, n), np.complex64), "pop_S": np.empty((P, n, n), np.uint8),
+              "pop_err": np.empty(P, np.float64)}
+        pop = Population(0, st["pop_x"].ctypes.data, st["pop_S"].ctypes.data, st["pop_err"].ctypes.data)
+        _call("spring_mpr_run_until", self.handle, C.byref(p), int(g_stop), C.byref(pop))
+        st["generation"] = pop.generation
+        return st
+
+    def resume(self, p: Params, state, want_arrays=True):
+        """Continue from a state returned by run_until; returns the result dict."""
+        import numpy as np
+        x = np.ascontiguousarray(state["pop_x"], np.complex64)
+        S = np.ascontiguousarray(state["pop_S"], np.uint8)
+        e = np.ascontiguousarray(state["pop_err"], np.float64)
+        pop = Population(int(state["generation"]), x.ctypes.data, S.ctypes.data, e.ctypes.data)
+        r, keep = _result_buffers(self.n if want_arrays else None, p.generations)
+        _call("spring_mpr_resume", self.handle, C.byref(p), C.byref(pop), C.byref(r))
         return _result_dict(r, keep)
 
     def submit(self, p: Params) -> int:

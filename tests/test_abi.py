@@ -73,7 +73,7 @@ int main(void) {
   F(spring_params, pop) F(spring_params, beta) F(spring_params, sw_period) F(spring_params, chi)
   F(spring_params, tile_min) F(spring_params, init_gamma) F(spring_params, precision)
   F(spring_params, use_graph) F(spring_params, schedule) F(spring_params, repetitions)
-  F(spring_params, ca) F(spring_params, seed)
+  F(spring_params, ca) F(spring_params, monitor_avg) F(spring_params, seed)
   F(spring_result, gen_stats) F(spring_result, final_error_avg) F(spring_result, t_done_s)
   F(spring_kernel_stat, total_ms) F(spring_kernel_stat, bytes_per_launch)
   F(spring_bounds, eta) F(spring_bounds, max_missing) F(spring_bounds, max_saturated)

@@ -142,3 +142,17 @@ def test_mpr_with_crossover_averaging_runs(orc):
     b = orc.mpr_run(pat.intensities, pat.mask, pat.support0, ca=0.2, **kw)
     assert np.isfinite(b["gen_stats"][:, [0, 1, 2]]).all()
     assert a["final_error_best"] != b["final_error_best"]  # the averaging takes part
+
+
+def test_monitor_average_every_generation(orc):
+    # monitoring the average reconstruction does not change the run; its error is finite
+    # every generation and the last one is the final average's error
+    pat = synthetic.config_pattern("sphere64", 6)
+    kw = dict(KW, generations=3, iters_per_gen=40, sw_period=20, er_tail=5)
+    a = orc.mpr_run(pat.intensities, pat.mask, pat.support0, **kw)
+    b = orc.mpr_run(pat.intensities, pat.mask, pat.support0, monitor_avg=1, **kw)
+    assert np.array_equal(a["rho_avg"], b["rho_avg"])
+    assert np.isfinite(b["gen_stats"][:, 3]).all()
+    assert np.isnan(a["gen_stats"][:-1, 3]).all()
+    assert b["gen_stats"][-1, 3] == b["final_error_avg"]
+    assert (b["gen_stats"][:, 3] >= 0).all() and (b["gen_stats"][:, 3] <= 2).all()
