@@ -184,10 +184,16 @@ __device__ __forceinline__ void stage_twiddle(float2 (&b)[E], int t, const float
     // powers by binary decomposition from table entries W^1, W^2, W^4, ...
     float2 pw[6];
     int np = 0;
+    // W^1 from the table, W^2, W^4, ... by squaring (one load per butterfly: the exchange
+    // traffic already keeps the load/store pipe busy)
+    {
+      float2 w = __ldg(&tw[k1 % N]);
+      w = DIR < 0 ? w : cconj(w);
 #pragma unroll
-    for (int q = 1; q < R; q <<= 1) {
-      float2 w = __ldg(&tw[(k1 * q) % N]);
-      pw[np++] = DIR < 0 ? w : cconj(w);
+      for (int q = 1; q < R; q <<= 1) {
+        pw[np++] = w;
+        w = cmul(w, w);
+      }
     }
 #pragma unroll
     for (int r = 1; r < R; ++r) {
