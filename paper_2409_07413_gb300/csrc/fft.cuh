@@ -37,10 +37,25 @@ __host__ __device__ constexpr double cos32(int k) {
 }
 __host__ __device__ constexpr double sin32(int k) { return cos32(k - 8); }
 
+// Two complex values moved and transformed together: a thread that owns two adjacent
+// columns carries both through one transform, so every load, store and exchange is a
+// 16-byte access.  Arithmetic is lane-wise (each half exactly as a float2 would be).
+struct __align__(16) cpair {
+  float2 a, b;
+};
+__device__ __forceinline__ cpair cadd(cpair x, cpair y) { return {cadd(x.a, y.a), cadd(x.b, y.b)}; }
+__device__ __forceinline__ cpair csub(cpair x, cpair y) { return {csub(x.a, y.a), csub(x.b, y.b)}; }
+__device__ __forceinline__ cpair cmul(cpair x, float2 w) { return {cmul(x.a, w), cmul(x.b, w)}; }
+__device__ __forceinline__ cpair cscale(cpair x, float s) { return {cscale(x.a, s), cscale(x.b, s)}; }
+
 // a * (DIR i)
 template <int DIR>
 __device__ __forceinline__ float2 rot90(float2 a) {
   return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+template <int DIR>
+__device__ __forceinline__ cpair rot90(cpair x) {
+  return {rot90<DIR>(x.a), rot90<DIR>(x.b)};
 }
 
 // a * W_R^k with W_R = e^{DIR 2 pi i / R}, R | 32, constant-folded special cases.
@@ -65,12 +80,23 @@ __device__ __forceinline__ float2 twc(float2 a) {
     return make_float2(c * a.x - s * a.y, c * a.y + s * a.x);
   }
 }
+template <int R, int K, int DIR>
+__device__ __forceinline__ cpair twc(cpair x) {
+  return {twc<R, K, DIR>(x.a), twc<R, K, DIR>(x.b)};
+}
+
+// v0 - t / 2 (radix 3)
+__device__ __forceinline__ float2 sub_half(float2 v0, float2 t) {
+  return make_float2(v0.x - 0.5f * t.x, v0.y - 0.5f * t.y);
+}
+__device__ __forceinline__ cpair sub_half(cpair v0, cpair t) { return {sub_half(v0.a, t.a), sub_half(v0.b, t.b)}; }
 
 // In-place radix-R DFT of v[0..R), natural order in and out.
 template <int R, int DIR>
 struct DFT {
-  __device__ __forceinline__ static void run(float2* v) {
-    float2 e[R / 2], o[R / 2];
+  template <class V>
+  __device__ __forceinline__ static void run(V* v) {
+    V e[R / 2], o[R / 2];
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
       e[k] = v[2 * k];
@@ -80,11 +106,10 @@ struct DFT {
     DFT<R / 2, DIR>::run(o);
     combine(v, e, o, std::integral_constant<int, 0>());
   }
-  template <int K>
-  __device__ __forceinline__ static void combine(float2* v, const float2* e, const float2* o,
-                                                 std::integral_constant<int, K>) {
+  template <int K, class V>
+  __device__ __forceinline__ static void combine(V* v, const V* e, const V* o, std::integral_constant<int, K>) {
     if constexpr (K < R / 2) {
-      float2 t = twc<R, K, DIR>(o[K]);
+      V t = twc<R, K, DIR>(o[K]);
       v[K] = cadd(e[K], t);
       v[K + R / 2] = csub(e[K], t);
       combine(v, e, o, std::integral_constant<int, K + 1>());
@@ -93,21 +118,24 @@ struct DFT {
 };
 template <int DIR>
 struct DFT<1, DIR> {
-  __device__ __forceinline__ static void run(float2*) {}
+  template <class V>
+  __device__ __forceinline__ static void run(V*) {}
 };
 template <int DIR>
 struct DFT<2, DIR> {
-  __device__ __forceinline__ static void run(float2* v) {
-    float2 a = v[0];
+  template <class V>
+  __device__ __forceinline__ static void run(V* v) {
+    V a = v[0];
     v[0] = cadd(a, v[1]);
     v[1] = csub(a, v[1]);
   }
 };
 template <int DIR>
 struct DFT<4, DIR> {
-  __device__ __forceinline__ static void run(float2* v) {
-    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    float2 t2 = cadd(v[1], v[3]), t3 = rot90<DIR>(csub(v[1], v[3]));
+  template <class V>
+  __device__ __forceinline__ static void run(V* v) {
+    V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    V t2 = cadd(v[1], v[3]), t3 = rot90<DIR>(csub(v[1], v[3]));
     v[0] = cadd(t0, t2);
     v[2] = csub(t0, t2);
     v[1] = cadd(t1, t3);
@@ -116,11 +144,12 @@ struct DFT<4, DIR> {
 };
 template <int DIR>
 struct DFT<3, DIR> {
-  __device__ __forceinline__ static void run(float2* v) {
+  template <class V>
+  __device__ __forceinline__ static void run(V* v) {
     constexpr float h3 = 0.86602540378443864676f;  // sqrt(3) / 2
-    float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
-    float2 m = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
-    float2 r = cscale(rot90<DIR>(t2), h3);
+    V t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+    V m = sub_half(v[0], t1);
+    V r = cscale(rot90<DIR>(t2), h3);
     v[0] = cadd(v[0], t1);
     v[1] = cadd(m, r);
     v[2] = csub(m, r);
@@ -173,8 +202,8 @@ __host__ __device__ constexpr int pad_elems() { return pad_elems_p<Plan<N>>(); }
 
 // ------------------------------------------------------------------ stage helpers
 // twiddle multiplications of a stage: input r of butterfly u times W_{NS R}^{(j mod NS) r}
-template <int N, int E, int R, int NS, int DIR>
-__device__ __forceinline__ void stage_twiddle(float2 (&b)[E], int t, const float2* __restrict__ tw) {
+template <int N, int E, int R, int NS, int DIR, class V>
+__device__ __forceinline__ void stage_twiddle(V (&b)[E], int t, const float2* __restrict__ tw) {
   constexpr int T = N / E;
   constexpr int STEP = N / (NS * R);  // table index of W_{NS R}^{1}
 #pragma unroll
@@ -211,8 +240,8 @@ __device__ __forceinline__ void stage_twiddle(float2 (&b)[E], int t, const float
 }
 
 // radix-3 stages (N = 192 only) use direct table loads
-template <int N, int E, int NS, int DIR>
-__device__ __forceinline__ void stage_twiddle3(float2 (&b)[E], int t, const float2* __restrict__ tw) {
+template <int N, int E, int NS, int DIR, class V>
+__device__ __forceinline__ void stage_twiddle3(V (&b)[E], int t, const float2* __restrict__ tw) {
   constexpr int T = N / E, R = 3, STEP = N / (NS * R);
 #pragma unroll
   for (int u = 0; u < E / R; ++u) {
@@ -232,8 +261,8 @@ __device__ __forceinline__ int xlayout(int i) {
 }
 
 // write the outputs of a stage (radix R, NS) in the exchange layout
-template <int N, int E, int R, int NS, bool PAD, int STRIDE>
-__device__ __forceinline__ void stage_store(const float2 (&b)[E], float2* sm, int t) {
+template <int N, int E, int R, int NS, bool PAD, int STRIDE, class V>
+__device__ __forceinline__ void stage_store(const V (&b)[E], V* sm, int t) {
   constexpr int T = N / E;
 #pragma unroll
   for (int u = 0; u < E / R; ++u) {
@@ -246,8 +275,8 @@ __device__ __forceinline__ void stage_store(const float2 (&b)[E], float2* sm, in
 
 // read the inputs of a stage of radix R from the layout of the previous stage (groups L,
 // padding PADN)
-template <int N, int E, int R, int L, int PADN, bool PAD, int STRIDE>
-__device__ __forceinline__ void stage_load(float2 (&b)[E], const float2* sm, int t) {
+template <int N, int E, int R, int L, int PADN, bool PAD, int STRIDE, class V>
+__device__ __forceinline__ void stage_load(V (&b)[E], const V* sm, int t) {
   constexpr int T = N / E;
 #pragma unroll
   for (int u = 0; u < E / R; ++u) {
@@ -257,14 +286,14 @@ __device__ __forceinline__ void stage_load(float2 (&b)[E], const float2* sm, int
   }
 }
 
-template <int N, int E, int R, int DIR>
-__device__ __forceinline__ void stage_dft(float2 (&b)[E]) {
+template <int N, int E, int R, int DIR, class V>
+__device__ __forceinline__ void stage_dft(V (&b)[E]) {
 #pragma unroll
   for (int u = 0; u < E / R; ++u) DFT<R, DIR>::run(&b[u * R]);
 }
 
-template <int N, int E, int R, int NS, int DIR>
-__device__ __forceinline__ void stage_tw(float2 (&b)[E], int t, const float2* __restrict__ tw) {
+template <int N, int E, int R, int NS, int DIR, class V>
+__device__ __forceinline__ void stage_tw(V (&b)[E], int t, const float2* __restrict__ tw) {
   if constexpr (NS > 1) {
     if constexpr (R == 3)
       stage_twiddle3<N, E, NS, DIR>(b, t, tw);
@@ -278,11 +307,11 @@ __device__ __forceinline__ void stage_tw(float2 (&b)[E], int t, const float2* __
 // (with STRIDE between consecutive elements).  tw: table of e^{-2 pi i k / N}.
 // TAIL = false leaves out the barrier after the last shared-memory read: for callers that
 // synchronise themselves before the buffer is written again, or never write it again.
-template <class P, int DIR, bool PAD, int STRIDE, bool TAIL = true, class Sync>
-__device__ __forceinline__ void fft_plan(float2 (&v)[P::E], float2* sm, int t,
-                                         const float2* __restrict__ tw, const Sync& sync) {
+template <class P, int DIR, bool PAD, int STRIDE, bool TAIL = true, class Sync, class V>
+__device__ __forceinline__ void fft_plan(V (&v)[P::E], V* sm, int t, const float2* __restrict__ tw,
+                                         const Sync& sync) {
   constexpr int N = P::N, E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2;
-  float2 b[E];
+  V b[E];
   // stage 0 (NS = 1): inputs j + r N/R0 are the registers u + r E/R0
 #pragma unroll
   for (int u = 0; u < E / R0; ++u)

@@ -28,7 +28,9 @@
 //           4 / 5 = persistent blocks fed by TMA: while a block transforms one tile, the
 //           next tile is already being copied into a second shared buffer (16 / 8 columns);
 //           6 / 7 = transposed tiles, one lane group per column (16 / 32 columns; 8 at
-//           N >= 1024 / 512)
+//           N >= 1024 / 512); 8 / 9 = two adjacent columns per thread (16-byte accesses
+//           throughout), 16 / 32-column tiles, plans of at most 8 elements per thread
+//           (16 at N = 1024)
 #pragma once
 
 #include <cuda_fp16.h>
@@ -48,7 +50,7 @@ enum { OP_ROW_ITER = 0, OP_ROW_FWD, OP_ROW_INV, OP_COL_PM, OP_COL_FWD, OP_COL_IN
 
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_VARIANTS = 7;
-constexpr int COL_VARIANTS = 8;
+constexpr int COL_VARIANTS = 10;
 constexpr int ERR_W = 16;  // column tile of the error pass (layout of its partial sums)
 
 // alternative column-pass plans
@@ -59,6 +61,15 @@ template <> struct AltPlan<192>  : PlanT<192, 24, 3, 8, 8> {};
 template <> struct AltPlan<256>  : PlanT<256, 32, 32, 8> {};
 template <> struct AltPlan<512>  : PlanT<512, 8, 8, 8, 8> {};
 template <> struct AltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
+
+// plans of the paired column pass (two columns per thread, E <= 16)
+template <int N> struct Col2Plan;
+template <> struct Col2Plan<64>   : PlanT<64, 8, 8, 8> {};
+template <> struct Col2Plan<128>  : PlanT<128, 8, 8, 4, 4> {};
+template <> struct Col2Plan<192>  : PlanT<192, 24, 8, 8, 3> {};
+template <> struct Col2Plan<256>  : PlanT<256, 8, 8, 8, 4> {};
+template <> struct Col2Plan<512>  : PlanT<512, 8, 8, 8, 8> {};
+template <> struct Col2Plan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
 // alternative row-pass plans (fewer elements per thread; T = 64 rows sync by named barrier)
 template <int N> struct RowAltPlan : Plan<N> {};
@@ -376,6 +387,46 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
 template <class P>
 __host__ __device__ constexpr int colt_stride() { return pad_elems_p<P>() | 1; }
 
+// Column pass with two adjacent columns per thread (cpair values): the column loads and
+// stores, the modulus reads and every shared-memory exchange move 16 bytes at a time, which
+// halves the load/store instructions of k_col<COL_PM>; the arithmetic per column is the
+// same as k_col's for the same plan.
+template <class P, int W>
+__global__ void __launch_bounds__((W / 2) * P::T, ((W / 2) * P::T <= 512 ? 2 : 1)) k_col2(ColArgs a) {
+  constexpr int N = P::N, E = P::E, T = P::T, WP = W / 2, STRIPS = N / W;
+  extern __shared__ __align__(16) float2 smem2[];
+  cpair* tile = reinterpret_cast<cpair*>(smem2);
+  float* Ms = reinterpret_cast<float*>(smem2 + (size_t)N * W);
+  const int cp = threadIdx.x % WP, t = threadIdx.x / WP;
+  const int img = blockIdx.x / STRIPS, strip = blockIdx.x % STRIPS;
+  cpair* base = reinterpret_cast<cpair*>(a.data + (size_t)img * N * N + strip * W) + cp;
+  const BlockSync sync;
+  {
+    constexpr int CH = W / 4;  // 16-byte chunks per row of the strip
+    for (int k = threadIdx.x; k < N * CH; k += blockDim.x) {
+      const int row = k / CH, q = k % CH;
+      cp_async16(Ms + row * W + 4 * q, a.M + (size_t)row * N + strip * W + 4 * q);
+    }
+    cp_async_commit();
+  }
+  cpair v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = base[(size_t)(t + m * T) * (N / 2)];
+  fft_plan<P, -1, false, WP, false>(v, tile + cp, t, a.tw, sync);
+  cp_async_wait_all();
+  sync();  // also ends the transform's shared-memory reads
+  constexpr float inv_n = 1.0f / N;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const float2 mv = *reinterpret_cast<const float2*>(Ms + (t + m * T) * W + 2 * cp);
+    v[m].a = pm_value(v[m].a, mv.x, inv_n);
+    v[m].b = pm_value(v[m].b, mv.y, inv_n);
+  }
+  fft_plan<P, +1, false, WP, false>(v, tile + cp, t, a.tw, sync);
+#pragma unroll
+  for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * (N / 2)] = v[m];
+}
+
 template <class P, int W>
 __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_colT(ColArgs a) {
   constexpr int N = P::N, E = P::E, T = P::T, STRIPS = N / W, RS = colt_stride<P>(), MS = N + 1;
@@ -551,6 +602,23 @@ constexpr int fit_w() {  // keep the column tile within shared memory and 1024 t
   return ((size_t)N * W * 8 > 200 * 1024 || W * Plan<N>::T > 1024) ? W / 2 : W;
 }
 
+template <int N, int W>
+constexpr int fit_w2() {  // paired tile: shared memory and at most 1024 threads
+  return ((size_t)N * W * 12 > 216 * 1024 || (W / 2) * Col2Plan<N>::T > 1024) ? W / 2 : W;
+}
+
+template <class P, int W>
+inline spring_status col2_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
+  const size_t smem = (size_t)P::N * W * (sizeof(float2) + sizeof(float));
+  if (prepare_only) return allow_smem(k_col2<P, W>, smem);
+  if (op.ca.batch < 1) return SPRING_OK;
+  launch_begin(op.kclass, s);
+  k_col2<P, W><<<op.ca.batch * (P::N / W), (W / 2) * P::T, smem, s>>>(op.ca);
+  SPRING_CHECK_LAUNCH();
+  launch_end(op.kclass, s, op.bytes);
+  return SPRING_OK;
+}
+
 template <class P, int W, int MODE, class ST = float2>
 inline spring_status col_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
   const size_t smem = (size_t)P::N * W * sizeof(float2) +
@@ -619,8 +687,14 @@ inline spring_status col_variant(const FftOp& op, cudaStream_t s, bool prep) {
     case 6:
       if constexpr (MODE == COL_PM) return colT_launch<Plan<N>, (N >= 1024 ? 8 : 16)>(op, s, prep);
       return col_launch<Plan<N>, 16, MODE>(op, s, prep);
-    default:
+    case 7:
       if constexpr (MODE == COL_PM) return colT_launch<Plan<N>, (N >= 512 ? 8 : 32)>(op, s, prep);
+      return col_launch<Plan<N>, 16, MODE>(op, s, prep);
+    case 8:
+      if constexpr (MODE == COL_PM) return col2_launch<Col2Plan<N>, 16>(op, s, prep);
+      return col_launch<Plan<N>, 16, MODE>(op, s, prep);
+    default:
+      if constexpr (MODE == COL_PM) return col2_launch<Col2Plan<N>, fit_w2<N, 32>()>(op, s, prep);
       return col_launch<Plan<N>, 16, MODE>(op, s, prep);
   }
 }

@@ -74,7 +74,7 @@ def sweep(n, batch, iters, alg):
     res = []
     try:
         for rv in range(7):
-            for cv in range(8):
+            for cv in range(10):
                 spring.set_kernel_variant(n, rv, cv)
                 r = run(n, batch, iters, alg)
                 r["variant"] = [rv, cv]

@@ -122,7 +122,7 @@ def test_bounded_projection_in_every_column_variant(sp, n):
     ref = oracle.iterate(c64(x), S, M, mask, 2, 0.9, 1.0, 1, U=U)
     saved = sp.get_kernel_variant(n)
     try:
-        for cv in range(8):
+        for cv in range(10):
             sp.set_kernel_variant(n, saved[0], cv)
             xg = dev(c64(x))
             sp.spring_iterate(xg, dev(S), dev(enc), 2, 0.9, 1.0, 1)
