@@ -81,6 +81,118 @@ __global__ void __launch_bounds__(256) k_smooth_cols(const float* __restrict__ t
   }
 }
 
+// Radius-specialised passes (r = R <= 8, i.e. sigma <= 2): taps in registers and a sliding
+// window, so each output costs 2R+1 FMAs and about one shared-memory read.  The sum of each
+// output runs over d = 0..2R in the same order as in the general kernels (same bits).
+constexpr int SW_RK = 4;  // row outputs per thread
+
+template <int R>
+__global__ void __launch_bounds__(256) k_smooth_rows_r(const float2* __restrict__ x, float* __restrict__ tmp,
+                                                       int n, long long nrows, const Taps taps) {
+  extern __shared__ float ext_r[];  // rows_per_block x (n + 2R)
+  const int tpr = n / SW_RK;                   // threads per row
+  const int rpb = blockDim.x / tpr;            // rows per block
+  const int lr = threadIdx.x / tpr, lt = threadIdx.x % tpr;
+  const long long row = (long long)blockIdx.x * rpb + lr;
+  const int len = n + 2 * R;
+  float* ext = ext_r + lr * len;
+  float w[2 * R + 1];
+#pragma unroll
+  for (int d = 0; d <= 2 * R; ++d) w[d] = taps.w[d];
+  if (row < nrows) {
+    const long long row0 = row * n;
+    for (int k = lt; k < len; k += tpr) {
+      int c = k - R;
+      c %= n;
+      if (c < 0) c += n;
+      const float2 v = __ldg(&x[row0 + c]);
+      ext[k] = sqrtf(v.x * v.x + v.y * v.y);
+    }
+  }
+  __syncthreads();
+  if (row >= nrows || lr >= rpb) return;
+  const int c0 = lt * SW_RK;
+  float win[SW_RK + 2 * R];
+#pragma unroll
+  for (int k = 0; k < SW_RK + 2 * R; ++k) win[k] = ext[c0 + k];
+  float4 o;
+  float* op = &o.x;
+#pragma unroll
+  for (int j = 0; j < SW_RK; ++j) {
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) acc = fmaf(w[d], win[j + d], acc);
+    op[j] = acc;
+  }
+  *reinterpret_cast<float4*>(&tmp[row * n + c0]) = o;
+}
+
+constexpr int SW_CK = 8;  // column outputs per thread
+
+template <int R>
+__global__ void __launch_bounds__(256) k_smooth_cols_r(const float* __restrict__ tmp, float* __restrict__ out,
+                                                       int n, const Taps taps, unsigned* __restrict__ img_max) {
+  extern __shared__ float tile_r[];  // (SW_TILE_ROWS + 2R) x 32
+  const int tiles_x = n / 32, tiles_y = (n + SW_TILE_ROWS - 1) / SW_TILE_ROWS;
+  const int img = blockIdx.x / (tiles_x * tiles_y);
+  const int rem = blockIdx.x % (tiles_x * tiles_y);
+  const int c0 = (rem % tiles_x) * 32, r0 = (rem / tiles_x) * SW_TILE_ROWS;
+  const int rows_out = min(SW_TILE_ROWS, n - r0), rows_in = rows_out + 2 * R;
+  const long long base = (long long)img * n * n;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int k = ly; k < rows_in; k += 8) {
+    int rr = r0 - R + k;
+    rr %= n;
+    if (rr < 0) rr += n;
+    tile_r[k * 32 + lx] = __ldg(&tmp[base + (long long)rr * n + c0 + lx]);
+  }
+  float w[2 * R + 1];
+#pragma unroll
+  for (int d = 0; d <= 2 * R; ++d) w[d] = taps.w[d];
+  __syncthreads();
+  unsigned vmax = 0u;
+  const int k0 = ly * SW_CK;  // 8 consecutive output rows per thread
+  if (k0 < rows_out) {
+    float win[SW_CK + 2 * R];
+#pragma unroll
+    for (int k = 0; k < SW_CK + 2 * R; ++k) win[k] = (k0 + k < rows_in) ? tile_r[(k0 + k) * 32 + lx] : 0.f;
+#pragma unroll
+    for (int j = 0; j < SW_CK; ++j) {
+      if (k0 + j < rows_out) {
+        float acc = 0.f;
+#pragma unroll
+        for (int d = 0; d <= 2 * R; ++d) acc = fmaf(w[d], win[j + d], acc);
+        out[base + (long long)(r0 + k0 + j) * n + c0 + lx] = acc;
+        vmax = max(vmax, __float_as_uint(fmaxf(acc, 0.f)));
+      }
+    }
+  }
+  if (img_max) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    if (lx == 0) atomicMax(&img_max[img], vmax);
+  }
+}
+
+template <int R>
+static spring_status smooth_r(int n, const float2* x, float* tmp, float* out, int batch, const Taps& taps,
+                              unsigned* img_max, cudaStream_t s) {
+  const long long total = (long long)batch * n * n, nrows = (long long)batch * n;
+  const int tpr = n / SW_RK, rpb = 256 / tpr > 0 ? 256 / tpr : 1;
+  const size_t row_smem = sizeof(float) * rpb * (n + 2 * R);
+  const size_t col_smem = sizeof(float) * 32 * (SW_TILE_ROWS + 2 * R);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_smooth_rows_r<R><<<(int)((nrows + rpb - 1) / rpb), rpb * tpr, row_smem, s>>>(x, tmp, n, nrows, taps);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, total * 12.0);
+  const int tiles = (n / 32) * ((n + SW_TILE_ROWS - 1) / SW_TILE_ROWS);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_smooth_cols_r<R><<<batch * tiles, 256, col_smem, s>>>(tmp, out, n, taps, img_max);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, total * 8.0);
+  return SPRING_OK;
+}
+
 // S = [rho_sigma >= tau max].  The comparison is decided exactly as in FP64: with
 // t = tau * max in double, (double)v >= t holds for a float v iff v >= f, f the smallest
 // float not below t; f is formed once per block.
@@ -126,6 +238,17 @@ spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int 
   const long long total = (long long)batch * n * n;
   if (total == 0) return SPRING_OK;
   if (img_max) SPRING_CUDA(cudaMemsetAsync(img_max, 0, sizeof(unsigned) * batch, s));
+  switch (taps.r) {
+    case 1: return smooth_r<1>(n, x, tmp, out, batch, taps, img_max, s);
+    case 2: return smooth_r<2>(n, x, tmp, out, batch, taps, img_max, s);
+    case 3: return smooth_r<3>(n, x, tmp, out, batch, taps, img_max, s);
+    case 4: return smooth_r<4>(n, x, tmp, out, batch, taps, img_max, s);
+    case 5: return smooth_r<5>(n, x, tmp, out, batch, taps, img_max, s);
+    case 6: return smooth_r<6>(n, x, tmp, out, batch, taps, img_max, s);
+    case 7: return smooth_r<7>(n, x, tmp, out, batch, taps, img_max, s);
+    case 8: return smooth_r<8>(n, x, tmp, out, batch, taps, img_max, s);
+    default: break;
+  }
   const size_t row_smem = sizeof(float) * (n + 2 * taps.r);
   const size_t col_smem = sizeof(float) * 32 * (SW_TILE_ROWS + 2 * taps.r);
   SPRING_CUDA(cudaFuncSetAttribute(k_smooth_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
