@@ -148,6 +148,25 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Run seed of a rank: every rank reconstructs its own pattern instance (weak scaling,
+    no data-path collective)."""
+    return 1000 + rank
+
+
+def max_over_ranks(ms, dist, device):
+    """The timed region's length is the slowest rank's."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(ws, steps, ms_max):
+    """Whole-job reconstructions/s: every rank completed `steps` reconstructions."""
+    return ws * steps / (ms_max / 1000.0)
+
+
 def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -194,7 +213,7 @@ def run_ours(args, wl):
     name, seed, prm = WORKLOADS[wl]
     pat = synthetic.config_pattern(name, seed)
     n = pat.n
-    p = spring.params(**prm, seed=1000 + rank, use_graph=int(args.graph))
+    p = spring.params(**prm, seed=rank_seed(rank), use_graph=int(args.graph))
     ctx = spring.Context(local)
     dI = torch.from_numpy(pat.intensities).cuda()
     dm = torch.from_numpy(pat.mask).cuda()
@@ -232,10 +251,8 @@ def run_ours(args, wl):
     ms = ev0.elapsed_time(ev1)
     kst = {kc: spring.stats_get(kc) for kc in (spring.KC_ROW_ITER, spring.KC_COL_PM)}
     if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1000.0)
+        ms = max_over_ranks(ms, pg, "cuda")
+    value = weak_value(ws, args.steps, ms)
 
     # ---- end to end through the C ABI from host buffers
     h2d = pat.intensities.nbytes + pat.mask.nbytes + pat.support0.nbytes
@@ -248,6 +265,8 @@ def run_ours(args, wl):
         hp.destroy()
     barrier()
     te = time.perf_counter() - te0
+    if pg:
+        te = max_over_ranks(te * 1000.0, pg, "cuda") / 1000.0
     e2e = ws * max(1, args.steps) / te
 
     out = None
