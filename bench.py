@@ -148,6 +148,15 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_config(wl, n, prm, graph):
+    """The `config` object of a bench line (the same for both arms)."""
+    return {"workload": f"{wl}: {n}x{n}, P={prm['pop']} (2P={2 * prm['pop']} improved), "
+                        f"G={prm['generations']} x {prm['iters_per_gen']} RAAR iterations",
+            "n": n, **prm, "l2": "inputs larger than L2 (run state 2P x N^2 x 25 B = "
+                                 f"{2 * prm['pop'] * n * n * 25 / 2**20:.0f} MiB)",
+            "graph": bool(graph)}
+
+
 def rank_seed(rank):
     """Run seed of a rank: every rank reconstructs its own pattern instance (weak scaling,
     no data-path collective)."""
@@ -188,7 +197,7 @@ def run_reference(args, wl):
         "unit": "reconstructions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 / v if v > 0 else None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl, "n": pat.n, **prm},
+        "config": workload_config(wl, pat.n, prm, args.graph),
         "cpu_baseline": {"value": v, "unit": "reconstructions/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "reconstructions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -300,11 +309,7 @@ def run_ours(args, wl):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{wl}: {n}x{n}, P={prm['pop']} (2P={2 * prm['pop']} improved), "
-                                   f"G={prm['generations']} x {prm['iters_per_gen']} RAAR iterations",
-                       "n": n, **prm, "l2": "inputs larger than L2 (run state 2P x N^2 x 25 B = "
-                                              f"{2 * prm['pop'] * n * n * 25 / 2**20:.0f} MiB)",
-                       "graph": bool(args.graph)},
+            "config": workload_config(wl, n, prm, args.graph),
             "iteration_pixels_per_s": value * pixels_per_reconstruction(n, prm),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "error": {"final_error_avg": statistics.mean(ea), "final_error_best": statistics.mean(eb),
