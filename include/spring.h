@@ -395,9 +395,11 @@ spring_status spring_initialize(uint64_t seed, const uint8_t* S0, const float* M
  *   col 0: default radix plan, 16-column tiles; col 1: alternative radix plan;
  *   col 2: 32-column tiles (16 at N = 1024); col 3: 8-column tiles;
  *   col 4 / 5: persistent blocks fed by TMA (16 / 8-column tiles, next tile in flight);
- *   col 6 / 7: transposed tiles, one lane group per column (warp-level synchronisation).
+ *   col 6 / 7: transposed tiles, one lane group per column (warp-level synchronisation);
+ *   col 8 / 9: two adjacent columns per thread, 16-byte accesses throughout (16 / 32-column
+ *   tiles; their plan has the default's radices at N = 64, 192, 512, column 1's at 1024).
  * Variants sharing a radix plan give bit-identical results (row 0-4, row 5-6; column 0
- * and 2-7); the alternative plans (row 5-6, column 1) differ by rounding.  A run tunes each side once per process
+ * and 2-7, column 8-9); the alternative plans differ by rounding.  A run tunes each side once per process
  * (spring_autotune on the run's batch) unless the environment sets SPRING_AUTOTUNE=0 or
  * the variant was set explicitly. */
 spring_status spring_set_kernel_variant(int n, int row_variant, int col_variant); /* -1 = keep */

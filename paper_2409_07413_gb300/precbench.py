@@ -7,7 +7,9 @@ r = 24 px, 1e8 photons with Poisson noise, 200 px object) reconstructed with P =
                iteration blocks, FP32 math
 
 Both runs keep the Fourier-error fitness and the shrink-wrap threshold statistics in FP64
-on the GPU.  Per result it reports time, reconstructions/s, iteration-pixels/s, the final
+on the GPU.  The same pattern and run seed at 2 of the 20 generations are also run in both
+precisions and set beside the FP64 oracle's result for that configuration (stored by
+tests/golden/make_oracle_errors.py; the full 20 generations take the oracle hours).  Per result it reports time, reconstructions/s, iteration-pixels/s, the final
 Fourier error (Eq. error_calc) of the average and best individual, and the error of the
 aligned average against the synthetic object (aligned by spring_reshift: translation,
 twin and global phase; then the best real scale, since intensities in photon counts fix the
@@ -22,8 +24,11 @@ from __future__ import annotations
 import argparse
 import json
 import time
+from pathlib import Path
 
 import numpy as np
+
+GOLDEN = Path(__file__).resolve().parent.parent / "tests" / "golden" / "oracle_errors.json"
 
 
 def truth_error(spring, rho, truth):
@@ -74,6 +79,18 @@ def main():
             "final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
             "truth_error_of_average": truth_error(spring, r["rho_avg"], pat.truth),
         }
+    # the reduced configuration the oracle has run (2 generations, run seed 1000)
+    golden = {}
+    if GOLDEN.exists():
+        golden = json.loads(GOLDEN.read_text()).get("ell1024_g2", {})
+    red = dict(prm, generations=2)
+    cmp = {"config": red, "oracle_fp64": {k: golden[k] for k in ("final_error_avg", "final_error_best")
+                                          if k in golden} or None}
+    for prec in [int(v) for v in a.precisions.split(",")]:
+        r = prob.run(spring.params(**red, seed=1000, precision=prec))
+        cmp[str(prec)] = {"final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
+                          "truth_error_of_average": truth_error(spring, r["rho_avg"], pat.truth)}
+    out["versus_oracle"] = cmp
     prob.destroy()
     ctx.close()
     print(json.dumps(out), flush=True)
