@@ -62,6 +62,10 @@ template <> struct AltPlan<256>  : PlanT<256, 32, 32, 8> {};
 template <> struct AltPlan<512>  : PlanT<512, 8, 8, 8, 8> {};
 template <> struct AltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
+// row plan of the FP16-storage iteration pass
+template <int N> struct Row16Plan : Plan<N> {};
+template <> struct Row16Plan<1024> : PlanT<1024, 16, 16, 8, 8> {};
+
 // plans of the paired column pass (two columns per thread, E <= 16)
 template <int N> struct Col2Plan;
 template <> struct Col2Plan<64>   : PlanT<64, 8, 8, 8> {};
@@ -714,10 +718,11 @@ spring_status run_fft_op(const FftOp& op, cudaStream_t s, bool prep) {
     case OP_COL_INV: return col_launch<Plan<N>, 16, COL_INV>(op, s, prep);
     case OP_COL_ERR: return col_launch<Plan<N>, ERR_W, COL_ERR>(op, s, prep);
     case OP_ROW_ITER16:
-      if (op.alg == 0) return row_launch<Plan<N>, ROW_ITER, 0, true, 2, false, __half2>(op, s, prep);
-      if (op.alg == 1) return row_launch<Plan<N>, ROW_ITER, 1, true, 2, false, __half2>(op, s, prep);
-      return row_launch<Plan<N>, ROW_ITER, 2, true, 2, false, __half2>(op, s, prep);
-    case OP_COL_PM16: return col_launch<Plan<N>, 16, COL_PM, __half2>(op, s, prep);
+      // the FP32 path's fastest shapes at 1024: 16 elements per thread, 8-column tiles
+      if (op.alg == 0) return row_launch<Row16Plan<N>, ROW_ITER, 0, true, 2, false, __half2>(op, s, prep);
+      if (op.alg == 1) return row_launch<Row16Plan<N>, ROW_ITER, 1, true, 2, false, __half2>(op, s, prep);
+      return row_launch<Row16Plan<N>, ROW_ITER, 2, true, 2, false, __half2>(op, s, prep);
+    case OP_COL_PM16: return col_launch<Plan<N>, (N >= 1024 ? 8 : 16), COL_PM, __half2>(op, s, prep);
     case OP_ROW_INIT16: return row_launch<Plan<N>, ROW_INIT16, 0, false, 1>(op, s, prep);
   }
   return invalid("unknown transform operation");
