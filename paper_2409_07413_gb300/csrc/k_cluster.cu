@@ -41,8 +41,8 @@ struct ClusterLayout {
   static constexpr size_t X_OFF = 0, R_OFF = (size_t)RB * N, C_OFF = R_OFF + (size_t)RB * PITCH,
                           END = C_OFF + (size_t)N * RB;
   static constexpr size_t SMEM = END * sizeof(float2) + (size_t)RB * N;
-  // CTAs per SM the register budget is sized for (shared memory allows 2 at N = 128)
-  static constexpr int MINB = (N == 128) ? 2 : 1;
+  // CTAs per SM the register budget is sized for (shared memory allows 2 at N = 128, 4 at 64)
+  static constexpr int MINB = (N == 128) ? 2 : (N == 64) ? 4 : 1;
   static_assert(C >= 1 && C <= 8 && N % RB == 0, "cluster of at most 8 CTAs");
   static_assert(T <= 32, "row transforms are owned by lane groups inside a warp");
 };
