@@ -7,7 +7,7 @@ r = 24 px, 1e8 photons with Poisson noise, 200 px object) reconstructed with P =
                iteration blocks, FP32 math
 
 Both runs keep the Fourier-error fitness and the shrink-wrap threshold statistics in FP64
-on the GPU.  The same pattern and run seed at 2 of the 20 generations are also run in both
+on the GPU.  The same pattern, schedule and run seed at P = 32 and 2 generations are also run in both
 precisions and set beside the FP64 oracle's result for that configuration (stored by
 tests/golden/make_oracle_errors.py; the full 20 generations take the oracle hours).  Per result it reports time, reconstructions/s, iteration-pixels/s, the final
 Fourier error (Eq. error_calc) of the average and best individual, and the error of the
@@ -83,7 +83,7 @@ def main():
     golden = {}
     if GOLDEN.exists():
         golden = json.loads(GOLDEN.read_text()).get("ell1024_g2", {})
-    red = dict(prm, generations=2)
+    red = dict(prm, pop=32, generations=2)
     cmp = {"config": red, "oracle_fp64": {k: golden[k] for k in ("final_error_avg", "final_error_best")
                                           if k in golden} or None}
     for prec in [int(v) for v in a.precisions.split(",")]:

@@ -4,7 +4,7 @@ the benchmark workloads (synthetic patterns from paper_2409_07413_gb300.syntheti
 Calls only the oracle.  Run from the repository root:
     python tests/golden/make_oracle_errors.py [--threads T]
 The 512 x 512 run (P = 64, 10 x 200 iterations) takes ~20 min on 8 cores, the reduced
-1024 x 1024 run ~40 min.
+1024 x 1024 run ~10 min.
 """
 import argparse
 import json
@@ -23,9 +23,9 @@ WORKLOADS = {
                                  sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
     "sphere64": ("sphere64", 0, dict(pop=8, iters_per_gen=100, generations=5, algorithm=2, beta=0.9,
                                      sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
-    # the precision workload (1024 x 1024, P = 128, 300 iterations per generation) at 2 of its
-    # 20 generations: ~40 min on 8 cores
-    "ell1024_g2": ("ell1024", 0, dict(pop=128, iters_per_gen=300, generations=2, algorithm=2, beta=0.9,
+    # the precision workload's pattern and schedule (1024 x 1024, 300 iterations per
+    # generation) at P = 32 and 2 generations: ~10 min on 8 cores
+    "ell1024_g2": ("ell1024", 0, dict(pop=32, iters_per_gen=300, generations=2, algorithm=2, beta=0.9,
                                       sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
 }
 
