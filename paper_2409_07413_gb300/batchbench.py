@@ -9,10 +9,14 @@ G generations x 200 RAAR iterations.  Two ways to run the same set:
   served: every pattern submitted at once (spring_submit); the scheduler runs several
           populations of different sides concurrently on prioritised streams, advancing
           each a generation at a time (continuous batching);
-  plain:  spring_mpr_run one pattern after another.
+  plain:  spring_mpr_run one pattern after another;
+  batched: the patterns grouped by side, each group run K at a time with
+          spring_mpr_run_batch (one launch per iteration pass over K x 2P images; K such
+          that a launch covers about --batch-pixels pixels).
 
 Reports reconstructions/s and iteration-pixels/s of each (makespan of the whole set) and
-the mean final error; both see identical requests and seeds, so the errors agree exactly.
+the mean final error; all see identical requests and seeds, so the errors agree exactly
+(checked pattern by pattern).
 Prints one JSON line.
 """
 from __future__ import annotations
@@ -45,7 +49,8 @@ def main():
     ap.add_argument("--patterns", type=int, default=256)
     ap.add_argument("--generations", type=int, default=5)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--modes", default="served,plain")
+    ap.add_argument("--modes", default="served,plain,batched")
+    ap.add_argument("--batch-pixels", type=float, default=2.0 ** 26)
     a = ap.parse_args()
     import torch  # noqa: F401  (device selection through the library)
     from paper_2409_07413_gb300 import spring
@@ -59,24 +64,38 @@ def main():
     out = {"benchmark": "batched uneven", "patterns": len(jobs),
            "sides": {str(n): int(sum(1 for j in jobs if j[0] == n)) for n in SIDES}, "params": prm,
            "iteration_pixels": work_px}
+    per_mode = {}
     for mode in a.modes.split(","):
         probs = [ctx.problem(p.intensities, p.mask, p.support0) for _, p, _ in jobs]
         torch.cuda.synchronize()
-        errs = []
+        errs = [None] * len(jobs)
         t0 = time.perf_counter()
-        if mode == "served":
+        if mode == "batched":
+            for n in SIDES:
+                idx = [i for i, j in enumerate(jobs) if j[0] == n]
+                K = max(1, int(a.batch_pixels // (2 * prm["pop"] * n * n)))
+                for c in range(0, len(idx), K):
+                    part = idx[c:c + K]
+                    rs = ctx.run_batch([probs[i] for i in part], spring.params(**prm),
+                                       [jobs[i][2] for i in part], want_arrays=False)
+                    for i, r in zip(part, rs):
+                        errs[i] = r["final_error_best"]
+        elif mode == "served":
             tickets = [pr.submit(spring.params(**prm, seed=sd)) for pr, (_, _, sd) in zip(probs, jobs)]
-            for t in tickets:
+            for i, t in enumerate(tickets):
                 st, r = ctx.poll(t, -1, want_arrays=False)
-                errs.append(r["final_error_best"])
+                errs[i] = r["final_error_best"]
         else:
-            for pr, (_, _, sd) in zip(probs, jobs):
-                errs.append(pr.run(spring.params(**prm, seed=sd), want_arrays=False)["final_error_best"])
+            for i, (pr, (_, _, sd)) in enumerate(zip(probs, jobs)):
+                errs[i] = pr.run(spring.params(**prm, seed=sd), want_arrays=False)["final_error_best"]
         span = time.perf_counter() - t0
         for pr in probs:
             pr.destroy()
+        per_mode[mode] = errs
         out[mode] = {"seconds": span, "reconstructions_per_s": len(jobs) / span,
                      "iteration_pixels_per_s": work_px / span, "mean_final_error_best": float(np.mean(errs))}
+    modes = list(per_mode)
+    out["errors_identical_across_modes"] = all(per_mode[m] == per_mode[modes[0]] for m in modes)
     ctx.close()
     print(json.dumps(out), flush=True)
 

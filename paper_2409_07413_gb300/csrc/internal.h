@@ -10,8 +10,9 @@ namespace spring {
 // iteration row pass: w (column-pass output) -> P_M x -> update -> x, rowFFT(x) -> w
 spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint8_t* S,
                               long long batch, float beta, float chi, bool zout, cudaStream_t s);
-// iteration column pass: colFFT, masked modulus projection, colIFFT, in place on w
-spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s);
+// iteration column pass: colFFT, masked modulus projection, colIFFT, in place on w.
+// m_group > 0: M holds one N x N array per m_group consecutive images (a batch of patterns)
+spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s, int m_group = 0);
 // plain row transform (dir -1 forward, +1 inverse), unnormalised times `scale`;
 // Smul (forward only, may be null) multiplies the input by the support first
 spring_status launch_row_fft(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,
@@ -21,7 +22,7 @@ spring_status launch_col_fft(int n, int dir, float2* data, int batch, float scal
 // column forward transform + per-block FP64 partial sums of the Fourier error
 int err_strips(int n);
 spring_status launch_col_err(int n, float2* w, const float* M, int batch, double* partials,
-                             cudaStream_t s);
+                             cudaStream_t s, int m_group = 0);
 spring_status launch_err_finalize(int n, const double* partials, int batch, double* err,
                                   int* status, cudaStream_t s);
 // the same two error launchers with a caller-supplied twiddle table (all sides, laid out
@@ -29,7 +30,7 @@ spring_status launch_err_finalize(int n, const double* partials, int batch, doub
 spring_status launch_row_fft_tw(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,
                                 long long batch, float scale, const float2* tw_all, cudaStream_t s);
 spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
-                                const float2* tw_all, cudaStream_t s);
+                                const float2* tw_all, cudaStream_t s, int m_group = 0);
 
 // FP16 storage of the iteration buffers (precision 1): wh, xh are half2 arrays; x is kept
 // scaled by the device scalar s16 (a power of two from launch_fp16_scale), w by s16 times a
@@ -48,7 +49,7 @@ bool cluster_side(int n);
 spring_status prepare_cluster_kernels(int n);
 spring_status cluster_supported(int n, bool* ok);
 spring_status launch_cluster_iter(int n, int alg, float2* x, const uint8_t* S, const float* M, long long batch,
-                                  float beta, float chi, int n_iter, cudaStream_t s);
+                                  float beta, float chi, int n_iter, cudaStream_t s, int m_group = 0);
 // 0: two passes through HBM per iteration; 1: the on-chip kernel (set by the autotuner)
 int iteration_path(int n);
 
@@ -75,8 +76,9 @@ spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int 
                             unsigned* img_max, cudaStream_t s);
 spring_status launch_threshold(int n, const float* sm, const unsigned* img_max, float tau,
                                uint8_t* S, int batch, cudaStream_t s);
+// image b uses alpha[(b / alpha_group) * alpha_stride]
 spring_status launch_select_area(int n, const float* sm, const int64_t* alpha, int alpha_stride,
-                                 uint8_t* S, int batch, cudaStream_t s);
+                                 uint8_t* S, int batch, cudaStream_t s, int alpha_group = 1);
 
 // ---------------------------------------------------------------- k_ga.cu
 spring_status launch_random_choice(uint64_t seed, int g, int P, int32_t* abc, cudaStream_t s);

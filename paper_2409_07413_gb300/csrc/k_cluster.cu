@@ -54,6 +54,7 @@ struct ClusterArgs {
   const float2* tw;
   float beta, cchi;
   int chi_on, n_iter;
+  int m_group;        // > 0: one modulus array per m_group consecutive images
 };
 
 template <int N, int ALG>
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(ClusterLayout<N>::THREADS, ClusterLayout<N>::M
   const BlockSync bsync;
   float2* xg = a.x + img * N * N + (long long)r0 * N;
   const uint8_t* Sg = a.S + img * N * N + (long long)r0 * N;
+  const float* Mi = a.m_group > 0 ? a.M + (img / a.m_group) * N * N : a.M;
   constexpr float inv_n = 1.0f / N;
 
   for (int k = tid; k < RB * N; k += L::THREADS) {
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(ClusterLayout<N>::THREADS, ClusterLayout<N>::M
     for (int m = 0; m < E; ++m) {
       const int i = ct + m * T;
       v[m] = Cc[i * RB + cc];
-      Mv[m] = __ldg(&a.M[(long long)i * N + r0 + cc]);
+      Mv[m] = __ldg(&Mi[(long long)i * N + r0 + cc]);
     }
     bsync();  // every input is in registers before the exchange reuses the tile
     fft_plan<P, -1, false, RB>(v, Cc + cc, ct, a.tw, bsync);
@@ -247,7 +249,7 @@ spring_status cluster_supported(int n, bool* ok) {
 }
 
 spring_status launch_cluster_iter(int n, int alg, float2* x, const uint8_t* S, const float* M, long long batch,
-                                  float beta, float chi, int n_iter, cudaStream_t s) {
+                                  float beta, float chi, int n_iter, cudaStream_t s, int m_group) {
   if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
@@ -260,6 +262,7 @@ spring_status launch_cluster_iter(int n, int alg, float2* x, const uint8_t* S, c
   a.chi_on = chi < 1.0f;
   a.cchi = (float)((chi == 0.5f) ? 0.0 : std::cos((double)chi * 3.14159265358979323846));
   a.n_iter = n_iter;
+  a.m_group = m_group;
   return cluster_any(n, alg, a, batch, false, s);
 }
 

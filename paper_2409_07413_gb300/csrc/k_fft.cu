@@ -118,7 +118,7 @@ spring_status launch_row_fft(int n, int dir, const float2* in, float2* out, cons
   return launch_row_fft_tw(n, dir, in, out, Smul, batch, scale, tb.tw, s);
 }
 
-spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s) {
+spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s, int m_group) {
   if (side_index(n) < 0) return invalid("unsupported pattern side");
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
@@ -130,7 +130,9 @@ spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStr
   op.ca.M = M;
   op.ca.tw = tb.tw + tw_offset(n);
   op.ca.batch = batch;
-  op.bytes = (double)batch * n * n * 16.0 + (double)n * n * 4.0;
+  op.ca.m_group = m_group;
+  const double nm = m_group > 0 ? (double)((batch + m_group - 1) / m_group) : 1.0;
+  op.bytes = (double)batch * n * n * 16.0 + nm * n * n * 4.0;
   return dispatch(n, op, s);
 }
 
@@ -150,7 +152,7 @@ spring_status launch_col_fft(int n, int dir, float2* data, int batch, float scal
 int err_strips(int n) { return n / ERR_W; }
 
 spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
-                                const float2* tw_all, cudaStream_t s) {
+                                const float2* tw_all, cudaStream_t s, int m_group) {
   FftOp op;
   op.kind = OP_COL_ERR;
   op.ca.data = w;
@@ -158,15 +160,16 @@ spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, dou
   op.ca.tw = tw_all + tw_offset(n);
   op.ca.batch = batch;
   op.ca.partials = partials;
+  op.ca.m_group = m_group;
   op.bytes = (double)batch * n * n * 8.0 + (double)n * n * 4.0;
   return dispatch(n, op, s);
 }
 
 spring_status launch_col_err(int n, float2* w, const float* M, int batch, double* partials,
-                             cudaStream_t s) {
+                             cudaStream_t s, int m_group) {
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
-  return launch_col_err_tw(n, w, M, batch, partials, tb.tw, s);
+  return launch_col_err_tw(n, w, M, batch, partials, tb.tw, s, m_group);
 }
 
 __global__ void k_err_finalize(const double* __restrict__ partials, int strips, int batch,

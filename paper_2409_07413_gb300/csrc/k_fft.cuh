@@ -130,7 +130,13 @@ struct ColArgs {
   float scale;        // FWD / INV output scale
   double* partials;   // ERR: [batch][N / ERR_W][2] (sum Xi (|X| - M)^2, sum Xi M^2)
   const float* s16;   // FP16 storage: device scalar s16 (power of two)
+  int m_group;        // > 0: M holds one N x N array per m_group consecutive images
 };
+
+// the modulus array of image img
+__device__ __forceinline__ const float* m_of(const ColArgs& a, int img, int n) {
+  return a.m_group > 0 ? a.M + (size_t)(img / a.m_group) * n * n : a.M;
+}
 
 struct FftOp {
   int kind = 0, alg = 0, variant = 0, kclass = SPRING_KC_OTHER;
@@ -310,7 +316,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
     constexpr int CH = W / 4;  // 16-byte chunks per row
     for (int k = threadIdx.x; k < N * CH; k += blockDim.x) {
       const int row = k / CH, q = k % CH;
-      cp_async16(Ms + row * W + 4 * q, a.M + (size_t)row * N + strip * W + 4 * q);
+      cp_async16(Ms + row * W + 4 * q, m_of(a, img, N) + (size_t)row * N + strip * W + 4 * q);
     }
     cp_async_commit();
   }
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__((W / 2) * P::T, ((W / 2) * P::T <= 512 ? 2 : 1
     constexpr int CH = W / 4;  // 16-byte chunks per row of the strip
     for (int k = threadIdx.x; k < N * CH; k += blockDim.x) {
       const int row = k / CH, q = k % CH;
-      cp_async16(Ms + row * W + 4 * q, a.M + (size_t)row * N + strip * W + 4 * q);
+      cp_async16(Ms + row * W + 4 * q, m_of(a, img, N) + (size_t)row * N + strip * W + 4 * q);
     }
     cp_async_commit();
   }
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_colT(Co
   float* MsT = reinterpret_cast<float*>(smem + (size_t)W * RS);  // W x MS
   const int img = blockIdx.x / STRIPS, strip = blockIdx.x % STRIPS;
   float2* base = a.data + (size_t)img * N * N + strip * W;
-  const float* Mb = a.M + strip * W;
+  const float* Mb = m_of(a, img, N) + strip * W;
   // phase A: coalesced loads (lanes along the columns), transposed writes
   {
     const int ca = threadIdx.x % W, ra = threadIdx.x / W;
@@ -532,7 +538,8 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 256 ? 2 : 1))
 #pragma unroll
     for (int k = 0; k < NBOX; ++k) {
       tma_load_3d(dst + k * BOXR * W, &tmap, strip * 2 * W, k * BOXR, img, &mbar[b]);
-      tma_load_3d(mdst + k * BOXR * W, &mmap, strip * W, k * BOXR, 0, &mbar[b]);
+      tma_load_3d(mdst + k * BOXR * W, &mmap, strip * W, k * BOXR, a.m_group > 0 ? img / a.m_group : 0,
+                  &mbar[b]);
     }
   };
   int tile = blockIdx.x;
@@ -645,7 +652,8 @@ inline spring_status col_pm_tma_launch(const FftOp& op, cudaStream_t s, bool pre
   if (op.ca.batch < 1) return SPRING_OK;
   CUtensorMap map, mmap;
   SPRING_TRY(encode_tmap_f32_3d(&map, op.ca.data, 2 * N, N, op.ca.batch, 2 * W, BOXR));
-  SPRING_TRY(encode_tmap_f32_3d(&mmap, op.ca.M, N, N, 1, W, BOXR));
+  const int nm = op.ca.m_group > 0 ? (op.ca.batch + op.ca.m_group - 1) / op.ca.m_group : 1;
+  SPRING_TRY(encode_tmap_f32_3d(&mmap, op.ca.M, N, N, nm, W, BOXR));
   static int per_sm = 0;
   if (!per_sm) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_col_pm_tma<P, W>, W * P::T, smem);

@@ -312,7 +312,7 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_t
 
 __global__ void __launch_bounds__(SEL_THREADS) k_select_area(const float* __restrict__ sm,
                                                              const int64_t* __restrict__ alpha,
-                                                             int alpha_stride,
+                                                             int alpha_stride, int alpha_group,
                                                              uint8_t* __restrict__ S, int n) {
   __shared__ unsigned hist[2048];
   __shared__ unsigned warp_tot[32];
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_area(const float* __rest
   const long long nn = (long long)n * n;
   const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)blockIdx.x * nn;
   uint8_t* out = S + (long long)blockIdx.x * nn;
-  long long a = alpha[(long long)blockIdx.x * alpha_stride];
+  long long a = alpha[(long long)(blockIdx.x / alpha_group) * alpha_stride];
   if (a <= 0 || a >= nn) {
     const uint8_t fill = a <= 0 ? 0 : 1;
     for (long long i = threadIdx.x; i < nn; i += blockDim.x) out[i] = fill;
@@ -374,10 +374,11 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_area(const float* __rest
 }
 
 spring_status launch_select_area(int n, const float* sm, const int64_t* alpha, int alpha_stride,
-                                 uint8_t* S, int batch, cudaStream_t s) {
+                                 uint8_t* S, int batch, cudaStream_t s, int alpha_group) {
   if (batch < 1) return SPRING_OK;
+  if (alpha_group < 1) return invalid("alpha_group must be >= 1");
   launch_begin(SPRING_KC_OTHER, s);
-  k_select_area<<<batch, SEL_THREADS, 0, s>>>(sm, alpha, alpha_stride, S, n);
+  k_select_area<<<batch, SEL_THREADS, 0, s>>>(sm, alpha, alpha_stride, alpha_group, S, n);
   SPRING_CHECK_LAUNCH();
   launch_end(SPRING_KC_OTHER, s, (double)batch * n * n * 13.0);
   return SPRING_OK;

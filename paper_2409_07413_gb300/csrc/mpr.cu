@@ -78,13 +78,15 @@ static spring_status validate_params(int n, const spring_params& p) {
 // ------------------------------------------------------------------ device layout of a run
 struct Layout {
   size_t x, w, S, sm0, sm1, err, abc, ix, ir, info, best, ph, alpha, repl, dens, part_err,
-      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, total;
+      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, mall, total;
 };
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-static Layout make_layout(int n, const spring_params& p) {
-  const size_t nn = (size_t)n * n, P = p.pop, B = 2 * P, G = p.generations, Q = 3 * P;
+// K patterns of side n run together (K = 1: a single run); per-pattern state is K times
+// the single run's, GA scratch is shared (the patterns' GA steps run one after another)
+static Layout make_layout(int n, const spring_params& p, int K = 1) {
+  const size_t nn = (size_t)n * n, P = p.pop, B = 2 * P * K, G = p.generations, Q = 3 * P;
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -102,23 +104,24 @@ static Layout make_layout(int n, const spring_params& p) {
   L.ix = take(sizeof(int32_t) * Q);
   L.ir = take(sizeof(int32_t) * Q);
   L.info = take(sizeof(int32_t) * 3 * Q);
-  L.best = take(sizeof(int32_t) * 4);
+  L.best = take(sizeof(int32_t) * 4 * K);
   L.ph = take(sizeof(float2) * Q);
-  L.alpha = take(sizeof(int64_t) * 4);
+  L.alpha = take(sizeof(int64_t) * 4 * K);
   L.repl = take(P);
   L.dens = take(sizeof(double) * 2 * P);
   L.part_err = take(sizeof(double) * 2 * B * err_strips(n));
   L.part_norm = take(normalise_scratch_bytes((int)P));
   L.part_dens = take(density_scratch_bytes((int)P));
   L.imgmax = take(sizeof(unsigned) * B);
-  L.stats = take(sizeof(double) * 8 * G);
-  L.avg = take(sizeof(float2) * nn);
-  L.Savg = take(nn);
-  L.err_avg = take(sizeof(double) * 2);
+  L.stats = take(sizeof(double) * 8 * G * K);
+  L.avg = take(sizeof(float2) * nn * K);
+  L.Savg = take(nn * K);
+  L.err_avg = take(sizeof(double) * 2 * K);
   L.status = take(sizeof(int) * 4);
   L.peaks = take(peaks_scratch_bytes(n, (int)P));
   L.init = take(init_scratch_bytes((int)P, p.init_n_spheres) + 128);
   L.mavg = take(p.ca > 0.f ? sizeof(float) * nn : 0);
+  L.mall = take(K > 1 ? sizeof(float) * nn * K : 0);  // the K modulus arrays, gathered
   L.total = o;
   return L;
 }
@@ -128,10 +131,16 @@ class Run {
   // B: image slots (both populations); NB: individuals improved per generation (B for MPR,
   // P for independent reconstructions, which use the second half as scratch)
   int n = 0, P = 0, B = 0, NB = 0, G = 0, R = 0, last = 0;
+  // a batch: K patterns of side n, each with its own population (B image slots each, one
+  // after another); whole-batch launches cover NBT = K NB images; the GA steps of pattern
+  // cq use the accessors below
+  int K = 1, cq = 0, NBT = 0;
+  std::vector<const spring_problem*> probs;
+  std::vector<uint64_t> seeds;
+  const float* Mall = nullptr;  // K modulus arrays one after another (K = 1: the problem's)
+  int mgroup = 0;               // images per modulus array in whole-batch launches (0: one)
   spring_params prm{};
-  const float* M = nullptr;
   const float* s16 = nullptr;  // FP16 storage scale of the problem (device scalar)
-  const uint8_t* S0 = nullptr;
   cudaStream_t s = nullptr;
   char* mem = nullptr;
   Layout L{};
@@ -166,7 +175,15 @@ class Run {
   }
 
   spring_status setup(const spring_problem* prob, const spring_params& p, cudaStream_t stream) {
-    n = prob->n;
+    return setup_batch(&prob, 1, &p.seed, p, stream);
+  }
+
+  spring_status setup_batch(const spring_problem* const* pr, int k, const uint64_t* sd, const spring_params& p,
+                            cudaStream_t stream) {
+    K = k;
+    probs.assign(pr, pr + k);
+    seeds.assign(sd, sd + k);
+    n = pr[0]->n;
     prm = p;
     P = p.pop;
     B = 2 * P;
@@ -178,12 +195,12 @@ class Run {
       R = p.iters_per_gen / p.sw_period;
       last = p.iters_per_gen - (R - 1) * p.sw_period;
     }
-    M = prob->M;
-    s16 = prob->s16;
-    S0 = prob->S0;
+    NBT = K * NB;
+    mgroup = K > 1 ? B : 0;
+    s16 = pr[0]->s16;
     s = stream;
     fp16 = p.precision == 1;
-    L = make_layout(n, p);
+    L = make_layout(n, p, K);
     SPRING_TRY(prepare_fft_kernels(n));
     SPRING_TRY(ensure_tuned(n, B, s));
     DeviceTables tb;
@@ -222,6 +239,14 @@ class Run {
     peaks = mem + L.peaks;
     init_sc = mem + L.init;
     mavg = p.ca > 0.f ? reinterpret_cast<float*>(mem + L.mavg) : nullptr;
+    if (K > 1) {
+      float* m = reinterpret_cast<float*>(mem + L.mall);
+      for (int q = 0; q < K; ++q)
+        SPRING_CUDA(cudaMemcpyAsync(m + q * nn(), probs[q]->M, sizeof(float) * nn(), cudaMemcpyDeviceToDevice, s));
+      Mall = m;
+    } else {
+      Mall = probs[0]->M;
+    }
     return SPRING_OK;
   }
 
@@ -232,28 +257,41 @@ class Run {
   // bring the FP32 state up to date with the FP16 iteration state
   spring_status sync_x() {
     if (x16_newer) {
-      SPRING_TRY(launch_half_to_float(xh(), x, (long long)NB * nn(), s16, s));
+      SPRING_TRY(launch_half_to_float(xh(), x, (long long)NBT * nn(), s16, s));
       x16_newer = false;
     }
     return SPRING_OK;
   }
-  float2* x_pop() { return x; }
-  float2* x_new() { return x + P * nn(); }
-  float2* w_pop() { return w; }
-  float2* w_new() { return w + P * nn(); }
-  uint8_t* S_pop() { return S; }
-  uint8_t* S_new() { return S + P * nn(); }
-  double* err_pop() { return err; }
-  double* err_new() { return err + P; }
+  // pattern cq of the batch
+  float2* x_pop() { return x + (size_t)cq * B * nn(); }
+  float2* x_new() { return x_pop() + P * nn(); }
+  float2* w_pop() { return w + (size_t)cq * B * nn(); }
+  float2* w_new() { return w_pop() + P * nn(); }
+  uint8_t* S_pop() { return S + (size_t)cq * B * nn(); }
+  uint8_t* S_new() { return S_pop() + P * nn(); }
+  double* err_pop() { return err + (size_t)cq * B; }
+  double* err_new() { return err_pop() + P; }
+  int32_t* bestq() { return best + 4 * cq; }
+  int64_t* alphaq() { return alpha + 4 * cq; }
+  double* statsq() { return stats + (size_t)8 * G * cq; }
+  float2* avgq() { return avg + (size_t)cq * nn(); }
+  uint8_t* Savgq() { return Savg + (size_t)cq * nn(); }
+  double* err_avgq() { return err_avg + 2 * cq; }
+  const float* Mq() { return Mall + (K > 1 ? (size_t)cq * nn() : 0); }
+  const uint8_t* S0q() { return probs[cq]->S0; }
+  uint64_t seed() const { return seeds[cq]; }
 
   // Initialize (App. "Initialization of the starting densities")
   spring_status enqueue_init() {
     SPRING_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * 4, s));
-    SPRING_TRY(launch_init_spheres(n, prm.seed, S0, P, prm.init_n_spheres, prm.init_gamma,
-                                   prm.init_phi_max, x_pop(), init_sc, s));
-    SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
-    SPRING_TRY(launch_normalise(n, w_pop(), M, P, x_pop(), part_norm, s));
-    SPRING_TRY(launch_broadcast_support(n, S0, P, S_pop(), s));
+    for (cq = 0; cq < K; ++cq) {
+      SPRING_TRY(launch_init_spheres(n, seed(), S0q(), P, prm.init_n_spheres, prm.init_gamma,
+                                     prm.init_phi_max, x_pop(), init_sc, s));
+      SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
+      SPRING_TRY(launch_normalise(n, w_pop(), Mq(), P, x_pop(), part_norm, s));
+      SPRING_TRY(launch_broadcast_support(n, S0q(), P, S_pop(), s));
+    }
+    cq = 0;
     z_valid = z16_valid = x16_newer = false;
     return SPRING_OK;
   }
@@ -261,7 +299,7 @@ class Run {
   // alignment of P pairs (ix, ir) given population spectra in w_pop; correlations go to
   // the free new-population halves of x and w
   spring_status align(const int32_t* pix, const int32_t* pir, int32_t* pinfo, float2* pph) {
-    SPRING_TRY(launch_xcorr_spectra(n, w_pop(), pix, pir, P, M, x_new(), w_new(), s));
+    SPRING_TRY(launch_xcorr_spectra(n, w_pop(), pix, pir, P, Mq(), x_new(), w_new(), s));
     SPRING_TRY(fft2_unitary(n, +1, x_new(), x_new(), nullptr, P, s));
     SPRING_TRY(fft2_unitary(n, +1, w_new(), w_new(), nullptr, P, s));
     return launch_peaks(n, x_new(), w_new(), P, pinfo, pph, peaks, s);
@@ -271,22 +309,22 @@ class Run {
   // (|F rho_avg| + mean_p |F rho_p|) / 2 into mavg, with rho_avg the population aligned onto
   // its best individual (Eq. avgrec).  Needs the population spectra in w_pop.
   spring_status average_moduli(int g) {
-    SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, best, s));
-    SPRING_TRY(launch_pairs_onto_best(P, best, ix, ir, s));
+    SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, bestq(), s));
+    SPRING_TRY(launch_pairs_onto_best(P, bestq(), ix, ir, s));
     SPRING_TRY(align(ix, ir, info, ph));
-    SPRING_TRY(launch_average(n, x_pop(), S_pop(), info, ph, best, P, avg, Savg, s));
-    SPRING_TRY(fft2_unitary(n, -1, avg, avg, nullptr, 1, s));
-    return launch_average_moduli(n, w_pop(), avg, P, mavg, s);
+    SPRING_TRY(launch_average(n, x_pop(), S_pop(), info, ph, bestq(), P, avgq(), Savgq(), s));
+    SPRING_TRY(fft2_unitary(n, -1, avgq(), avgq(), nullptr, 1, s));
+    return launch_average_moduli(n, w_pop(), avgq(), P, mavg, s);
   }
 
   // Crossover (Alg. crossover)
   spring_status crossover(int g) {
     SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
     if (prm.ca > 0.f) SPRING_TRY(average_moduli(g));
-    SPRING_TRY(launch_random_choice(prm.seed, g, P, abc, s));
+    SPRING_TRY(launch_random_choice(seed(), g, P, abc, s));
     SPRING_TRY(launch_pairs_crossover(P, abc, ix, ir, s));
     for (int c = 0; c < 3; ++c) SPRING_TRY(align(ix + c * P, ir + c * P, info + 3 * c * P, ph + c * P));
-    SPRING_TRY(launch_crossover_mix(n, w_pop(), abc, info, ph, P, prm.seed, g, prm.cw, prm.cp,
+    SPRING_TRY(launch_crossover_mix(n, w_pop(), abc, info, ph, P, seed(), g, prm.cw, prm.cp,
                                     prm.tile_min, prm.tile_max, prm.ca, mavg, x_new(), s));
     SPRING_TRY(fft2_unitary(n, +1, x_new(), x_new(), nullptr, P, s));
     SPRING_TRY(launch_crossover_support(n, S_pop(), abc, info, P, S_new(), s));
@@ -302,45 +340,46 @@ class Run {
         z16_valid = true;
       }
       for (int it = 0; it < k; ++it) {
-        SPRING_TRY(launch_col_pm16(n, wh(), M, NB, s16, s));
+        SPRING_TRY(launch_col_pm16(n, wh(), Mall, NB, s16, s));
         SPRING_TRY(launch_row_iter16(n, alg, wh(), xh(), S, NB, prm.beta, prm.chi, s16, s));
       }
       x16_newer = true;
       return SPRING_OK;
     }
     if (iteration_path(n) == 1) {  // on chip: x in, x out; w is left stale
-      SPRING_TRY(launch_cluster_iter(n, alg, x, S, M, NB, prm.beta, prm.chi, k, s));
+      SPRING_TRY(launch_cluster_iter(n, alg, x, S, Mall, NBT, prm.beta, prm.chi, k, s, mgroup));
       z_valid = false;
       return SPRING_OK;
     }
     if (!z_valid) {
-      SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, NB, 1.0f, s));
+      SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, NBT, 1.0f, s));
       z_valid = true;
     }
     for (int it = 0; it < k; ++it) {
-      SPRING_TRY(launch_col_pm(n, w, M, NB, s));
-      SPRING_TRY(launch_row_iter(n, alg, w, x, S, NB, prm.beta, prm.chi, true, s));
+      SPRING_TRY(launch_col_pm(n, w, Mall, NBT, s, mgroup));
+      SPRING_TRY(launch_row_iter(n, alg, w, x, S, NBT, prm.beta, prm.chi, true, s));
     }
     return SPRING_OK;
   }
 
   spring_status shrinkwrap(float sigma, float tau) {
     SPRING_TRY(sync_x());
-    SPRING_TRY(launch_smooth(n, x, sm0, sm1, NB, sigma, imgmax, s));
-    return launch_threshold(n, sm1, imgmax, tau, S, NB, s);
+    SPRING_TRY(launch_smooth(n, x, sm0, sm1, NBT, sigma, imgmax, s));
+    return launch_threshold(n, sm1, imgmax, tau, S, NBT, s);
   }
 
-  spring_status shrinkwrap_area(float sigma, const int64_t* a) {
+  // area k of the statistics (0: alpha_best, 2: alpha_eval), each pattern's own
+  spring_status shrinkwrap_area(float sigma, int k) {
     SPRING_TRY(sync_x());
-    SPRING_TRY(launch_smooth(n, x, sm0, sm1, NB, sigma, nullptr, s));
-    return launch_select_area(n, sm1, a, 0, S, NB, s);
+    SPRING_TRY(launch_smooth(n, x, sm0, sm1, NBT, sigma, nullptr, s));
+    return launch_select_area(n, sm1, alpha + k, 4, S, NBT, s, NB);
   }
 
   spring_status errors() {
     SPRING_TRY(sync_x());
-    SPRING_TRY(launch_row_fft(n, -1, x, w, S, NB, 1.0f, s));
-    SPRING_TRY(launch_col_err(n, w, M, NB, part_err, s));
-    SPRING_TRY(launch_err_finalize(n, part_err, NB, err, status, s));
+    SPRING_TRY(launch_row_fft(n, -1, x, w, S, NBT, 1.0f, s));
+    SPRING_TRY(launch_col_err(n, w, Mall, NBT, part_err, s, mgroup));
+    SPRING_TRY(launch_err_finalize(n, part_err, NBT, err, status, s));
     z_valid = z16_valid = false;  // w served as scratch
     return SPRING_OK;
   }
@@ -374,9 +413,9 @@ class Run {
       SPRING_TRY(shrinkwrap(sigma, tau));
     }
     SPRING_TRY(sequence(ia, er));
-    SPRING_TRY(shrinkwrap_area(sigma, alpha + 0));  // UpdateSupportSize(alpha_best)
+    SPRING_TRY(shrinkwrap_area(sigma, 0));  // UpdateSupportSize(alpha_best)
     SPRING_TRY(sequence(ia, er));
-    SPRING_TRY(shrinkwrap_area(sigma, alpha + 2));  // UpdateSupportSize(alpha_eval)
+    SPRING_TRY(shrinkwrap_area(sigma, 2));  // UpdateSupportSize(alpha_eval)
     SPRING_TRY(iterations(0, prm.seq_eval));        // EvalSequence: ER
     SPRING_TRY(errors());                           // GetError
     SPRING_TRY(shrinkwrap(sigma, tau));
@@ -412,10 +451,10 @@ class Run {
       if (blk <= R - 2) {
         SPRING_TRY(shrinkwrap(sigma, tau));
       } else if (blk == R - 1) {
-        SPRING_TRY(shrinkwrap_area(sigma, alpha + 0));  // UpdateSupportSize(alpha_best)
+        SPRING_TRY(shrinkwrap_area(sigma, 0));  // UpdateSupportSize(alpha_best)
       } else {
         SPRING_TRY(iterations(alg, last - prm.er_tail));
-        SPRING_TRY(shrinkwrap_area(sigma, alpha + 2));  // UpdateSupportSize(alpha_eval)
+        SPRING_TRY(shrinkwrap_area(sigma, 2));  // UpdateSupportSize(alpha_eval)
         SPRING_TRY(iterations(0, prm.er_tail));         // EvalSequence: ER
         SPRING_TRY(errors());                           // GetError
         SPRING_TRY(shrinkwrap(sigma, tau));
@@ -432,42 +471,54 @@ class Run {
       SPRING_TRY(improve_independent(g, sigma, tau));
       SPRING_CUDA(cudaMemsetAsync(repl, 0, P, s));
       SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
-      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s));
+      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + 8 * (g - 1), s));
       return monitor(g);
     }
-    SPRING_TRY(crossover(g));
-    SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, best, s));
-    SPRING_TRY(launch_area_stats(n, S_pop(), best, P, g, G, alpha, s));
+    // the GA steps pattern by pattern, the improvement of all K patterns' populations at once
+    for (cq = 0; cq < K; ++cq) {
+      SPRING_TRY(crossover(g));
+      SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, bestq(), s));
+      SPRING_TRY(launch_area_stats(n, S_pop(), bestq(), P, g, G, alphaq(), s));
+    }
+    cq = 0;
     if (prm.schedule == 1)
       SPRING_TRY(improve_paper(g, sigma, tau));
     else
       SPRING_TRY(improve(sigma, tau));
-    SPRING_TRY(launch_select(n, x_pop(), S_pop(), err_pop(), x_new(), S_new(), err_new(), P, repl, s));
-    SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
-    SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, stats + 8 * (g - 1), s));
-    return monitor(g);
+    for (cq = 0; cq < K; ++cq) {
+      SPRING_TRY(launch_select(n, x_pop(), S_pop(), err_pop(), x_new(), S_new(), err_new(), P, repl, s));
+      SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
+      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + 8 * (g - 1), s));
+      SPRING_TRY(monitor(g));
+    }
+    cq = 0;
+    return SPRING_OK;
   }
 
   // the average reconstruction's error every generation (gen_stats column 3)
   spring_status monitor(int g) {
     if (!prm.monitor_avg || g == G) return SPRING_OK;  // generation G: finish() computes it
     SPRING_TRY(average_and_error());
-    SPRING_CUDA(cudaMemcpyAsync(stats + 8 * (g - 1) + 3, err_avg, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SPRING_CUDA(cudaMemcpyAsync(statsq() + 8 * (g - 1) + 3, err_avgq(), sizeof(double), cudaMemcpyDeviceToDevice, s));
     return SPRING_OK;
   }
 
-  // Average (Eq. avgrec) of the final population and its error
-  spring_status finish() { return average_and_error(); }
+  // Average (Eq. avgrec) of each pattern's final population and its error
+  spring_status finish() {
+    for (cq = 0; cq < K; ++cq) SPRING_TRY(average_and_error());
+    cq = 0;
+    return SPRING_OK;
+  }
 
   spring_status average_and_error() {
     SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
-    SPRING_TRY(launch_argmin(err_pop(), P, best, s));
-    SPRING_TRY(launch_pairs_onto_best(P, best, ix, ir, s));
+    SPRING_TRY(launch_argmin(err_pop(), P, bestq(), s));
+    SPRING_TRY(launch_pairs_onto_best(P, bestq(), ix, ir, s));
     SPRING_TRY(align(ix, ir, info, ph));
-    SPRING_TRY(launch_average(n, x_pop(), S_pop(), info, ph, best, P, avg, Savg, s));
-    SPRING_TRY(launch_row_fft(n, -1, avg, w_new(), Savg, 1, 1.0f, s));
-    SPRING_TRY(launch_col_err(n, w_new(), M, 1, part_err, s));
-    SPRING_TRY(launch_err_finalize(n, part_err, 1, err_avg, status, s));
+    SPRING_TRY(launch_average(n, x_pop(), S_pop(), info, ph, bestq(), P, avgq(), Savgq(), s));
+    SPRING_TRY(launch_row_fft(n, -1, avgq(), w_new(), Savgq(), 1, 1.0f, s));
+    SPRING_TRY(launch_col_err(n, w_new(), Mq(), 1, part_err, s));
+    SPRING_TRY(launch_err_finalize(n, part_err, 1, err_avgq(), status, s));
     return SPRING_OK;
   }
 
@@ -524,28 +575,31 @@ class Run {
     return SPRING_OK;
   }
 
-  // after the stream has completed: copy results to host buffers
-  spring_status collect(spring_result* out) {
+  // after the stream has completed: copy results to host buffers (K of them for a batch)
+  spring_status collect(spring_result* outs) {
     int st[4] = {0, 0, 0, 0};
-    int32_t b = 0;
-    double ea = 0.0;
     SPRING_CUDA(cudaMemcpy(st, status, sizeof(st), cudaMemcpyDeviceToHost));
-    SPRING_CUDA(cudaMemcpy(&b, best, sizeof(b), cudaMemcpyDeviceToHost));
-    SPRING_CUDA(cudaMemcpy(&ea, err_avg, sizeof(ea), cudaMemcpyDeviceToHost));
-    double eb = 0.0;
-    SPRING_CUDA(cudaMemcpy(&eb, err_pop() + b, sizeof(eb), cudaMemcpyDeviceToHost));
-    out->final_error_avg = ea;
-    out->final_error_best = eb;
-    if (out->rho_avg) SPRING_CUDA(cudaMemcpy(out->rho_avg, avg, sizeof(float2) * nn(), cudaMemcpyDeviceToHost));
-    if (out->rho_best)
-      SPRING_CUDA(cudaMemcpy(out->rho_best, x_pop() + (size_t)b * nn(), sizeof(float2) * nn(), cudaMemcpyDeviceToHost));
-    if (out->support_avg) SPRING_CUDA(cudaMemcpy(out->support_avg, Savg, nn(), cudaMemcpyDeviceToHost));
-    if (out->gen_stats) {
-      SPRING_CUDA(cudaMemcpy(out->gen_stats, stats, sizeof(double) * 8 * G, cudaMemcpyDeviceToHost));
-      out->gen_stats[8 * (G - 1) + 3] = ea;
-      for (int g = 1; g < first_gen; ++g)  // generations run before a resume
-        for (int k = 0; k < 8; ++k) out->gen_stats[8 * (g - 1) + k] = std::numeric_limits<double>::quiet_NaN();
+    for (cq = 0; cq < K; ++cq) {
+      spring_result* out = outs + cq;
+      int32_t b = 0;
+      double ea = 0.0, eb = 0.0;
+      SPRING_CUDA(cudaMemcpy(&b, bestq(), sizeof(b), cudaMemcpyDeviceToHost));
+      SPRING_CUDA(cudaMemcpy(&ea, err_avgq(), sizeof(ea), cudaMemcpyDeviceToHost));
+      SPRING_CUDA(cudaMemcpy(&eb, err_pop() + b, sizeof(eb), cudaMemcpyDeviceToHost));
+      out->final_error_avg = ea;
+      out->final_error_best = eb;
+      if (out->rho_avg) SPRING_CUDA(cudaMemcpy(out->rho_avg, avgq(), sizeof(float2) * nn(), cudaMemcpyDeviceToHost));
+      if (out->rho_best)
+        SPRING_CUDA(cudaMemcpy(out->rho_best, x_pop() + (size_t)b * nn(), sizeof(float2) * nn(), cudaMemcpyDeviceToHost));
+      if (out->support_avg) SPRING_CUDA(cudaMemcpy(out->support_avg, Savgq(), nn(), cudaMemcpyDeviceToHost));
+      if (out->gen_stats) {
+        SPRING_CUDA(cudaMemcpy(out->gen_stats, statsq(), sizeof(double) * 8 * G, cudaMemcpyDeviceToHost));
+        out->gen_stats[8 * (G - 1) + 3] = ea;
+        for (int g = 1; g < first_gen; ++g)  // generations run before a resume
+          for (int k = 0; k < 8; ++k) out->gen_stats[8 * (g - 1) + k] = std::numeric_limits<double>::quiet_NaN();
+      }
     }
+    cq = 0;
     if (st[0]) {
       set_error("non-finite Fourier error in the run");
       return SPRING_E_NUMERIC;
@@ -945,14 +999,17 @@ spring_status spring_problem_destroy(spring_problem* pr) {
   return SPRING_OK;
 }
 
-// A blocking run: from Initialize (from = NULL) or from a saved population, up to
-// generation stop (0 = all, then the average into *out), saving the population if asked.
-static spring_status run_blocking(spring_problem* pr, const spring_params* p, const spring_population* from,
-                                  int stop, spring_population* save, spring_result* out) {
+// A blocking run of K problems of one side (K = 1: a single run; seeds[q] is problem q's
+// seed): from Initialize (from = NULL) or from a saved population, up to generation stop
+// (0 = all, then the averages into out[0..K)), saving the population if asked.
+static spring_status run_blocking_k(spring_problem* const* probs, int K, const uint64_t* seeds,
+                                    const spring_params* p, const spring_population* from, int stop,
+                                    spring_population* save, spring_result* out) {
+  spring_problem* pr = probs[0];
   SPRING_TRY(validate_params(pr->n, *p));
   spring_ctx* c = pr->ctx;
   SPRING_CUDA(cudaSetDevice(c->device));
-  const size_t fp = make_layout(pr->n, *p).total;
+  const size_t fp = make_layout(pr->n, *p, K).total;
   {
     std::lock_guard<std::mutex> lk(c->mu);
     if (!reserve(c, fp)) {
@@ -966,7 +1023,7 @@ static spring_status run_blocking(spring_problem* pr, const spring_params* p, co
     Run run;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__);
-    if (st == SPRING_OK) st = run.setup(pr, *p, s);
+    if (st == SPRING_OK) st = run.setup_batch(probs, K, seeds, *p, s);
     if (st == SPRING_OK && from) st = run.upload_population(*from);
     run.stop_after = stop;
     if (st == SPRING_OK) {
@@ -1004,9 +1061,13 @@ static spring_status run_blocking(spring_problem* pr, const spring_params* p, co
     }
     if (st == SPRING_OK && save) st = run.download_population(save);
     if (st == SPRING_OK && out) {
-      out->t_submit_s = out->t_admit_s = now_s();
+      const double t0 = now_s();
       st = run.collect(out);
-      out->t_done_s = now_s();
+      const double t1 = now_s();
+      for (int q = 0; q < K; ++q) {
+        out[q].t_submit_s = out[q].t_admit_s = t0;
+        out[q].t_done_s = t1;
+      }
     }
     run.release();
     if (s) {
@@ -1019,9 +1080,28 @@ static spring_status run_blocking(spring_problem* pr, const spring_params* p, co
   return st;
 }
 
+static spring_status run_blocking(spring_problem* pr, const spring_params* p, const spring_population* from,
+                                  int stop, spring_population* save, spring_result* out) {
+  return run_blocking_k(&pr, 1, &p->seed, p, from, stop, save, out);
+}
+
 spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_result* out) {
   if (!pr || !p || !out) return invalid("null argument");
   return run_blocking(pr, p, nullptr, 0, nullptr, out);
+}
+
+spring_status spring_mpr_run_batch(spring_problem* const* probs, int K, const spring_params* p,
+                                   const uint64_t* seeds, spring_result* out) {
+  if (!probs || !p || !seeds || !out) return invalid("null argument");
+  if (K <= 0) return invalid("batch size must be positive");
+  for (int q = 0; q < K; ++q) {
+    if (!probs[q]) return invalid("null problem in the batch");
+    if (probs[q]->n != probs[0]->n) return invalid("the problems of a batch must have the same side");
+    if (probs[q]->ctx != probs[0]->ctx) return invalid("the problems of a batch must share a context");
+  }
+  if (K > 1 && p->precision != 0) return invalid("batched runs keep FP32 storage (precision 0)");
+  if (K > 1 && p->mode != 0) return invalid("batched runs are memetic (mode 0)");
+  return run_blocking_k(probs, K, seeds, p, nullptr, 0, nullptr, out);
 }
 
 spring_status spring_mpr_run_until(spring_problem* pr, const spring_params* p, int g_stop,

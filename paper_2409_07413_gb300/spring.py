@@ -77,6 +77,7 @@ _SIGS = {
     "spring_problem_destroy": (_i, [_vp]),
     "spring_footprint_bytes": (C.c_size_t, [_i, C.POINTER(Params)]),
     "spring_mpr_run": (_i, [_vp, C.POINTER(Params), C.POINTER(Result)]),
+    "spring_mpr_run_batch": (_i, [_vp, _i, C.POINTER(Params), _vp, _vp]),
     "spring_submit": (_i, [_vp, _vp, C.POINTER(Params), C.POINTER(_u64)]),
     "spring_mpr_run_until": (_i, [_vp, C.POINTER(Params), _i, C.POINTER(Population)]),
     "spring_mpr_resume": (_i, [_vp, C.POINTER(Params), C.POINTER(Population), C.POINTER(Result)]),
@@ -528,6 +529,25 @@ class Context:
         _call("spring_problem_create_device", self.handle, I.shape[0], I.shape[1], _ptr(I),
               _ptr(mask), _ptr(support0), _stream(), C.byref(h))
         return Problem(self, h, I.shape[0])
+
+    def run_batch(self, problems, p: Params, seeds, want_arrays=True):
+        """Blocking batched run of same-side problems (problem q with seeds[q]); returns
+        one result dict per problem, each equal to problems[q].run with that seed."""
+        import numpy as np
+        K = len(problems)
+        if len(seeds) != K:
+            raise ValueError("one seed per problem")
+        hs = (C.c_void_p * K)(*[pr.handle for pr in problems])
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        rs = (Result * K)()
+        keeps = []
+        for q in range(K):
+            r, keep = _result_buffers(problems[q].n if want_arrays else None, p.generations)
+            rs[q] = r
+            keeps.append(keep)
+        _call("spring_mpr_run_batch", C.cast(hs, C.c_void_p), K, C.byref(p),
+              sd.ctypes.data_as(C.c_void_p), C.cast(rs, C.c_void_p))
+        return [_result_dict(rs[q], keeps[q]) for q in range(K)]
 
     def submit(self, problem, p: Params) -> int:
         t = C.c_uint64()
