@@ -30,10 +30,10 @@ import numpy as np
 SIDES = (128, 192, 256, 512)
 
 
-def make_set(seed, count, variants=4):
+def make_set(seed, count, variants=4, sides_from=SIDES):
     from paper_2409_07413_gb300 import synthetic
     rng = np.random.default_rng(seed)
-    sides = rng.choice(SIDES, size=count)
+    sides = rng.choice(sides_from, size=count)
     cache = {}
     out = []
     for i, n in enumerate(sides):
@@ -51,18 +51,20 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--modes", default="served,plain,batched")
     ap.add_argument("--batch-pixels", type=float, default=2.0 ** 26)
+    ap.add_argument("--sides", default=",".join(map(str, SIDES)))
     a = ap.parse_args()
+    sides = tuple(int(v) for v in a.sides.split(","))
     import torch  # noqa: F401  (device selection through the library)
     from paper_2409_07413_gb300 import spring
     prm = dict(pop=32, iters_per_gen=200, generations=a.generations, algorithm=2, beta=0.9,
                sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)
-    jobs = make_set(a.seed, a.patterns)
+    jobs = make_set(a.seed, a.patterns, sides_from=sides)
     ctx = spring.Context(0)
-    for n in SIDES:  # tune each side once, outside the timed region
+    for n in sides:  # tune each side once, outside the timed region
         spring.autotune(n, 2 * prm["pop"])
     work_px = sum(2 * prm["pop"] * prm["iters_per_gen"] * prm["generations"] * n * n for n, _, _ in jobs)
     out = {"benchmark": "batched uneven", "patterns": len(jobs),
-           "sides": {str(n): int(sum(1 for j in jobs if j[0] == n)) for n in SIDES}, "params": prm,
+           "sides": {str(n): int(sum(1 for j in jobs if j[0] == n)) for n in sides}, "params": prm,
            "iteration_pixels": work_px}
     per_mode = {}
     for mode in a.modes.split(","):
@@ -71,7 +73,7 @@ def main():
         errs = [None] * len(jobs)
         t0 = time.perf_counter()
         if mode == "batched":
-            for n in SIDES:
+            for n in sides:
                 idx = [i for i, j in enumerate(jobs) if j[0] == n]
                 K = max(1, int(a.batch_pixels // (2 * prm["pop"] * n * n)))
                 for c in range(0, len(idx), K):
