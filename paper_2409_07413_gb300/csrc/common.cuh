@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <stdint.h>
 
 #include <string>
@@ -39,18 +40,40 @@ void launch_begin(int kclass, cudaStream_t s);
 void launch_end(int kclass, cudaStream_t s, double bytes);
 
 // ------------------------------------------------------------------ sizes and plans
-inline bool valid_n(int n) {
-  return n == 64 || n == 128 || n == 192 || n == 256 || n == 512 || n == 1024;
+// The supported sides: even N in [64, 1024] of the form 2^a 3^b with b <= 1, in
+// ascending order.  side_slot(N) is N's index (-1 if unsupported).
+constexpr int N_SIDES = 9;
+__host__ __device__ constexpr int side_at(int i) {
+  return i == 0 ? 64 : i == 1 ? 96 : i == 2 ? 128 : i == 3 ? 192 : i == 4 ? 256
+       : i == 5 ? 384 : i == 6 ? 512 : i == 7 ? 768 : i == 8 ? 1024 : 0;
 }
+__host__ __device__ constexpr int side_slot(int n) {
+  for (int i = 0; i < N_SIDES; ++i)
+    if (side_at(i) == n) return i;
+  return -1;
+}
+inline bool valid_n(int n) { return side_slot(n) >= 0; }
 
 // Per-device constant tables, built once on the host in double precision:
 //   tw:      e^{-2 pi i k / N}, k < N, for every supported N (rounded once to float),
-//            at offset tw_offset(N);
+//            at offset tw_offset(N) (the sides' tables one after another);
 //   rot_cos, rot_sin: Q30 fixed point cos/sin((pi/2) k / 1024), k < 1024 (crossover map).
 __host__ __device__ constexpr int tw_offset(int n) {
-  return n == 64 ? 0 : n == 128 ? 64 : n == 192 ? 192 : n == 256 ? 384 : n == 512 ? 640 : 1152;
+  int o = 0;
+  for (int i = 0; i < N_SIDES && side_at(i) != n; ++i) o += side_at(i);
+  return o;
 }
-constexpr int TW_TOTAL = 1152 + 1024;
+constexpr int TW_TOTAL = tw_offset(0);  // past the last side: the sum of all sides
+// the twiddle tables of every side into tw[TW_TOTAL]
+inline void fill_twiddles(float2* tw) {
+  for (int i = 0; i < N_SIDES; ++i) {
+    const int n = side_at(i);
+    for (int k = 0; k < n; ++k) {
+      const double ang = -2.0 * 3.14159265358979323846 * (double)k / (double)n;
+      tw[tw_offset(n) + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  }
+}
 struct DeviceTables {
   const float2* tw;
   const long long* rot_cos;

@@ -174,28 +174,36 @@ struct NamedSync {
 
 // ------------------------------------------------------------------ plans
 // A plan: transform length N, elements per thread E (T = N / E threads per transform),
-// radices R0, R1, R2 (R2 = 0: two stages).  E is a multiple of every radix.
-template <int N_, int E_, int R0_, int R1_, int R2_ = 0>
+// radices R0, R1, R2, R3 (R2 = 0: two stages; R3 = 0: at most three).  E is a multiple of
+// every radix.
+template <int N_, int E_, int R0_, int R1_, int R2_ = 0, int R3_ = 0>
 struct PlanT {
-  static constexpr int N = N_, E = E_, R0 = R0_, R1 = R1_, R2 = R2_, T = N_ / E_;
-  static_assert(R0_ * R1_ * (R2_ ? R2_ : 1) == N_, "radices must multiply to N");
-  static_assert(E_ % R0_ == 0 && E_ % R1_ == 0 && (R2_ == 0 || E_ % R2_ == 0), "E vs radices");
+  static constexpr int N = N_, E = E_, R0 = R0_, R1 = R1_, R2 = R2_, R3 = R3_, T = N_ / E_;
+  static_assert(R0_ * R1_ * (R2_ ? R2_ : 1) * (R3_ ? R3_ : 1) == N_, "radices must multiply to N");
+  static_assert(R3_ == 0 || R2_ != 0, "a fourth stage needs a third");
+  static_assert(E_ % R0_ == 0 && E_ % R1_ == 0 && (R2_ == 0 || E_ % R2_ == 0) && (R3_ == 0 || E_ % R3_ == 0),
+                "E vs radices");
 };
 // default plan for each supported N
 template <int N> struct Plan;
 template <> struct Plan<64>   : PlanT<64, 8, 8, 8> {};
+template <> struct Plan<96>   : PlanT<96, 24, 4, 8, 3> {};
 template <> struct Plan<128>  : PlanT<128, 16, 8, 16> {};
 template <> struct Plan<192>  : PlanT<192, 24, 8, 8, 3> {};
 template <> struct Plan<256>  : PlanT<256, 16, 16, 16> {};
+template <> struct Plan<384>  : PlanT<384, 24, 8, 4, 4, 3> {};
 template <> struct Plan<512>  : PlanT<512, 16, 8, 8, 8> {};
+template <> struct Plan<768>  : PlanT<768, 24, 8, 8, 4, 3> {};
 template <> struct Plan<1024> : PlanT<1024, 32, 32, 32> {};
 
-// shared-memory elements of one transform's padded exchange buffer
+// shared-memory elements of one transform's padded exchange buffer: the largest layout
+// of a stage whose outputs go through shared memory (every stage but the last)
 template <class P>
 __host__ __device__ constexpr int pad_elems_p() {
   int a = P::N + P::N / P::R0;
   int b = P::R2 ? P::N + P::N / P::R1 : 0;
-  return a > b ? a : b;
+  int c = P::R3 ? P::N + P::N / P::R2 : 0;
+  return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 template <int N>
 __host__ __device__ constexpr int pad_elems() { return pad_elems_p<Plan<N>>(); }
@@ -239,7 +247,7 @@ __device__ __forceinline__ void stage_twiddle(V (&b)[E], int t, const float2* __
   }
 }
 
-// radix-3 stages (N = 192 only) use direct table loads
+// radix-3 stages (sides 3 x 2^k) use direct table loads
 template <int N, int E, int NS, int DIR, class V>
 __device__ __forceinline__ void stage_twiddle3(V (&b)[E], int t, const float2* __restrict__ tw) {
   constexpr int T = N / E, R = 3, STEP = N / (NS * R);
@@ -310,7 +318,7 @@ __device__ __forceinline__ void stage_tw(V (&b)[E], int t, const float2* __restr
 template <class P, int DIR, bool PAD, int STRIDE, bool TAIL = true, class Sync, class V>
 __device__ __forceinline__ void fft_plan(V (&v)[P::E], V* sm, int t, const float2* __restrict__ tw,
                                          const Sync& sync) {
-  constexpr int N = P::N, E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2;
+  constexpr int N = P::N, E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2, R3 = P::R3;
   V b[E];
   // stage 0 (NS = 1): inputs j + r N/R0 are the registers u + r E/R0
 #pragma unroll
@@ -334,13 +342,27 @@ __device__ __forceinline__ void fft_plan(V (&v)[P::E], V* sm, int t, const float
     stage_store<N, E, R1, R0, PAD, STRIDE>(b, sm, t);
     sync();
     stage_load<N, E, R2, R0 * R1, R0, PAD, STRIDE>(b, sm, t);
-    if (TAIL) sync();
+    if (TAIL || R3 != 0) sync();
     stage_tw<N, E, R2, R0 * R1, DIR>(b, t, tw);
     stage_dft<N, E, R2, DIR>(b);
+    if constexpr (R3 == 0) {
 #pragma unroll
-    for (int u = 0; u < E / R2; ++u)
+      for (int u = 0; u < E / R2; ++u)
 #pragma unroll
-      for (int r = 0; r < R2; ++r) v[u + r * (E / R2)] = b[u * R2 + r];
+        for (int r = 0; r < R2; ++r) v[u + r * (E / R2)] = b[u * R2 + r];
+    } else {
+      // stage 3 (NS = R0 R1 R2)
+      stage_store<N, E, R2, R0 * R1, PAD, STRIDE>(b, sm, t);
+      sync();
+      stage_load<N, E, R3, R0 * R1 * R2, R0 * R1, PAD, STRIDE>(b, sm, t);
+      if (TAIL) sync();
+      stage_tw<N, E, R3, R0 * R1 * R2, DIR>(b, t, tw);
+      stage_dft<N, E, R3, DIR>(b);
+#pragma unroll
+      for (int u = 0; u < E / R3; ++u)
+#pragma unroll
+        for (int r = 0; r < R3; ++r) v[u + r * (E / R3)] = b[u * R3 + r];
+    }
   }
 }
 

@@ -11,10 +11,13 @@
 namespace spring {
 
 extern template spring_status run_fft_op<64>(const FftOp&, cudaStream_t, bool);
+extern template spring_status run_fft_op<96>(const FftOp&, cudaStream_t, bool);
 extern template spring_status run_fft_op<128>(const FftOp&, cudaStream_t, bool);
 extern template spring_status run_fft_op<192>(const FftOp&, cudaStream_t, bool);
 extern template spring_status run_fft_op<256>(const FftOp&, cudaStream_t, bool);
+extern template spring_status run_fft_op<384>(const FftOp&, cudaStream_t, bool);
 extern template spring_status run_fft_op<512>(const FftOp&, cudaStream_t, bool);
+extern template spring_status run_fft_op<768>(const FftOp&, cudaStream_t, bool);
 extern template spring_status run_fft_op<1024>(const FftOp&, cudaStream_t, bool);
 
 static spring_status prepare_once(int n);
@@ -23,37 +26,31 @@ static spring_status dispatch(int n, const FftOp& op, cudaStream_t s, bool prep 
   if (!prep) SPRING_TRY(prepare_once(n));
   switch (n) {
     case 64: return run_fft_op<64>(op, s, prep);
+    case 96: return run_fft_op<96>(op, s, prep);
     case 128: return run_fft_op<128>(op, s, prep);
     case 192: return run_fft_op<192>(op, s, prep);
     case 256: return run_fft_op<256>(op, s, prep);
+    case 384: return run_fft_op<384>(op, s, prep);
     case 512: return run_fft_op<512>(op, s, prep);
+    case 768: return run_fft_op<768>(op, s, prep);
     case 1024: return run_fft_op<1024>(op, s, prep);
   }
   return invalid("unsupported pattern side " + std::to_string(n));
 }
 
-static int side_index(int n) {
-  switch (n) {
-    case 64: return 0;
-    case 128: return 1;
-    case 192: return 2;
-    case 256: return 3;
-    case 512: return 4;
-    case 1024: return 5;
-  }
-  return -1;
-}
+static int side_index(int n) { return side_slot(n); }
 
 // ------------------------------------------------------------------ variant table
 // Launch-shape variants of the two per-iteration passes, per side (see k_fft.cuh); the
 // defaults are the fastest measured on a GB300 at 33.5 M pixels per launch.
 static std::mutex g_var_mu;
-static int g_row_var[6] = {0, 5, 1, 0, 6, 5};
-static int g_col_var[6] = {0, 2, 0, 0, 0, 3};
-static bool g_tuned[6] = {false, false, false, false, false, false};
+// (sides 64, 96, 128, 192, 256, 384, 512, 768, 1024)
+static int g_row_var[N_SIDES] = {0, 0, 5, 1, 0, 1, 6, 1, 5};
+static int g_col_var[N_SIDES] = {0, 0, 2, 0, 0, 0, 0, 3, 3};
+static bool g_tuned[N_SIDES] = {};
 // iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
 // (N <= 256, k_cluster.cu); chosen by the autotuner, the two-pass path until then
-static int g_path[6] = {0, 0, 0, 0, 0, 0};
+static int g_path[N_SIDES] = {};
 
 int iteration_path(int n) {
   const int si = side_index(n);

@@ -56,23 +56,30 @@ constexpr int ERR_W = 16;  // column tile of the error pass (layout of its parti
 // alternative column-pass plans
 template <int N> struct AltPlan;
 template <> struct AltPlan<64>   : PlanT<64, 16, 16, 4> {};
+template <> struct AltPlan<96>   : PlanT<96, 24, 3, 8, 4> {};
 template <> struct AltPlan<128>  : PlanT<128, 16, 16, 8> {};
 template <> struct AltPlan<192>  : PlanT<192, 24, 3, 8, 8> {};
 template <> struct AltPlan<256>  : PlanT<256, 32, 32, 8> {};
+template <> struct AltPlan<384>  : PlanT<384, 24, 3, 8, 4, 4> {};
 template <> struct AltPlan<512>  : PlanT<512, 8, 8, 8, 8> {};
+template <> struct AltPlan<768>  : PlanT<768, 24, 3, 8, 8, 4> {};
 template <> struct AltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
 // row plan of the FP16-storage iteration pass
 template <int N> struct Row16Plan : Plan<N> {};
 template <> struct Row16Plan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
-// plans of the paired column pass (two columns per thread, E <= 16)
+// plans of the paired column pass (two columns per thread; the fewest elements per
+// thread that the radices allow)
 template <int N> struct Col2Plan;
 template <> struct Col2Plan<64>   : PlanT<64, 8, 8, 8> {};
+template <> struct Col2Plan<96>   : PlanT<96, 12, 4, 4, 2, 3> {};
 template <> struct Col2Plan<128>  : PlanT<128, 8, 8, 4, 4> {};
 template <> struct Col2Plan<192>  : PlanT<192, 24, 8, 8, 3> {};
 template <> struct Col2Plan<256>  : PlanT<256, 8, 8, 8, 4> {};
+template <> struct Col2Plan<384>  : Plan<384> {};
 template <> struct Col2Plan<512>  : PlanT<512, 8, 8, 8, 8> {};
+template <> struct Col2Plan<768>  : Plan<768> {};
 template <> struct Col2Plan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
 // alternative row-pass plans (fewer elements per thread; T = 64 rows sync by named barrier)
@@ -81,6 +88,7 @@ template <> struct RowAltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 template <> struct RowAltPlan<512> : PlanT<512, 8, 8, 8, 8> {};
 template <> struct RowAltPlan<256> : PlanT<256, 32, 32, 8> {};
 template <> struct RowAltPlan<128> : PlanT<128, 16, 16, 8> {};
+template <> struct RowAltPlan<96> : PlanT<96, 12, 4, 4, 2, 3> {};
 
 // FP16 storage of the iteration buffers (precision 1): x as half2 scaled by the problem's
 // power of two s16 (chosen from ||M||_2 so that every stored value stays well inside the
@@ -504,6 +512,14 @@ inline spring_status colT_launch(const FftOp& op, cudaStream_t s, bool prepare_o
   return SPRING_OK;
 }
 
+// rows of one TMA box of the column pass: the largest divisor of N of at most 256 (a box
+// dimension is limited to 256 elements)
+__host__ __device__ constexpr int tma_box_rows(int n) {
+  int r = n < 256 ? n : 256;
+  while (n % r) --r;
+  return r;
+}
+
 // Persistent column pass (COL_PM) fed by TMA.  Tiles (image, 16- or 8-column strip) are
 // taken in a grid-stride sequence; the next tile's bulk tensor copy into the second
 // shared buffer is issued before the current tile is transformed, so HBM reads overlap the
@@ -514,7 +530,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 256 ? 2 : 1))
     k_col_pm_tma(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap mmap,
                  ColArgs a, int ntiles, int* status) {
   constexpr int N = P::N, E = P::E, T = P::T, STRIPS = N / W;
-  constexpr int BOXR = N > 256 ? 256 : N, NBOX = N / BOXR;
+  constexpr int BOXR = tma_box_rows(N), NBOX = N / BOXR;
   constexpr uint32_t TILE_BYTES = (uint32_t)N * W * 8 + (uint32_t)N * W * 4;  // w tile + M strip
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // TMA destinations 1024-byte aligned (the launch reserves the slack)
@@ -609,8 +625,13 @@ inline spring_status row_launch(const FftOp& op, cudaStream_t s, bool prepare_on
 }
 
 template <int N, int W>
-constexpr int fit_w() {  // keep the column tile within shared memory and 1024 threads
-  return ((size_t)N * W * 8 > 200 * 1024 || W * Plan<N>::T > 1024) ? W / 2 : W;
+constexpr int fit_w() {  // keep the column tile and its modulus strip within shared memory and 1024 threads
+  return ((size_t)N * W * 12 > 216 * 1024 || W * Plan<N>::T > 1024) ? W / 2 : W;
+}
+
+template <int N>
+constexpr int tma_w() {  // the TMA pass holds two tiles and two modulus strips
+  return (size_t)2 * N * 16 * 12 + 1024 > 220 * 1024 ? 8 : 16;
 }
 
 template <int N, int W>
@@ -646,7 +667,7 @@ inline spring_status col_launch(const FftOp& op, cudaStream_t s, bool prepare_on
 // the TMA column pass: tensor map of the batch (floats: 2N x N x batch), box 2W x min(N,256)
 template <class P, int W>
 inline spring_status col_pm_tma_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
-  constexpr int N = P::N, BOXR = N > 256 ? 256 : N;
+  constexpr int N = P::N, BOXR = tma_box_rows(N);
   const size_t smem = (size_t)2 * N * W * (sizeof(float2) + sizeof(float)) + 1024;
   if (prepare_only) return allow_smem(k_col_pm_tma<P, W>, smem);
   if (op.ca.batch < 1) return SPRING_OK;
@@ -691,7 +712,7 @@ inline spring_status col_variant(const FftOp& op, cudaStream_t s, bool prep) {
     case 2: return col_launch<Plan<N>, fit_w<N, 32>(), MODE>(op, s, prep);
     case 3: return col_launch<Plan<N>, 8, MODE>(op, s, prep);
     case 4:
-      if constexpr (MODE == COL_PM) return col_pm_tma_launch<Plan<N>, (N >= 1024 ? 8 : 16)>(op, s, prep);
+      if constexpr (MODE == COL_PM) return col_pm_tma_launch<Plan<N>, tma_w<N>()>(op, s, prep);
       return col_launch<Plan<N>, 16, MODE>(op, s, prep);
     case 5:
       if constexpr (MODE == COL_PM) return col_pm_tma_launch<Plan<N>, 8>(op, s, prep);

@@ -47,13 +47,8 @@ static spring_status noalloc_setup(NoallocDevice** out) {
     d.scratch = static_cast<unsigned char*>(p);
     SPRING_CUDA(cudaGetSymbolAddress(&p, g_noalloc_twiddle));
     d.tw = static_cast<float2*>(p);
-    const int ns[6] = {64, 128, 192, 256, 512, 1024};
     std::vector<float2> tw(TW_TOTAL);
-    for (int a = 0; a < 6; ++a)
-      for (int k = 0; k < ns[a]; ++k) {
-        const double ang = -2.0 * 3.14159265358979323846 * (double)k / (double)ns[a];
-        tw[tw_offset(ns[a]) + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-      }
+    fill_twiddles(tw.data());
     SPRING_CUDA(cudaMemcpyToSymbol(g_noalloc_twiddle, tw.data(), sizeof(float2) * TW_TOTAL));
     d.ready = true;
   }

@@ -134,15 +134,8 @@ spring_status device_tables(DeviceTables* out) {
   }
   std::lock_guard<std::mutex> lk(g_tab_mu);
   if (!g_tab_ok[dev]) {
-    const int ns[6] = {64, 128, 192, 256, 512, 1024};
     std::vector<float2> tw(TW_TOTAL);
-    for (int a = 0; a < 6; ++a) {
-      const int n = ns[a];
-      for (int k = 0; k < n; ++k) {
-        const double ang = -2.0 * 3.14159265358979323846 * (double)k / (double)n;
-        tw[tw_offset(n) + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-      }
-    }
+    fill_twiddles(tw.data());
     std::vector<long long> rc(1024), rs(1024);
     for (int k = 0; k < 1024; ++k) {
       const double th = (3.14159265358979323846 / 2.0) * (double)k / 1024.0;

@@ -129,7 +129,7 @@ def config_pattern(name: str, seed: int = 0) -> Pattern:
                    99.9th-percentile saturation.
     ``ell1024``    1024x1024, 200 px extent, 1e8 photons, hole r=24, 30-row gap (a split
                    two-panel detector; no saturation).
-    ``ellN``       N in {128, 192, 256, 512}: extent 0.25 N, photons log-uniform in
+    ``ellN``       any other supported N (96 ... 768): extent 0.25 N, photons log-uniform in
                    [1e6, 1e7], beamstop r = N/40, gap N/25 rows.
     """
     if name == "sphere64":

@@ -10,7 +10,7 @@ from paper_2409_07413_gb300 import synthetic
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-SIDES = [64, 128, 192, 256, 512, 1024]
+SIDES = [64, 96, 128, 192, 256, 384, 512, 768, 1024]
 
 
 @pytest.fixture(scope="module")

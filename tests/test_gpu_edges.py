@@ -54,7 +54,7 @@ def test_empty_batches_and_zero_iterations(sp):
     assert np.array_equal(host(xg), c64(x))  # no iteration: untouched
 
 
-@pytest.mark.parametrize("n", [32, 96, 100, 384, 2048])
+@pytest.mark.parametrize("n", [32, 48, 100, 320, 576, 1536, 2048])
 def test_unsupported_sides_are_rejected(sp, n):
     x = dev(np.zeros((1, n, n), np.complex64))
     with pytest.raises(sp.SpringError) as e:

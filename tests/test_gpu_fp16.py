@@ -91,7 +91,7 @@ def fp16_model(x, S, M, mask, alg, beta, k, sx, ws):
     return xs
 
 
-@pytest.mark.parametrize("n", [64, 128, 192, 256, 512, 1024])
+@pytest.mark.parametrize("n", [64, 96, 128, 192, 256, 384, 512, 768, 1024])
 @pytest.mark.parametrize("alg,k", [(2, 1), (2, 6), (0, 3), (1, 3)])
 def test_iterate_fp16_within_storage_drift(sp, n, alg, k):
     B = 2
@@ -180,7 +180,8 @@ def test_mpr_fp16_matches_oracle_statistically(sp, ctx):
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
 
 
-@pytest.mark.parametrize("name", ["ell128", "ell192", "ell256", "ell512", "ell1024"])
+@pytest.mark.parametrize("name", ["ell96", "ell128", "ell192", "ell256", "ell384", "ell512", "ell768",
+                                  "ell1024"])
 def test_mpr_fp16_every_side(sp, ctx, name):
     pat = synthetic.config_pattern(name, 0)
     prob = ctx.problem(pat.intensities, pat.mask, pat.support0)

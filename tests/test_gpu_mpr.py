@@ -64,7 +64,8 @@ def test_mpr_sphere64_matches_oracle_statistically(sp, ctx):
     assert abs(np.median(rg) - np.median(ro)) <= 0.05
 
 
-@pytest.mark.parametrize("name", ["sphere64", "ell128", "ell192", "ell256", "ell512", "ell1024"])
+@pytest.mark.parametrize("name", ["sphere64", "ell96", "ell128", "ell192", "ell256", "ell384", "ell512",
+                                  "ell768", "ell1024"])
 def test_mpr_runs_at_every_side(sp, ctx, name):
     # a short run at each supported side exercises every kernel of the run at that side
     pat = synthetic.config_pattern(name, 0)
@@ -73,6 +74,24 @@ def test_mpr_runs_at_every_side(sp, ctx, name):
     prob.destroy()
     assert 0 < r["final_error_best"] < 1.5 and np.isfinite(r["final_error_avg"])
     assert r["support_avg"].sum() > 0 and np.isfinite(r["rho_avg"]).all()
+
+
+def test_mpr_ell96_matches_oracle_statistically(sp, ctx):
+    # a side of the form 3 x 2^k with a gap and saturation: the same bar as at 64
+    eg, eo = [], []
+    for seed in range(12):
+        pat = synthetic.config_pattern("ell96", seed)
+        prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
+        r = prob.run(sp.params(**C1, seed=seed))
+        prob.destroy()
+        o = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=seed, **C1)
+        eg.append(r["final_error_best"])
+        eo.append(o["final_error_best"])
+        assert np.isfinite(r["rho_avg"]).all()
+    eg, eo = np.array(eg), np.array(eo)
+    se = np.sqrt(eg.var(ddof=1) / len(eg) + eo.var(ddof=1) / len(eo))
+    print(f"ell96: mean E gpu {eg.mean():.4f} oracle {eo.mean():.4f} (se {se:.4f})")
+    assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
 
 
 def test_mpr_deterministic_and_graph_identical(sp, ctx):

@@ -14,7 +14,7 @@ from paper_2409_07413_gb300 import synthetic
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
-SIDES = [64, 128, 192, 256, 512, 1024]
+SIDES = [64, 96, 128, 192, 256, 384, 512, 768, 1024]
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +67,7 @@ def test_fft2(sp, n, inverse):
 
 
 # ----------------------------------------------------------------------------- a2 modulus
-@pytest.mark.parametrize("n", [64, 192, 512])
+@pytest.mark.parametrize("n", [64, 96, 192, 384, 512, 768])
 def test_project_modulus(sp, n):
     x, _ = synthetic.population_state(n + 1, 3, n)
     M, mask = synthetic.random_modulus(n, n, masked_frac=0.15)
@@ -91,7 +91,7 @@ def _expected_one_iteration(x, S, M, mask, alg, beta, chi):
     return np.where(in_c, m, out_c), m, out_c, margin
 
 
-@pytest.mark.parametrize("n", [64, 192, 256, 512])
+@pytest.mark.parametrize("n", [64, 96, 192, 256, 384, 512, 768])
 @pytest.mark.parametrize("alg", [0, 1, 2])
 @pytest.mark.parametrize("chi", [0.5, 1.0])
 def test_iterate_one_step(sp, n, alg, chi):
@@ -345,7 +345,7 @@ def test_initialize(sp, n):
 
 
 # ----------------------------------------------------------------------------- launch variants
-@pytest.mark.parametrize("n", [64, 128, 192, 256, 512, 1024])
+@pytest.mark.parametrize("n", SIDES)
 def test_kernel_variants_parity(sp, n):
     """Every launch-shape variant of the two iteration passes matches the oracle; row
     variants and the same-plan column variants are bit-identical to each other."""
@@ -368,9 +368,9 @@ def test_kernel_variants_parity(sp, n):
         sp.set_kernel_variant(n, *saved)
     # same plans give the same bits: row variants 0-4 share the default plan, 5-6 the
     # alternative row plan; column variants 0 and 2-7 the default column plan; the paired
-    # variants 8-9 share their own plan, which has the default's radices at 64, 192 and
-    # 512 and the alternative's at 1024
-    paired_like = {64: 0, 192: 0, 512: 0, 1024: 1}.get(n, 8)
+    # variants 8-9 share their own plan, which has the default's radices at 64, 192, 384,
+    # 512 and 768 and the alternative's at 1024
+    paired_like = {64: 0, 192: 0, 384: 0, 512: 0, 768: 0, 1024: 1}.get(n, 8)
     for rv in range(7):
         r0 = 0 if rv < 5 else 5
         for cv in (0, 2, 3, 4, 5, 6, 7):

@@ -37,7 +37,7 @@ def test_bruteforce_dft_is_unitary_dft(orc):
     assert np.allclose(orc.dft2_naive(x), np.fft.fft2(x, norm="ortho"), atol=1e-13)
 
 
-@pytest.mark.parametrize("n", [64, 96, 128, 192, 256, 512])
+@pytest.mark.parametrize("n", [64, 96, 128, 192, 256, 384, 512, 768])
 def test_fft_matches_numpy(orc, n):
     rng = np.random.default_rng(n)
     x = rand_c(rng, 2, n, n)
