@@ -7,8 +7,10 @@ by the plain path (spring_mpr_run one pattern at a time, in arrival order).
 
 Sizes are drawn from {128, 256, 512, 1024} with weights 0.4/0.3/0.2/0.1; every request
 runs P = 32, 5 generations x 200 RAAR iterations.  Latency is completion - arrival
-(arrival = scheduled submission time); both modes see the same requests and arrival times.
-Prints one JSON line.
+(arrival = scheduled submission time); service time is completion - admission (served: the
+library's admission and completion clocks of each request; plain: the run itself).  Both
+modes see the same requests and arrival times, and report percentiles overall and per
+side.  Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -63,7 +65,7 @@ def run_served(ctx, spring, reqs):
 
     th = threading.Thread(target=feeder)
     th.start()
-    lat, errs, sizes = [], [], []
+    lat, svc, errs, sizes = [], [], [], []
     done = 0
     while done < len(reqs):
         for i in range(len(reqs)):
@@ -73,6 +75,7 @@ def run_served(ctx, spring, reqs):
             if st == spring.OK:
                 tdone = time.monotonic() - t0
                 lat.append(tdone - reqs[i][0])
+                svc.append(r["t_done_s"] - r["t_admit_s"])
                 errs.append(r["final_error_best"])
                 sizes.append(reqs[i][1])
                 tickets[i] = -1
@@ -82,24 +85,27 @@ def run_served(ctx, spring, reqs):
     makespan = time.monotonic() - t0
     for pr in probs:  # after timing: freeing device memory may synchronise the device
         pr.destroy()
-    return lat, errs, sizes, makespan
+    return lat, svc, errs, sizes, makespan
 
 
 def run_plain(ctx, spring, reqs):
     """One pattern at a time in arrival order (waiting for arrivals)."""
     t0 = time.monotonic()
-    lat, errs, sizes = [], [], []
+    lat, svc, errs, sizes = [], [], [], []
     for (ta, n, pat, seed) in reqs:
         d = t0 + ta - time.monotonic()
         if d > 0:
             time.sleep(d)
+        ts = time.monotonic()
         pr = ctx.problem(pat.intensities, pat.mask, pat.support0)
         r = pr.run(spring.params(**PARAMS, seed=seed), want_arrays=False)
         pr.destroy()
-        lat.append(time.monotonic() - t0 - ta)
+        te = time.monotonic()
+        lat.append(te - t0 - ta)
+        svc.append(te - ts)
         errs.append(r["final_error_best"])
         sizes.append(n)
-    return lat, errs, sizes, time.monotonic() - t0
+    return lat, svc, errs, sizes, time.monotonic() - t0
 
 
 def main():
@@ -121,9 +127,14 @@ def main():
     work_px = sum(2 * PARAMS["pop"] * PARAMS["iters_per_gen"] * PARAMS["generations"] * r[1] ** 2 for r in reqs)
     for mode in a.modes.split(","):
         fn = run_served if mode == "served" else run_plain
-        lat, errs, sizes, span = fn(ctx, spring, reqs)
+        lat, svc, errs, sizes, span = fn(ctx, spring, reqs)
+        sizes = np.asarray(sizes)
         out[mode] = {"reconstructions_per_s": len(lat) / span, "makespan_s": span,
                      "iteration_pixels_per_s": work_px / span, **percentiles(lat),
+                     "service": percentiles(svc),
+                     "per_side": {str(n): {"latency": percentiles(np.asarray(lat)[sizes == n]),
+                                           "service": percentiles(np.asarray(svc)[sizes == n])}
+                                  for n in SIDES if (sizes == n).any()},
                      "mean_final_error_best": float(np.mean(errs))}
     ctx.close()
     print(json.dumps(out), flush=True)
