@@ -5,6 +5,11 @@ pass with the fused modulus projection) on random state.
 
 Prints one JSON line per side with each pass's average CUDA-event time, algorithmic bytes
 and GB/s (events are recorded on the launching stream around every launch).
+
+With --cufft it also times, as a reference point only, cuFFT through torch.fft on the same
+batch: the forward + inverse unitary 2D transform pair alone, and one whole RAAR iteration
+written as library calls (fft2, the masked modulus projection and the update as torch
+elementwise operations, ifft2).  Neither is on the library's path.
 """
 from __future__ import annotations
 
@@ -67,6 +72,43 @@ def run_fused(n, batch, iters, alg, warm=3):
             "iteration_ms": ms / iters, "iteration_px_per_s": batch * n * n * iters / (ms / 1e3)}
 
 
+def run_cufft(n, batch, iters, warm=3, beta=0.9):
+    """cuFFT reference (torch.fft): the transform pair, and a RAAR iteration from library calls."""
+    import torch
+
+    g = torch.Generator(device="cuda").manual_seed(n)
+    x = torch.randn((batch, n, n), dtype=torch.complex64, device="cuda", generator=g)
+    S = torch.rand((batch, n, n), device="cuda", generator=g) < 0.25
+    M = torch.rand((n, n), device="cuda", generator=g) + 0.1
+    meas = torch.rand((n, n), device="cuda", generator=g) >= 0.05
+
+    def pair(v):
+        return torch.fft.ifft2(torch.fft.fft2(v, norm="ortho"), norm="ortho")
+
+    def iteration(v):
+        X = torch.fft.fft2(v, norm="ortho")
+        a = X.abs()
+        Y = torch.where(meas & (a > 0), X * (M / torch.where(a > 0, a, torch.ones_like(a))), X)
+        m = torch.fft.ifft2(Y, norm="ortho")
+        return torch.where(S, m, beta * v + (1 - 2 * beta) * m)
+
+    out = {"n": n, "batch": batch, "iters": iters, "reference": "cuFFT via torch.fft"}
+    for name, fn in (("fft_pair", pair), ("library_iteration", iteration)):
+        y = x
+        for _ in range(warm):
+            y = fn(y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(iters):
+            y = fn(y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        out[name] = {"ms": ms, "px_per_s": batch * n * n / (ms / 1e3)}
+    return out
+
+
 def sweep(n, batch, iters, alg):
     """Time every (row, column) launch variant of side n; returns the list of results."""
     from paper_2409_07413_gb300 import spring
@@ -93,6 +135,7 @@ def main():
     ap.add_argument("--precision", type=int, default=0, help="0: FP32 storage, 1: FP16 storage")
     ap.add_argument("--sweep", action="store_true", help="time every launch variant")
     ap.add_argument("--fused", action="store_true", help="also time the on-chip kernel (N <= 256)")
+    ap.add_argument("--cufft", action="store_true", help="also time the cuFFT reference (torch.fft)")
     a = ap.parse_args()
     for n in a.n:
         b = a.batch if a.batch > 0 else max(1, (128 * 512 * 512) // (n * n))
@@ -105,6 +148,8 @@ def main():
             print(json.dumps(run(n, b, a.iters, a.alg, precision=a.precision)), flush=True)
         if a.fused and n <= 256:
             print(json.dumps(run_fused(n, b, a.iters, a.alg)), flush=True)
+        if a.cufft:
+            print(json.dumps(run_cufft(n, b, a.iters)), flush=True)
 
 
 if __name__ == "__main__":
