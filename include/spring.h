@@ -22,8 +22,9 @@
  *    missing pixel whose modulus is bounded above (Eq. pm_bounds) carries M = -2 - U
  *    (M <= -2, bound U >= 0); entries in (-2, 0) (the library writes -1) are free.
  *  - Supports and masks are uint8, 0 or 1.
- *  - Sizes: N in {64, 128, 192, 256, 512, 1024} (square patterns; N = 2^a or 3 * 2^a).
- *    Other sizes return SPRING_E_INVALID.
+ *  - Sizes: square patterns, N in {64, 96, 128, 192, 256, 384, 512, 768, 1024} (every even
+ *    N in [64, 1024] of the form 2^a 3^b with b <= 1).  Other sizes return
+ *    SPRING_E_INVALID.
  *  - Streams: the operator API takes a cudaStream_t as void* (NULL = legacy default
  *    stream) and is asynchronous on it; device pointers must be valid on the current
  *    device.  Scratch memory is taken from the stream-ordered allocator of the current
