@@ -14,6 +14,9 @@ G generations x 200 RAAR iterations.  Two ways to run the same set:
           spring_mpr_run_batch (one launch per iteration pass over K x 2P images; K such
           that a launch covers about --batch-pixels pixels).
 
+--graph 1 captures each plain and batched run as one CUDA graph (instantiated and
+launched inside the timed region).
+
 Reports reconstructions/s and iteration-pixels/s of each (makespan of the whole set) and
 the mean final error; all see identical requests and seeds, so the errors agree exactly
 (checked pattern by pattern).
@@ -52,6 +55,7 @@ def main():
     ap.add_argument("--modes", default="served,plain,batched")
     ap.add_argument("--batch-pixels", type=float, default=2.0 ** 26)
     ap.add_argument("--sides", default=",".join(map(str, SIDES)))
+    ap.add_argument("--graph", type=int, default=0, help="1: plain and batched runs captured as CUDA graphs")
     a = ap.parse_args()
     sides = tuple(int(v) for v in a.sides.split(","))
     import torch  # noqa: F401  (device selection through the library)
@@ -63,7 +67,7 @@ def main():
     for n in sides:  # tune each side once, outside the timed region
         spring.autotune(n, 2 * prm["pop"])
     work_px = sum(2 * prm["pop"] * prm["iters_per_gen"] * prm["generations"] * n * n for n, _, _ in jobs)
-    out = {"benchmark": "batched uneven", "patterns": len(jobs),
+    out = {"benchmark": "batched uneven", "patterns": len(jobs), "graph": a.graph,
            "sides": {str(n): int(sum(1 for j in jobs if j[0] == n)) for n in sides}, "params": prm,
            "iteration_pixels": work_px}
     per_mode = {}
@@ -78,7 +82,7 @@ def main():
                 K = max(1, int(a.batch_pixels // (2 * prm["pop"] * n * n)))
                 for c in range(0, len(idx), K):
                     part = idx[c:c + K]
-                    rs = ctx.run_batch([probs[i] for i in part], spring.params(**prm),
+                    rs = ctx.run_batch([probs[i] for i in part], spring.params(**prm, use_graph=a.graph),
                                        [jobs[i][2] for i in part], want_arrays=False)
                     for i, r in zip(part, rs):
                         errs[i] = r["final_error_best"]
@@ -89,7 +93,8 @@ def main():
                 errs[i] = r["final_error_best"]
         else:
             for i, (pr, (_, _, sd)) in enumerate(zip(probs, jobs)):
-                errs[i] = pr.run(spring.params(**prm, seed=sd), want_arrays=False)["final_error_best"]
+                errs[i] = pr.run(spring.params(**prm, seed=sd, use_graph=a.graph),
+                                 want_arrays=False)["final_error_best"]
         span = time.perf_counter() - t0
         for pr in probs:
             pr.destroy()
