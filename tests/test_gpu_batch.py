@@ -95,3 +95,18 @@ def test_batch_invalid_arguments(sp, ctx):
         ctx.run_batch([], sp.params(**BASE), [])
     for pr in a + b:
         pr.destroy()
+
+
+def test_batch_of_bounded_and_plain_problems(sp, ctx):
+    # the gathered modulus arrays carry each problem's own upper bounds (Eq. pm_bounds)
+    pats = [synthetic.config_pattern("ell128", s) for s in (20, 21, 22)]
+    probs = [ctx.problem(pats[0].intensities, pats[0].mask, pats[0].support0, saturated=pats[0].saturated,
+                         bounds=sp.bounds()),
+             ctx.problem(pats[1].intensities, pats[1].mask, pats[1].support0),
+             ctx.problem(pats[2].intensities, pats[2].mask, pats[2].support0, bounds=sp.bounds(eta=1.0))]
+    seeds = [7, 8, 9]
+    batch = ctx.run_batch(probs, sp.params(**BASE), seeds)
+    for q in range(3):
+        same(batch[q], probs[q].run(sp.params(**BASE, seed=seeds[q])))
+    for pr in probs:
+        pr.destroy()
