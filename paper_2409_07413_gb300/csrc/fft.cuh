@@ -174,14 +174,22 @@ struct NamedSync {
 
 // ------------------------------------------------------------------ plans
 // A plan: transform length N, elements per thread E (T = N / E threads per transform),
-// radices R0, R1, R2, R3 (R2 = 0: two stages; R3 = 0: at most three).  E is a multiple of
-// every radix.
-template <int N_, int E_, int R0_, int R1_, int R2_ = 0, int R3_ = 0>
+// radices R0 .. R4 (two to five stages; the unused trailing radices are 0).  E is a
+// multiple of every radix.
+template <int N_, int E_, int R0_, int R1_, int R2_ = 0, int R3_ = 0, int R4_ = 0>
 struct PlanT {
-  static constexpr int N = N_, E = E_, R0 = R0_, R1 = R1_, R2 = R2_, R3 = R3_, T = N_ / E_;
-  static_assert(R0_ * R1_ * (R2_ ? R2_ : 1) * (R3_ ? R3_ : 1) == N_, "radices must multiply to N");
-  static_assert(R3_ == 0 || R2_ != 0, "a fourth stage needs a third");
-  static_assert(E_ % R0_ == 0 && E_ % R1_ == 0 && (R2_ == 0 || E_ % R2_ == 0) && (R3_ == 0 || E_ % R3_ == 0),
+  static constexpr int N = N_, E = E_, R0 = R0_, R1 = R1_, R2 = R2_, R3 = R3_, R4 = R4_, T = N_ / E_;
+  // radix of stage s (0 past the last stage)
+  __host__ __device__ static constexpr int radix(int s) {
+    return s == 0 ? R0_ : s == 1 ? R1_ : s == 2 ? R2_ : s == 3 ? R3_ : s == 4 ? R4_ : 0;
+  }
+  // product of the radices of the stages before s
+  __host__ __device__ static constexpr int span(int s) { return s <= 0 ? 1 : span(s - 1) * radix(s - 1); }
+  static_assert(R0_ * R1_ * (R2_ ? R2_ : 1) * (R3_ ? R3_ : 1) * (R4_ ? R4_ : 1) == N_,
+                "radices must multiply to N");
+  static_assert((R3_ == 0 || R2_ != 0) && (R4_ == 0 || R3_ != 0), "no gaps between stages");
+  static_assert(E_ % R0_ == 0 && E_ % R1_ == 0 && (R2_ == 0 || E_ % R2_ == 0) && (R3_ == 0 || E_ % R3_ == 0) &&
+                    (R4_ == 0 || E_ % R4_ == 0),
                 "E vs radices");
 };
 // default plan for each supported N
@@ -200,10 +208,12 @@ template <> struct Plan<1024> : PlanT<1024, 32, 32, 32> {};
 // of a stage whose outputs go through shared memory (every stage but the last)
 template <class P>
 __host__ __device__ constexpr int pad_elems_p() {
-  int a = P::N + P::N / P::R0;
-  int b = P::R2 ? P::N + P::N / P::R1 : 0;
-  int c = P::R3 ? P::N + P::N / P::R2 : 0;
-  return a > b ? (a > c ? a : c) : (b > c ? b : c);
+  int m = 0;
+  for (int s = 0; P::radix(s + 1) != 0; ++s) {
+    const int e = P::N + P::N / P::radix(s);
+    m = e > m ? e : m;
+  }
+  return m;
 }
 template <int N>
 __host__ __device__ constexpr int pad_elems() { return pad_elems_p<Plan<N>>(); }
@@ -315,10 +325,38 @@ __device__ __forceinline__ void stage_tw(V (&b)[E], int t, const float2* __restr
 // (with STRIDE between consecutive elements).  tw: table of e^{-2 pi i k / N}.
 // TAIL = false leaves out the barrier after the last shared-memory read: for callers that
 // synchronise themselves before the buffer is written again, or never write it again.
+// stages S >= 1 of plan P: inputs from the layout of stage S - 1 (groups of span(S),
+// padding span(S - 1)), twiddles, radix-R DFT; then the next stage through shared memory,
+// or, after the last stage, the outputs into v
+template <class P, int DIR, bool PAD, int STRIDE, bool TAIL, int S, class Sync, class V>
+__device__ __forceinline__ void fft_stages(V (&v)[P::E], V (&b)[P::E], V* sm, int t, const float2* __restrict__ tw,
+                                           const Sync& sync) {
+  constexpr int N = P::N, E = P::E, R = P::radix(S), NS = P::span(S);
+  constexpr bool LAST = P::radix(S + 1) == 0;
+  stage_load<N, E, R, NS, P::span(S - 1), PAD, STRIDE>(b, sm, t);
+  if (TAIL || !LAST) sync();
+  stage_tw<N, E, R, NS, DIR>(b, t, tw);
+  stage_dft<N, E, R, DIR>(b);
+  if constexpr (LAST) {
+#pragma unroll
+    for (int u = 0; u < E / R; ++u)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u + r * (E / R)] = b[u * R + r];
+  } else {
+    stage_store<N, E, R, NS, PAD, STRIDE>(b, sm, t);
+    sync();
+    fft_stages<P, DIR, PAD, STRIDE, TAIL, S + 1>(v, b, sm, t, tw, sync);
+  }
+}
+
+// v: E registers of thread t (element t + m T).  sm: this transform's exchange buffer
+// (with STRIDE between consecutive elements).  tw: table of e^{-2 pi i k / N}.
+// TAIL = false leaves out the barrier after the last shared-memory read: for callers that
+// synchronise themselves before the buffer is written again, or never write it again.
 template <class P, int DIR, bool PAD, int STRIDE, bool TAIL = true, class Sync, class V>
 __device__ __forceinline__ void fft_plan(V (&v)[P::E], V* sm, int t, const float2* __restrict__ tw,
                                          const Sync& sync) {
-  constexpr int N = P::N, E = P::E, R0 = P::R0, R1 = P::R1, R2 = P::R2, R3 = P::R3;
+  constexpr int N = P::N, E = P::E, R0 = P::R0;
   V b[E];
   // stage 0 (NS = 1): inputs j + r N/R0 are the registers u + r E/R0
 #pragma unroll
@@ -328,42 +366,7 @@ __device__ __forceinline__ void fft_plan(V (&v)[P::E], V* sm, int t, const float
   stage_dft<N, E, R0, DIR>(b);
   stage_store<N, E, R0, 1, PAD, STRIDE>(b, sm, t);
   sync();
-  // stage 1 (NS = R0)
-  stage_load<N, E, R1, R0, 1, PAD, STRIDE>(b, sm, t);
-  if (TAIL || R2 != 0) sync();
-  stage_tw<N, E, R1, R0, DIR>(b, t, tw);
-  stage_dft<N, E, R1, DIR>(b);
-  if constexpr (R2 == 0) {
-#pragma unroll
-    for (int u = 0; u < E / R1; ++u)
-#pragma unroll
-      for (int r = 0; r < R1; ++r) v[u + r * (E / R1)] = b[u * R1 + r];
-  } else {
-    stage_store<N, E, R1, R0, PAD, STRIDE>(b, sm, t);
-    sync();
-    stage_load<N, E, R2, R0 * R1, R0, PAD, STRIDE>(b, sm, t);
-    if (TAIL || R3 != 0) sync();
-    stage_tw<N, E, R2, R0 * R1, DIR>(b, t, tw);
-    stage_dft<N, E, R2, DIR>(b);
-    if constexpr (R3 == 0) {
-#pragma unroll
-      for (int u = 0; u < E / R2; ++u)
-#pragma unroll
-        for (int r = 0; r < R2; ++r) v[u + r * (E / R2)] = b[u * R2 + r];
-    } else {
-      // stage 3 (NS = R0 R1 R2)
-      stage_store<N, E, R2, R0 * R1, PAD, STRIDE>(b, sm, t);
-      sync();
-      stage_load<N, E, R3, R0 * R1 * R2, R0 * R1, PAD, STRIDE>(b, sm, t);
-      if (TAIL) sync();
-      stage_tw<N, E, R3, R0 * R1 * R2, DIR>(b, t, tw);
-      stage_dft<N, E, R3, DIR>(b);
-#pragma unroll
-      for (int u = 0; u < E / R3; ++u)
-#pragma unroll
-        for (int r = 0; r < R3; ++r) v[u + r * (E / R3)] = b[u * R3 + r];
-    }
-  }
+  fft_stages<P, DIR, PAD, STRIDE, TAIL, 1>(v, b, sm, t, tw, sync);
 }
 
 // the default plan of side N

@@ -77,9 +77,9 @@ template <> struct Col2Plan<96>   : PlanT<96, 12, 4, 4, 2, 3> {};
 template <> struct Col2Plan<128>  : PlanT<128, 8, 8, 4, 4> {};
 template <> struct Col2Plan<192>  : PlanT<192, 12, 4, 4, 4, 3> {};
 template <> struct Col2Plan<256>  : PlanT<256, 8, 8, 8, 4> {};
-template <> struct Col2Plan<384>  : Plan<384> {};
+template <> struct Col2Plan<384>  : PlanT<384, 12, 4, 4, 4, 2, 3> {};
 template <> struct Col2Plan<512>  : PlanT<512, 8, 8, 8, 8> {};
-template <> struct Col2Plan<768>  : Plan<768> {};
+template <> struct Col2Plan<768>  : PlanT<768, 12, 4, 4, 4, 4, 3> {};
 template <> struct Col2Plan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
 // alternative row-pass plans (fewer elements per thread; T = 64 rows sync by named barrier)
@@ -90,6 +90,8 @@ template <> struct RowAltPlan<256> : PlanT<256, 32, 32, 8> {};
 template <> struct RowAltPlan<128> : PlanT<128, 16, 16, 8> {};
 template <> struct RowAltPlan<96> : PlanT<96, 12, 4, 4, 2, 3> {};
 template <> struct RowAltPlan<192> : PlanT<192, 12, 4, 4, 4, 3> {};
+template <> struct RowAltPlan<384> : PlanT<384, 12, 4, 4, 4, 2, 3> {};
+template <> struct RowAltPlan<768> : PlanT<768, 12, 4, 4, 4, 4, 3> {};
 
 // FP16 storage of the iteration buffers (precision 1): x as half2 scaled by the problem's
 // power of two s16 (chosen from ||M||_2 so that every stored value stays well inside the

@@ -368,9 +368,9 @@ def test_kernel_variants_parity(sp, n):
         sp.set_kernel_variant(n, *saved)
     # same plans give the same bits: row variants 0-4 share the default plan, 5-6 the
     # alternative row plan; column variants 0 and 2-7 the default column plan; the paired
-    # variants 8-9 share their own plan, which has the default's radices at 64, 384, 512
-    # and 768 and the alternative's at 1024
-    paired_like = {64: 0, 384: 0, 512: 0, 768: 0, 1024: 1}.get(n, 8)
+    # variants 8-9 share their own plan, which has the default's radices at 64 and 512 and
+    # the alternative's at 1024
+    paired_like = {64: 0, 512: 0, 1024: 1}.get(n, 8)
     for rv in range(7):
         r0 = 0 if rv < 5 else 5
         for cv in (0, 2, 3, 4, 5, 6, 7):
