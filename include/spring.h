@@ -443,6 +443,9 @@ typedef struct {
 #define SPRING_KC_FUSED 3     /* on-chip whole iterations (spring_iterate_fused, N <= 256) */
 #define SPRING_KC_COUNT 4
 void spring_stats_reset(void);
+/* on = 0: no timing; on = k >= 1: every k-th launch of each timed class (ROW_ITER,
+ * COL_PM, FUSED) is bracketed by two events (k = 1: every launch).  A stride that is
+ * coprime to the run's block lengths samples every position of a block evenly. */
 void spring_stats_enable_timing(int on);
 void spring_stats_get(int kernel_class, spring_kernel_stat* out);
 /* Total kernel launches of the library since the last reset. */

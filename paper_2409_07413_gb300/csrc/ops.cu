@@ -70,9 +70,10 @@ static bool capturing(cudaStream_t s) {
 
 void launch_begin(int kc, cudaStream_t s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  g_kstat[kc].launches.fetch_add(1, std::memory_order_relaxed);
+  const uint64_t idx = g_kstat[kc].launches.fetch_add(1, std::memory_order_relaxed);
   t_begin_event = nullptr;
-  if (g_timing.load(std::memory_order_relaxed) && kc != SPRING_KC_OTHER && !capturing(s)) {
+  const int stride = g_timing.load(std::memory_order_relaxed);
+  if (stride > 0 && idx % (uint64_t)stride == 0 && kc != SPRING_KC_OTHER && !capturing(s)) {
     std::lock_guard<std::mutex> lk(g_tmu);
     t_begin_event = take_event();
     cudaEventRecord(t_begin_event, s);
@@ -280,7 +281,7 @@ void spring_stats_reset(void) {
   g_launches = 0;
 }
 
-void spring_stats_enable_timing(int on) { g_timing = on ? 1 : 0; }
+void spring_stats_enable_timing(int on) { g_timing = on > 0 ? on : 0; }
 
 void spring_stats_get(int kc, spring_kernel_stat* out) {
   if (!out) return;

@@ -468,8 +468,10 @@ def stats_reset():
     lib().spring_stats_reset()
 
 
-def stats_enable_timing(on: bool):
-    lib().spring_stats_enable_timing(int(on))
+def stats_enable_timing(on, stride: int = 1):
+    """Per-launch CUDA-event timing of the iteration passes: off, or every `stride`-th
+    launch of each timed kernel class."""
+    lib().spring_stats_enable_timing(int(stride) if on else 0)
 
 
 def stats_get(kc: int) -> KernelStat:
