@@ -46,7 +46,7 @@ static int side_index(int n) { return side_slot(n); }
 static std::mutex g_var_mu;
 // (sides 64, 96, 128, 192, 256, 384, 512, 768, 1024)
 static int g_row_var[N_SIDES] = {0, 6, 5, 6, 0, 6, 6, 6, 5};
-static int g_col_var[N_SIDES] = {0, 1, 2, 1, 0, 0, 0, 3, 3};
+static int g_col_var[N_SIDES] = {0, 1, 2, 1, 0, 0, 0, 1, 1};
 static bool g_tuned[N_SIDES] = {};
 // iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
 // (N <= 256, k_cluster.cu); chosen by the autotuner, the two-pass path until then

@@ -24,7 +24,8 @@
 //           5 / 6 = alternative radix plan (results differ by rounding), loads after the
 //           inverse transform, register budget for 2 / 4 blocks per SM
 //   column: 0 = default plan, 16-column tiles; 1 = alternative plan (other radices:
-//           results differ by rounding); 2 = 32-column tiles; 3 = 8-column tiles;
+//           results differ by rounding), 16-column tiles, 8 where two such blocks would
+//           not fit an SM; 2 = 32-column tiles; 3 = 8-column tiles;
 //           4 / 5 = persistent blocks fed by TMA: while a block transforms one tile, the
 //           next tile is already being copied into a second shared buffer (16 / 8 columns);
 //           6 / 7 = transposed tiles, one lane group per column (16 / 32 columns; 8 at
@@ -65,9 +66,11 @@ template <> struct AltPlan<512>  : PlanT<512, 8, 8, 8, 8> {};
 template <> struct AltPlan<768>  : PlanT<768, 24, 3, 8, 8, 4> {};
 template <> struct AltPlan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
-// row plan of the FP16-storage iteration pass
+// row and column plans of the FP16-storage iteration passes
 template <int N> struct Row16Plan : Plan<N> {};
 template <> struct Row16Plan<1024> : PlanT<1024, 16, 16, 8, 8> {};
+template <int N> struct Col16Plan : Plan<N> {};
+template <> struct Col16Plan<1024> : PlanT<1024, 16, 16, 8, 8> {};
 
 // plans of the paired column pass (two columns per thread; the fewest elements per
 // thread that the radices allow)
@@ -633,6 +636,11 @@ constexpr int fit_w() {  // keep the column tile and its modulus strip within sh
 }
 
 template <int N>
+constexpr int fit_w_pair() {  // 16-column tiles while two blocks (tile + modulus strip) fit an SM
+  return (size_t)N * 16 * 12 > 100 * 1024 ? 8 : 16;
+}
+
+template <int N>
 constexpr int tma_w() {  // the TMA pass holds two tiles and two modulus strips
   return (size_t)2 * N * 16 * 12 + 1024 > 220 * 1024 ? 8 : 16;
 }
@@ -711,7 +719,7 @@ template <int N, int MODE>
 inline spring_status col_variant(const FftOp& op, cudaStream_t s, bool prep) {
   switch (op.variant) {
     case 0: return col_launch<Plan<N>, 16, MODE>(op, s, prep);
-    case 1: return col_launch<AltPlan<N>, 16, MODE>(op, s, prep);
+    case 1: return col_launch<AltPlan<N>, fit_w_pair<N>(), MODE>(op, s, prep);
     case 2: return col_launch<Plan<N>, fit_w<N, 32>(), MODE>(op, s, prep);
     case 3: return col_launch<Plan<N>, 8, MODE>(op, s, prep);
     case 4:
@@ -754,7 +762,7 @@ spring_status run_fft_op(const FftOp& op, cudaStream_t s, bool prep) {
       if (op.alg == 0) return row_launch<Row16Plan<N>, ROW_ITER, 0, true, 2, false, __half2>(op, s, prep);
       if (op.alg == 1) return row_launch<Row16Plan<N>, ROW_ITER, 1, true, 2, false, __half2>(op, s, prep);
       return row_launch<Row16Plan<N>, ROW_ITER, 2, true, 2, false, __half2>(op, s, prep);
-    case OP_COL_PM16: return col_launch<Plan<N>, (N >= 1024 ? 8 : 16), COL_PM, __half2>(op, s, prep);
+    case OP_COL_PM16: return col_launch<Col16Plan<N>, (N >= 1024 ? 8 : 16), COL_PM, __half2>(op, s, prep);
     case OP_ROW_INIT16: return row_launch<Plan<N>, ROW_INIT16, 0, false, 1>(op, s, prep);
   }
   return invalid("unknown transform operation");
