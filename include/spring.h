@@ -42,7 +42,9 @@
 extern "C" {
 #endif
 
-#define SPRING_ABI_VERSION 1
+#define SPRING_ABI_VERSION 2
+/* columns of spring_result.gen_stats */
+#define SPRING_GEN_STATS_COLS 9
 
 typedef enum {
   SPRING_OK = 0,
@@ -107,10 +109,11 @@ typedef struct {
   float* rho_avg;          /* N*N complex64: average of the aligned population (Alg. mpr) */
   float* rho_best;         /* N*N complex64: lowest-error individual */
   uint8_t* support_avg;    /* N*N: union of the aligned supports (Eq. avgrec) */
-  double* gen_stats;       /* G x 8 per generation: best E, mean E, worst E, E(avg) (last
-                              generation only, else NaN), O_d (Eq. oversampling),
-                              replacement factor, mean complexity Gamma (Eq. complexity),
-                              mean |sum rho|; may be NULL */
+  double* gen_stats;       /* G x SPRING_GEN_STATS_COLS (9) per generation: best E, mean E,
+                              worst E, E(avg) (last generation only, else NaN), O_d (Eq.
+                              oversampling), replacement factor, mean complexity Gamma (Eq.
+                              complexity), mean |sum rho|, and the population standard
+                              deviation of |sum rho| relative to that mean; may be NULL */
   double final_error_avg;  /* GetError (Eq. error_calc) of rho_avg on support_avg */
   double final_error_best; /* error of rho_best */
   double t_submit_s, t_admit_s, t_done_s; /* serving timestamps (monotonic seconds) */

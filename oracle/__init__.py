@@ -435,7 +435,7 @@ def mpr_run(I_centred, mask_centred, S0, keep_population=False, saturated=None, 
     avg = np.empty((n, n), np.complex128)
     best = np.empty((n, n), np.complex128)
     Sa = np.empty((n, n), np.uint8)
-    stats = np.empty((G, 8), np.float64)
+    stats = np.empty((G, 9), np.float64)
     res = OrcResult()
     res.rho_avg, res.rho_best, res.support_avg, res.gen_stats = _pd(avg), _pd(best), _pu8(Sa), _pd(stats)
     if keep_population:

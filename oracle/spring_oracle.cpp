@@ -998,7 +998,7 @@ struct orc_result {
   double* pop_x;        // P*n*n interleaved complex final population, may be null
   uint8_t* pop_S;       // P*n*n final supports, may be null
   double* pop_err;      // P final errors, may be null
-  double* gen_stats;    // G x 8, may be null
+  double* gen_stats;    // G x 9, may be null
   double final_error_avg, final_error_best;
 };
 
@@ -1154,15 +1154,15 @@ extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const u
   // per-generation monitors (Sec. "Monitoring the reconstruction process")
   auto monitors = [&](int g, int repl) {
     if (!res->gen_stats) return;
-    double* st = res->gen_stats + (size_t)(g - 1) * 8;
+    double* st = res->gen_stats + (size_t)(g - 1) * 9;
     int b = argmin_first(pe);
     double mn = 0.0, mx = pe[0], gam = 0.0, sm = 0.0;
+    std::vector<double> sums(P);
     for (int p = 0; p < P; p++) {
       mn += pe[p];
       mx = std::max(mx, pe[p]);
-      double s1;
-      gam += complexity(&px[p * nn], n, &s1);
-      sm += s1;
+      gam += complexity(&px[p * nn], n, &sums[p]);
+      sm += sums[p];
     }
     st[0] = pe[b];
     st[1] = mn / P;
@@ -1178,6 +1178,11 @@ extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const u
     st[5] = (double)repl / P;
     st[6] = gam / P;
     st[7] = sm / P;
+    // spread of the density sums (Sec. "Crossover averaging"): population standard
+    // deviation relative to the mean, by the two-pass formula
+    double var = 0.0;
+    for (int p = 0; p < P; p++) var += (sums[p] - sm / P) * (sums[p] - sm / P);
+    st[8] = sm > 0.0 ? std::sqrt(var / P) / (sm / P) : 0.0;
   };
 
   for (int g = 1; g <= G && pr.mode == 1; g++) {
@@ -1245,7 +1250,7 @@ extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const u
   average(px.data(), pS.data(), mask.data(), P, n, b, avg.data(), Savg.data());
   res->final_error_avg = fourier_error(avg.data(), Savg.data(), M.data(), mask.data(), n);
   res->final_error_best = pe[b];
-  if (res->gen_stats) res->gen_stats[(size_t)(G - 1) * 8 + 3] = res->final_error_avg;
+  if (res->gen_stats) res->gen_stats[(size_t)(G - 1) * 9 + 3] = res->final_error_avg;
   if (res->rho_avg) std::copy(avg.begin(), avg.end(), as_cd(res->rho_avg));
   if (res->rho_best) std::copy(px.begin() + b * nn, px.begin() + (b + 1) * nn, as_cd(res->rho_best));
   if (res->support_avg) std::copy(Savg.begin(), Savg.end(), res->support_avg);

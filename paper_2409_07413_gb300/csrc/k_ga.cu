@@ -847,6 +847,15 @@ __global__ void k_gen_stats(const double* __restrict__ err, const uint8_t* __res
     row[5] = (double)rep / P;
     row[6] = gam / P;
     row[7] = sm / P;
+    // spread of the density sums over the population: population standard deviation
+    // relative to their mean (Sec. "Crossover averaging" tracks it in % of the mean)
+    const double mean_s = sm / P;
+    double var = 0.0;
+    for (int p = 0; p < P; ++p) {
+      const double d = dens[2 * p] - mean_s;
+      var += d * d;
+    }
+    row[8] = mean_s > 0.0 ? sqrt(var / P) / mean_s : 0.0;
   }
 }
 

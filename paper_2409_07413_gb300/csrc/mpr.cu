@@ -113,7 +113,7 @@ static Layout make_layout(int n, const spring_params& p, int K = 1) {
   L.part_norm = take(normalise_scratch_bytes((int)P));
   L.part_dens = take(density_scratch_bytes((int)P));
   L.imgmax = take(sizeof(unsigned) * B);
-  L.stats = take(sizeof(double) * 8 * G * K);
+  L.stats = take(sizeof(double) * SPRING_GEN_STATS_COLS * G * K);
   L.avg = take(sizeof(float2) * nn * K);
   L.Savg = take(nn * K);
   L.err_avg = take(sizeof(double) * 2 * K);
@@ -273,7 +273,7 @@ class Run {
   double* err_new() { return err_pop() + P; }
   int32_t* bestq() { return best + 4 * cq; }
   int64_t* alphaq() { return alpha + 4 * cq; }
-  double* statsq() { return stats + (size_t)8 * G * cq; }
+  double* statsq() { return stats + (size_t)SPRING_GEN_STATS_COLS * G * cq; }
   float2* avgq() { return avg + (size_t)cq * nn(); }
   uint8_t* Savgq() { return Savg + (size_t)cq * nn(); }
   double* err_avgq() { return err_avg + 2 * cq; }
@@ -471,7 +471,7 @@ class Run {
       SPRING_TRY(improve_independent(g, sigma, tau));
       SPRING_CUDA(cudaMemsetAsync(repl, 0, P, s));
       SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
-      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + 8 * (g - 1), s));
+      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + SPRING_GEN_STATS_COLS * (g - 1), s));
       return monitor(g);
     }
     // the GA steps pattern by pattern, the improvement of all K patterns' populations at once
@@ -488,7 +488,7 @@ class Run {
     for (cq = 0; cq < K; ++cq) {
       SPRING_TRY(launch_select(n, x_pop(), S_pop(), err_pop(), x_new(), S_new(), err_new(), P, repl, s));
       SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
-      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + 8 * (g - 1), s));
+      SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + SPRING_GEN_STATS_COLS * (g - 1), s));
       SPRING_TRY(monitor(g));
     }
     cq = 0;
@@ -499,7 +499,8 @@ class Run {
   spring_status monitor(int g) {
     if (!prm.monitor_avg || g == G) return SPRING_OK;  // generation G: finish() computes it
     SPRING_TRY(average_and_error());
-    SPRING_CUDA(cudaMemcpyAsync(statsq() + 8 * (g - 1) + 3, err_avgq(), sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SPRING_CUDA(cudaMemcpyAsync(statsq() + SPRING_GEN_STATS_COLS * (g - 1) + 3, err_avgq(), sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
     return SPRING_OK;
   }
 
@@ -593,10 +594,12 @@ class Run {
         SPRING_CUDA(cudaMemcpy(out->rho_best, x_pop() + (size_t)b * nn(), sizeof(float2) * nn(), cudaMemcpyDeviceToHost));
       if (out->support_avg) SPRING_CUDA(cudaMemcpy(out->support_avg, Savgq(), nn(), cudaMemcpyDeviceToHost));
       if (out->gen_stats) {
-        SPRING_CUDA(cudaMemcpy(out->gen_stats, statsq(), sizeof(double) * 8 * G, cudaMemcpyDeviceToHost));
-        out->gen_stats[8 * (G - 1) + 3] = ea;
+        SPRING_CUDA(cudaMemcpy(out->gen_stats, statsq(), sizeof(double) * SPRING_GEN_STATS_COLS * G,
+                               cudaMemcpyDeviceToHost));
+        out->gen_stats[SPRING_GEN_STATS_COLS * (G - 1) + 3] = ea;
         for (int g = 1; g < first_gen; ++g)  // generations run before a resume
-          for (int k = 0; k < 8; ++k) out->gen_stats[8 * (g - 1) + k] = std::numeric_limits<double>::quiet_NaN();
+          for (int k = 0; k < SPRING_GEN_STATS_COLS; ++k)
+            out->gen_stats[SPRING_GEN_STATS_COLS * (g - 1) + k] = std::numeric_limits<double>::quiet_NaN();
       }
     }
     cq = 0;
@@ -765,7 +768,7 @@ static void scheduler(spring_ctx* c) {
         t->rho_avg.resize(2 * nn);
         t->rho_best.resize(2 * nn);
         t->support_avg.resize(nn);
-        t->gen_stats.resize(8 * (size_t)G);
+        t->gen_stats.resize(SPRING_GEN_STATS_COLS * (size_t)G);
         spring_result r{};
         r.rho_avg = t->rho_avg.data();
         r.rho_best = t->rho_best.data();

@@ -7,9 +7,11 @@ r = 24 px, 1e8 photons with Poisson noise, 200 px object) reconstructed with P =
                iteration blocks, FP32 math
 
 Both runs keep the Fourier-error fitness and the shrink-wrap threshold statistics in FP64
-on the GPU.  The same pattern, schedule and run seed at P = 32 and 2 generations are also run in both
-precisions and set beside the FP64 oracle's result for that configuration (stored by
-tests/golden/make_oracle_errors.py; the full 20 generations take the oracle hours).  Per result it reports time, reconstructions/s, iteration-pixels/s, the final
+on the GPU.  The same pattern and schedule at P = 32 and 2 generations are also run in both
+precisions at every run seed for which the FP64 oracle's result is stored
+(tests/golden/make_oracle_errors.py; the full 20 generations take the oracle hours) and
+compared seed by seed and in the mean; the GPU's spread over 16 further run seeds shows
+how far single trajectories scatter.  Per result it reports time, reconstructions/s, iteration-pixels/s, the final
 Fourier error (Eq. error_calc) of the average and best individual, and the error of the
 aligned average against the synthetic object (aligned by spring_reshift: translation,
 twin and global phase; then the best real scale, since intensities in photon counts fix the
@@ -79,17 +81,28 @@ def main():
             "final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
             "truth_error_of_average": truth_error(spring, r["rho_avg"], pat.truth),
         }
-    # the reduced configuration the oracle has run (2 generations, run seed 1000)
-    golden = {}
-    if GOLDEN.exists():
-        golden = json.loads(GOLDEN.read_text()).get("ell1024_g2", {})
+    # the reduced configuration the oracle has run (2 generations), at its run seeds
+    golden = json.loads(GOLDEN.read_text()) if GOLDEN.exists() else {}
+    orc = {g["run_seed"]: g for k, g in golden.items() if k == "ell1024_g2" or k.startswith("ell1024_g2_r")}
     red = dict(prm, pop=32, generations=2)
-    cmp = {"config": red, "oracle_fp64": {k: golden[k] for k in ("final_error_avg", "final_error_best")
-                                          if k in golden} or None}
+    keys = ("final_error_avg", "final_error_best")
+    cmp = {"config": red, "run_seeds": sorted(orc),
+           "oracle_fp64": {str(sd): {k: orc[sd][k] for k in keys} for sd in sorted(orc)}}
+    if orc:
+        cmp["oracle_fp64"]["mean"] = {k: float(np.mean([orc[sd][k] for sd in orc])) for k in keys}
     for prec in [int(v) for v in a.precisions.split(",")]:
-        r = prob.run(spring.params(**red, seed=1000, precision=prec))
-        cmp[str(prec)] = {"final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
-                          "truth_error_of_average": truth_error(spring, r["rho_avg"], pat.truth)}
+        per = {}
+        for sd in sorted(orc):
+            r = prob.run(spring.params(**red, seed=sd, precision=prec))
+            per[str(sd)] = {"final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
+                            "truth_error_of_average": truth_error(spring, r["rho_avg"], pat.truth)}
+        if orc:
+            per["mean"] = {k: float(np.mean([per[str(sd)][k] for sd in orc])) for k in keys}
+        spread = [prob.run(spring.params(**red, seed=2000 + i, precision=prec), want_arrays=False)
+                  for i in range(16)]
+        per["spread_16_seeds"] = {k: {"mean": float(np.mean([r[k] for r in spread])),
+                                      "std": float(np.std([r[k] for r in spread], ddof=1))} for k in keys}
+        cmp[str(prec)] = per
     out["versus_oracle"] = cmp
     prob.destroy()
     ctx.close()

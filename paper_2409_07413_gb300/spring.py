@@ -14,6 +14,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libspring.so"
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_BUSY, E_TIMEOUT, E_NOT_FOUND, E_NUMERIC, E_CANCELLED = range(9)
 KC_ROW_ITER, KC_COL_PM, KC_OTHER, KC_FUSED = 0, 1, 2, 3
+ABI_VERSION = 2  # SPRING_ABI_VERSION of the header this binding follows
 
 
 class SpringError(RuntimeError):
@@ -136,6 +137,9 @@ def lib():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
+        if L.spring_abi_version() != ABI_VERSION:
+            raise RuntimeError(f"{_LIB_PATH} has ABI version {L.spring_abi_version()}, this binding "
+                               f"expects {ABI_VERSION}: rebuild the library")
         _lib = L
     return _lib
 
@@ -183,6 +187,9 @@ def _batch_n(x):
 
 
 # ------------------------------------------------------------------ parameters
+GEN_STATS_COLS = 9  # columns of a result's gen_stats (SPRING_GEN_STATS_COLS)
+
+
 def params(**kw) -> Params:
     p = Params()
     lib().spring_params_default(C.byref(p))
@@ -630,7 +637,7 @@ def _result_buffers(n, generations):
         r.rho_best = keep["rho_best"].ctypes.data
         r.support_avg = keep["support_avg"].ctypes.data
     if generations:
-        keep["gen_stats"] = np.zeros((generations, 8), np.float64)
+        keep["gen_stats"] = np.zeros((generations, GEN_STATS_COLS), np.float64)
         r.gen_stats = keep["gen_stats"].ctypes.data
     return r, keep
 

@@ -3,8 +3,8 @@ the benchmark workloads (synthetic patterns from paper_2409_07413_gb300.syntheti
 
 Calls only the oracle.  Run from the repository root:
     python tests/golden/make_oracle_errors.py [--threads T]
-The 512 x 512 run (P = 64, 10 x 200 iterations) takes ~20 min on 8 cores, the reduced
-1024 x 1024 run ~10 min.
+The 512 x 512 run (P = 64, 10 x 200 iterations) takes ~20 min on 8 cores, each reduced
+1024 x 1024 run ~12 min.
 """
 import argparse
 import json
@@ -18,6 +18,8 @@ sys.path.insert(0, str(ROOT))
 import oracle  # noqa: E402
 from paper_2409_07413_gb300 import synthetic  # noqa: E402
 
+RUN_SEED = 1000
+
 WORKLOADS = {
     "ell512": ("ell512", 0, dict(pop=64, iters_per_gen=200, generations=10, algorithm=2, beta=0.9,
                                  sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
@@ -28,6 +30,10 @@ WORKLOADS = {
     "ell1024_g2": ("ell1024", 0, dict(pop=32, iters_per_gen=300, generations=2, algorithm=2, beta=0.9,
                                       sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
 }
+# the reduced 1024 x 1024 run at further run seeds (a single trajectory of HIO/RAAR and
+# the GA varies by several percent with the rounding, so the comparison is over seeds)
+for _s in (1001, 1002, 1003):
+    WORKLOADS[f"ell1024_g2_r{_s}"] = WORKLOADS["ell1024_g2"] + (_s,)
 
 
 def main():
@@ -39,14 +45,15 @@ def main():
         oracle.set_threads(a.threads)
     out_path = Path(__file__).resolve().parent / "oracle_errors.json"
     out = json.loads(out_path.read_text()) if out_path.exists() else {}
-    for name, (recipe, pseed, prm) in WORKLOADS.items():
-        if a.only and name != a.only:
+    for name, (recipe, pseed, prm, *rs) in WORKLOADS.items():
+        if a.only and not name.startswith(a.only):
             continue
+        run_seed = rs[0] if rs else RUN_SEED
         pat = synthetic.config_pattern(recipe, pseed)
         t0 = time.time()
-        r = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=1000, **prm)
+        r = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=run_seed, **prm)
         out[name] = {"final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
-                     "run_seed": 1000, "pattern_seed": pseed, "seconds": time.time() - t0,
+                     "run_seed": run_seed, "pattern_seed": pseed, "seconds": time.time() - t0,
                      "threads": oracle.get_threads(), "gen_best": r["gen_stats"][:, 0].tolist()}
         out_path.write_text(json.dumps(out, indent=1))
         print(name, out[name]["final_error_best"], out[name]["final_error_avg"], flush=True)

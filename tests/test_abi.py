@@ -47,7 +47,7 @@ def test_binding_covers_header(libpath):
 def test_loads_without_gpu_and_static_calls(libpath):
     from paper_2409_07413_gb300 import spring
     L = spring.lib()
-    assert L.spring_abi_version() == 1
+    assert L.spring_abi_version() == 2
     assert L.spring_status_string(0) == b"ok"
     assert L.spring_status_string(1) == b"invalid argument"
     p = spring.params(pop=64, iters_per_gen=200, generations=10)

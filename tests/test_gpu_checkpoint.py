@@ -73,3 +73,22 @@ def test_monitor_average_every_generation(sp, ctx):
     assert np.isfinite(b["gen_stats"][:, 3]).all()
     assert np.isnan(a["gen_stats"][:-1, 3]).all()
     assert b["gen_stats"][-1, 3] == b["final_error_avg"]
+
+
+@pytest.mark.parametrize("name", ["sphere64", "ell256"])
+def test_density_sum_monitors_match_the_population(sp, ctx, name):
+    # gen_stats columns 7 and 8 of generation g (Sec. "Crossover averaging": the mean of
+    # |sum rho| over the population and its population standard deviation relative to the
+    # mean) against numpy on the population saved after generation g of the same run
+    pat = synthetic.config_pattern(name, 1)
+    prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
+    p = sp.params(**C1)
+    whole = prob.run(p)
+    assert whole["gen_stats"].shape == (C1["generations"], 9)
+    for g in (2, C1["generations"]):
+        state = prob.run_until(p, g)
+        sums = np.abs(state["pop_x"].astype(np.complex128).reshape(C1["pop"], -1).sum(axis=1))
+        row = whole["gen_stats"][g - 1]
+        assert abs(row[7] - sums.mean()) <= 1e-5 * sums.mean(), g
+        assert abs(row[8] - sums.std() / sums.mean()) <= 1e-4 * row[8] + 1e-7, g
+    prob.destroy()

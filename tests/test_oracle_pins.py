@@ -503,7 +503,13 @@ def test_mpr_run_sphere64(orc):
     kw = dict(pop=8, iters_per_gen=100, generations=5, seed=0)
     r = orc.mpr_run(pat.intensities, pat.mask, pat.support0, keep_population=True, **kw)
     st = r["gen_stats"]
-    assert st.shape == (5, 8) and np.isfinite(st[:, [0, 1, 2, 4, 5, 6, 7]]).all()
+    assert st.shape == (5, 9) and np.isfinite(st[:, [0, 1, 2, 4, 5, 6, 7, 8]]).all()
+    # the density-sum monitors of the last generation are those of the returned population
+    # (Sec. "Crossover averaging": the mean of |sum rho| and its spread relative to the mean)
+    sums = np.abs(r["pop_x"].reshape(len(r["pop_x"]), -1).sum(axis=1))
+    assert abs(st[-1, 7] - sums.mean()) <= 1e-12 * sums.mean()
+    assert abs(st[-1, 8] - sums.std() / sums.mean()) <= 1e-9 * max(st[-1, 8], 1e-12)
+    assert st[-1, 8] > 0
     assert (st[:, 0] <= st[:, 1] + 1e-15).all() and (st[:, 1] <= st[:, 2] + 1e-15).all()
     assert ((st[:, 5] >= 0) & (st[:, 5] <= 1)).all()
     assert ((st[:, 6] >= 0) & (st[:, 6] <= 1)).all()
