@@ -30,10 +30,12 @@ WORKLOADS = {
     "ell1024_g2": ("ell1024", 0, dict(pop=32, iters_per_gen=300, generations=2, algorithm=2, beta=0.9,
                                       sw_sigma=1.5, sw_threshold=0.2, sw_period=20, er_tail=10)),
 }
-# the reduced 1024 x 1024 run at further run seeds (a single trajectory of HIO/RAAR and
-# the GA varies by several percent with the rounding, so the comparison is over seeds)
+# the reduced 1024 x 1024 run and the 512 x 512 run at further run seeds (a single
+# trajectory of HIO/RAAR and the GA varies by several percent with the rounding, so the
+# comparison is over seeds)
 for _s in (1001, 1002, 1003):
     WORKLOADS[f"ell1024_g2_r{_s}"] = WORKLOADS["ell1024_g2"] + (_s,)
+    WORKLOADS[f"ell512_r{_s}"] = WORKLOADS["ell512"] + (_s,)
 
 
 def main():
