@@ -94,6 +94,23 @@ def test_mpr_ell96_matches_oracle_statistically(sp, ctx):
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
 
 
+def test_replacement_and_average_error_behave_as_described(sp, ctx):
+    # Sec. "Monitoring the reconstruction process" (qualitative), the GPU's runs: about half
+    # of the new individuals replace their parents in the first generations, and the error
+    # of the average reconstruction falls over the run (the oracle shows the same)
+    rep, eavg = [], []
+    for seed in range(8):
+        pat = synthetic.config_pattern("sphere64", seed)
+        prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
+        st = prob.run(sp.params(**C1, seed=seed, monitor_avg=1), want_arrays=False)["gen_stats"]
+        prob.destroy()
+        rep.append(st[:, 5])
+        eavg.append(st[:, 3])
+    rep, eavg = np.array(rep), np.array(eavg)
+    assert 0.25 <= rep[:, :2].mean() <= 0.75
+    assert eavg[:, -1].mean() < eavg[:, 0].mean()
+
+
 def test_mpr_deterministic_and_graph_identical(sp, ctx):
     pat = synthetic.config_pattern("sphere64", 3)
     prob = ctx.problem(pat.intensities, pat.mask, pat.support0)

@@ -156,3 +156,20 @@ def test_monitor_average_every_generation(orc):
     assert np.isnan(a["gen_stats"][:-1, 3]).all()
     assert b["gen_stats"][-1, 3] == b["final_error_avg"]
     assert (b["gen_stats"][:, 3] >= 0).all() and (b["gen_stats"][:, 3] <= 2).all()
+
+
+def test_replacement_and_average_error_behave_as_described(orc):
+    # Sec. "Monitoring the reconstruction process" (qualitative): in the first generations
+    # about half of the new individuals replace their parents, and the error of the
+    # average reconstruction falls over the run (8 seeds of the 64 x 64 workload)
+    kw = dict(pop=8, iters_per_gen=100, generations=5, algorithm=2, beta=0.9, sw_sigma=1.5,
+              sw_threshold=0.2, sw_period=20, er_tail=10, monitor_avg=1)
+    rep, eavg = [], []
+    for seed in range(8):
+        pat = synthetic.config_pattern("sphere64", seed)
+        st = orc.mpr_run(pat.intensities, pat.mask, pat.support0, seed=seed, **kw)["gen_stats"]
+        rep.append(st[:, 5])
+        eavg.append(st[:, 3])
+    rep, eavg = np.array(rep), np.array(eavg)
+    assert 0.25 <= rep[:, :2].mean() <= 0.75
+    assert eavg[:, -1].mean() < eavg[:, 0].mean()
