@@ -16,6 +16,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <nvtx3/nvToolsExt.h>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -125,6 +126,15 @@ static Layout make_layout(int n, const spring_params& p, int K = 1) {
   L.total = o;
   return L;
 }
+
+// Host-side NVTX range around one phase of a run (enqueue time; a profiler attributes
+// the kernels launched inside it to the phase).  No-op unless a tool is attached.
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+  Phase(const Phase&) = delete;
+  Phase& operator=(const Phase&) = delete;
+};
 
 class Run {
  public:
@@ -283,6 +293,7 @@ class Run {
 
   // Initialize (App. "Initialization of the starting densities")
   spring_status enqueue_init() {
+    const Phase range("spring:initialize");
     SPRING_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * 4, s));
     for (cq = 0; cq < K; ++cq) {
       SPRING_TRY(launch_init_spheres(n, seed(), S0q(), P, prm.init_n_spheres, prm.init_gamma,
@@ -319,6 +330,7 @@ class Run {
 
   // Crossover (Alg. crossover)
   spring_status crossover(int g) {
+    const Phase range("spring:crossover");
     SPRING_TRY(fft2_unitary(n, -1, x_pop(), w_pop(), nullptr, P, s));
     if (prm.ca > 0.f) SPRING_TRY(average_moduli(g));
     SPRING_TRY(launch_random_choice(seed(), g, P, abc, s));
@@ -363,6 +375,7 @@ class Run {
   }
 
   spring_status shrinkwrap(float sigma, float tau) {
+    const Phase range("spring:update_support");
     SPRING_TRY(sync_x());
     SPRING_TRY(launch_smooth(n, x, sm0, sm1, NBT, sigma, imgmax, s));
     return launch_threshold(n, sm1, imgmax, tau, S, NBT, s);
@@ -370,12 +383,14 @@ class Run {
 
   // area k of the statistics (0: alpha_best, 2: alpha_eval), each pattern's own
   spring_status shrinkwrap_area(float sigma, int k) {
+    const Phase range("spring:update_support_size");
     SPRING_TRY(sync_x());
     SPRING_TRY(launch_smooth(n, x, sm0, sm1, NBT, sigma, nullptr, s));
     return launch_select_area(n, sm1, alpha + k, 4, S, NBT, s, NB);
   }
 
   spring_status errors() {
+    const Phase range("spring:get_error");
     SPRING_TRY(sync_x());
     SPRING_TRY(launch_row_fft(n, -1, x, w, S, NBT, 1.0f, s));
     SPRING_TRY(launch_col_err(n, w, Mall, NBT, part_err, s, mgroup));
@@ -406,6 +421,7 @@ class Run {
 
   // Improve (Alg. improve) of both populations with the paper's Sequence
   spring_status improve_paper(int g, float sigma, float tau) {
+    const Phase range("spring:improve");
     int ia = 0, er = 0;
     sequence_counts(g, &ia, &er);
     for (int r = 1; r <= R - 2; ++r) {
@@ -427,6 +443,7 @@ class Run {
   // UpdateSupport, the last er_tail iterations ER); the error is taken before the last
   // UpdateSupport
   spring_status improve_independent(int g, float sigma, float tau) {
+    const Phase range("spring:improve");
     if (prm.schedule == 1) {
       int ia = 0, er = 0;
       sequence_counts(g, &ia, &er);
@@ -445,6 +462,7 @@ class Run {
 
   // Improve (Alg. improve) of both populations at once
   spring_status improve(float sigma, float tau) {
+    const Phase range("spring:improve");
     const int K = prm.sw_period, alg = prm.algorithm;
     for (int blk = 1; blk <= R; ++blk) {
       if (blk < R) SPRING_TRY(iterations(alg, K));
@@ -464,6 +482,7 @@ class Run {
   }
 
   spring_status generation(int g) {
+    const Phase range("spring:generation");
     const double t = G > 1 ? (double)(g - 1) / (double)(G - 1) : 0.0;
     const float sigma = (float)(prm.sw_sigma + (prm.sw_sigma_end - prm.sw_sigma) * t);
     const float tau = (float)(prm.sw_threshold + (prm.sw_threshold_end - prm.sw_threshold) * t);
@@ -506,6 +525,7 @@ class Run {
 
   // Average (Eq. avgrec) of each pattern's final population and its error
   spring_status finish() {
+    const Phase range("spring:average");
     for (cq = 0; cq < K; ++cq) SPRING_TRY(average_and_error());
     cq = 0;
     return SPRING_OK;
