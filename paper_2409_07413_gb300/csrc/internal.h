@@ -76,9 +76,11 @@ spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int 
                             unsigned* img_max, cudaStream_t s);
 spring_status launch_threshold(int n, const float* sm, const unsigned* img_max, float tau,
                                uint8_t* S, int batch, cudaStream_t s);
-// image b uses alpha[(b / alpha_group) * alpha_stride]
+// image b uses alpha[(b / alpha_group) * alpha_stride]; scratch: device memory of
+// select_area_scratch_bytes(n, batch) bytes (at most batch x N x N floats for N >= 64)
+size_t select_area_scratch_bytes(int n, int batch);
 spring_status launch_select_area(int n, const float* sm, const int64_t* alpha, int alpha_stride,
-                                 uint8_t* S, int batch, cudaStream_t s, int alpha_group = 1);
+                                 uint8_t* S, int batch, cudaStream_t s, int alpha_group, void* scratch);
 
 // ---------------------------------------------------------------- k_ga.cu
 spring_status launch_random_choice(uint64_t seed, int g, int P, int32_t* abc, cudaStream_t s);

@@ -81,81 +81,72 @@ __global__ void __launch_bounds__(256) k_smooth_cols(const float* __restrict__ t
   }
 }
 
-// Radius-specialised passes (r = R <= 8, i.e. sigma <= 2): taps in registers and a sliding
-// window, so each output costs 2R+1 FMAs and about one shared-memory read.  The sum of each
-// output runs over d = 0..2R in the same order as in the general kernels (same bits).
-constexpr int SW_RK = 4;  // row outputs per thread
-
-template <int R>
-__global__ void __launch_bounds__(256) k_smooth_rows_r(const float2* __restrict__ x, float* __restrict__ tmp,
-                                                       int n, long long nrows, const Taps taps) {
-  extern __shared__ float ext_r[];  // rows_per_block x (n + 2R)
-  const int tpr = n / SW_RK;                   // threads per row
-  const int rpb = blockDim.x / tpr;            // rows per block
-  const int lr = threadIdx.x / tpr, lt = threadIdx.x % tpr;
-  const long long row = (long long)blockIdx.x * rpb + lr;
-  const int len = n + 2 * R;
-  float* ext = ext_r + lr * len;
-  float w[2 * R + 1];
-#pragma unroll
-  for (int d = 0; d <= 2 * R; ++d) w[d] = taps.w[d];
-  if (row < nrows) {
-    const long long row0 = row * n;
-    for (int k = lt; k < len; k += tpr) {
-      int c = k - R;
-      c %= n;
-      if (c < 0) c += n;
-      const float2 v = __ldg(&x[row0 + c]);
-      ext[k] = sqrtf(v.x * v.x + v.y * v.y);
-    }
-  }
-  __syncthreads();
-  if (row >= nrows || lr >= rpb) return;
-  const int c0 = lt * SW_RK;
-  float win[SW_RK + 2 * R];
-#pragma unroll
-  for (int k = 0; k < SW_RK + 2 * R; ++k) win[k] = ext[c0 + k];
-  float4 o;
-  float* op = &o.x;
-#pragma unroll
-  for (int j = 0; j < SW_RK; ++j) {
-    float acc = 0.f;
-#pragma unroll
-    for (int d = 0; d <= 2 * R; ++d) acc = fmaf(w[d], win[j + d], acc);
-    op[j] = acc;
-  }
-  *reinterpret_cast<float4*>(&tmp[row * n + c0]) = o;
-}
-
 constexpr int SW_CK = 8;  // column outputs per thread
 
+// Radius-specialised smoothing (r = R <= 8, i.e. sigma <= 2), both passes in one kernel: taps
+// in registers, and a block produces a tile of SW_TILE_ROWS rows x 32 columns.  |x| of the tile and its periodic halo (R rows above and below, R columns left
+// and right) is read once into shared memory, the row sums are formed for every row of the
+// halo'd tile, then the column sums from them.  Each output is summed over d = 0..2R in the
+// same order as in the general two-pass kernels above (same bits); the row-smoothed image
+// never goes through HBM.
 template <int R>
-__global__ void __launch_bounds__(256) k_smooth_cols_r(const float* __restrict__ tmp, float* __restrict__ out,
-                                                       int n, const Taps taps, unsigned* __restrict__ img_max) {
-  extern __shared__ float tile_r[];  // (SW_TILE_ROWS + 2R) x 32
-  const int tiles_x = n / 32, tiles_y = (n + SW_TILE_ROWS - 1) / SW_TILE_ROWS;
+__global__ void __launch_bounds__(256) k_smooth2d_r(const float2* __restrict__ x, float* __restrict__ out,
+                                                    int n, const Taps taps, unsigned* __restrict__ img_max) {
+  constexpr int TW = 32, IW = TW + 2 * R, IH = SW_TILE_ROWS + 2 * R;
+  __shared__ float a[IH * IW];  // |x| with halo
+  __shared__ float b[IH * TW];  // row sums
+  const int tiles_x = n / TW, tiles_y = (n + SW_TILE_ROWS - 1) / SW_TILE_ROWS;
   const int img = blockIdx.x / (tiles_x * tiles_y);
   const int rem = blockIdx.x % (tiles_x * tiles_y);
-  const int c0 = (rem % tiles_x) * 32, r0 = (rem / tiles_x) * SW_TILE_ROWS;
+  const int c0 = (rem % tiles_x) * TW, r0 = (rem / tiles_x) * SW_TILE_ROWS;
   const int rows_out = min(SW_TILE_ROWS, n - r0), rows_in = rows_out + 2 * R;
   const long long base = (long long)img * n * n;
   const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int k = ly; k < rows_in; k += 8) {
-    int rr = r0 - R + k;
-    rr %= n;
-    if (rr < 0) rr += n;
-    tile_r[k * 32 + lx] = __ldg(&tmp[base + (long long)rr * n + c0 + lx]);
+  // |x| of rows r0 - R .. r0 + rows_out + R - 1 and columns c0 - R .. c0 + TW + R - 1: every
+  // load of the warp's rows is issued before the first is used (IW - 32 = 2R < 32 extra
+  // columns: two loads per row at most)
+  constexpr int KPW = (IH + 7) / 8;  // rows per warp
+  int c_a = c0 - R + lx, c_b = c0 - R + 32 + lx;
+  c_a = c_a < 0 ? c_a + n : (c_a >= n ? c_a - n : c_a);  // R < n
+  c_b = c_b >= n ? c_b - n : c_b;
+  const bool has_b = lx < IW - 32;
+  float2 va[KPW], vb[KPW];
+#pragma unroll
+  for (int q = 0; q < KPW; ++q) {
+    const int k = ly + 8 * q;
+    if (k < rows_in) {
+      int rr = r0 - R + k;
+      rr = rr < 0 ? rr + n : (rr >= n ? rr - n : rr);
+      const float2* row = x + base + (long long)rr * n;
+      va[q] = __ldg(&row[c_a]);
+      if (has_b) vb[q] = __ldg(&row[c_b]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KPW; ++q) {
+    const int k = ly + 8 * q;
+    if (k < rows_in) {
+      a[k * IW + lx] = sqrtf(va[q].x * va[q].x + va[q].y * va[q].y);
+      if (has_b) a[k * IW + 32 + lx] = sqrtf(vb[q].x * vb[q].x + vb[q].y * vb[q].y);
+    }
   }
   float w[2 * R + 1];
 #pragma unroll
   for (int d = 0; d <= 2 * R; ++d) w[d] = taps.w[d];
+  __syncthreads();
+  for (int k = ly; k < rows_in; k += 8) {
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) acc = fmaf(w[d], a[k * IW + lx + d], acc);
+    b[k * TW + lx] = acc;
+  }
   __syncthreads();
   unsigned vmax = 0u;
   const int k0 = ly * SW_CK;  // 8 consecutive output rows per thread
   if (k0 < rows_out) {
     float win[SW_CK + 2 * R];
 #pragma unroll
-    for (int k = 0; k < SW_CK + 2 * R; ++k) win[k] = (k0 + k < rows_in) ? tile_r[(k0 + k) * 32 + lx] : 0.f;
+    for (int k = 0; k < SW_CK + 2 * R; ++k) win[k] = (k0 + k < rows_in) ? b[(k0 + k) * TW + lx] : 0.f;
 #pragma unroll
     for (int j = 0; j < SW_CK; ++j) {
       if (k0 + j < rows_out) {
@@ -175,21 +166,15 @@ __global__ void __launch_bounds__(256) k_smooth_cols_r(const float* __restrict__
 }
 
 template <int R>
-static spring_status smooth_r(int n, const float2* x, float* tmp, float* out, int batch, const Taps& taps,
+static spring_status smooth_r(int n, const float2* x, float* out, int batch, const Taps& taps,
                               unsigned* img_max, cudaStream_t s) {
-  const long long total = (long long)batch * n * n, nrows = (long long)batch * n;
-  const int tpr = n / SW_RK, rpb = 256 / tpr > 0 ? 256 / tpr : 1;
-  const size_t row_smem = sizeof(float) * rpb * (n + 2 * R);
-  const size_t col_smem = sizeof(float) * 32 * (SW_TILE_ROWS + 2 * R);
-  launch_begin(SPRING_KC_OTHER, s);
-  k_smooth_rows_r<R><<<(int)((nrows + rpb - 1) / rpb), rpb * tpr, row_smem, s>>>(x, tmp, n, nrows, taps);
-  SPRING_CHECK_LAUNCH();
-  launch_end(SPRING_KC_OTHER, s, total * 12.0);
+  static_assert(SW_TILE_ROWS == 8 * SW_CK, "eight warps of SW_CK output rows cover a tile");
+  const long long total = (long long)batch * n * n;
   const int tiles = (n / 32) * ((n + SW_TILE_ROWS - 1) / SW_TILE_ROWS);
   launch_begin(SPRING_KC_OTHER, s);
-  k_smooth_cols_r<R><<<batch * tiles, 256, col_smem, s>>>(tmp, out, n, taps, img_max);
+  k_smooth2d_r<R><<<batch * tiles, 256, 0, s>>>(x, out, n, taps, img_max);
   SPRING_CHECK_LAUNCH();
-  launch_end(SPRING_KC_OTHER, s, total * 8.0);
+  launch_end(SPRING_KC_OTHER, s, total * 12.0);
   return SPRING_OK;
 }
 
@@ -202,6 +187,9 @@ __global__ void k_threshold(const float* __restrict__ sm, const unsigned* __rest
                             double tau, uint8_t* __restrict__ S, long long nn) {
   __shared__ float f_s;
   const long long first = (long long)blockIdx.x * SW_THR_PER_BLOCK;  // blocks never straddle images
+  static_assert(SW_THR_PER_BLOCK == 4 * 256, "256 threads x 4 pixels");
+  // the thread's 4 consecutive pixels are loaded before the threshold is known
+  const float4 v = *reinterpret_cast<const float4*>(sm + first + 4 * threadIdx.x);
   if (threadIdx.x == 0) {
     const double t = tau * (double)__uint_as_float(img_max[first / nn]);
     float f = (float)t;
@@ -210,7 +198,12 @@ __global__ void k_threshold(const float* __restrict__ sm, const unsigned* __rest
   }
   __syncthreads();
   const float f = f_s;
-  for (int k = threadIdx.x; k < SW_THR_PER_BLOCK; k += blockDim.x) S[first + k] = sm[first + k] >= f ? 1 : 0;
+  uchar4 o;
+  o.x = v.x >= f ? 1 : 0;
+  o.y = v.y >= f ? 1 : 0;
+  o.z = v.z >= f ? 1 : 0;
+  o.w = v.w >= f ? 1 : 0;
+  *reinterpret_cast<uchar4*>(S + first + 4 * threadIdx.x) = o;
 }
 
 static Taps make_taps(float sigma) {
@@ -239,14 +232,14 @@ spring_status launch_smooth(int n, const float2* x, float* tmp, float* out, int 
   if (total == 0) return SPRING_OK;
   if (img_max) SPRING_CUDA(cudaMemsetAsync(img_max, 0, sizeof(unsigned) * batch, s));
   switch (taps.r) {
-    case 1: return smooth_r<1>(n, x, tmp, out, batch, taps, img_max, s);
-    case 2: return smooth_r<2>(n, x, tmp, out, batch, taps, img_max, s);
-    case 3: return smooth_r<3>(n, x, tmp, out, batch, taps, img_max, s);
-    case 4: return smooth_r<4>(n, x, tmp, out, batch, taps, img_max, s);
-    case 5: return smooth_r<5>(n, x, tmp, out, batch, taps, img_max, s);
-    case 6: return smooth_r<6>(n, x, tmp, out, batch, taps, img_max, s);
-    case 7: return smooth_r<7>(n, x, tmp, out, batch, taps, img_max, s);
-    case 8: return smooth_r<8>(n, x, tmp, out, batch, taps, img_max, s);
+    case 1: return smooth_r<1>(n, x, out, batch, taps, img_max, s);
+    case 2: return smooth_r<2>(n, x, out, batch, taps, img_max, s);
+    case 3: return smooth_r<3>(n, x, out, batch, taps, img_max, s);
+    case 4: return smooth_r<4>(n, x, out, batch, taps, img_max, s);
+    case 5: return smooth_r<5>(n, x, out, batch, taps, img_max, s);
+    case 6: return smooth_r<6>(n, x, out, batch, taps, img_max, s);
+    case 7: return smooth_r<7>(n, x, out, batch, taps, img_max, s);
+    case 8: return smooth_r<8>(n, x, out, batch, taps, img_max, s);
     default: break;
   }
   const size_t row_smem = sizeof(float) * (n + 2 * taps.r);
@@ -276,10 +269,7 @@ spring_status launch_threshold(int n, const float* sm, const unsigned* img_max, 
 }
 
 // ------------------------------------------------------------------ exact-area select
-// One block per image.  The alpha-th largest bit pattern is found digit by digit
-// (11, 11, 10 bits) from shared-memory histograms; pixels above it are selected, and of
-// the pixels equal to it the first (alpha - #above) in linear order.
-constexpr int SEL_THREADS = 1024;
+constexpr int SEL_THREADS = 1024;  // digit pick: two digits per thread
 
 __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_tot, unsigned* total) {
   // exclusive scan over the block in thread order
@@ -310,77 +300,208 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_t
   return r;
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) k_select_area(const float* __restrict__ sm,
-                                                             const int64_t* __restrict__ alpha,
-                                                             int alpha_stride, int alpha_group,
-                                                             uint8_t* __restrict__ S, int n) {
-  __shared__ unsigned hist[2048];
+// The alpha-th largest bit pattern of an image (sm >= 0, so the order of the float values
+// is that of their bit patterns) is found digit by digit, 11, 11 and 10 bits, from the
+// top.  Each pass histograms the digit over the pixels whose higher digits match the
+// prefix found so far: the image is split into chunks of SEL_CHUNK pixels, one block per
+// chunk, with block histograms in shared memory (equal bins of a warp merged first) added
+// into one global histogram per image; one block per image then picks the digit.  A final
+// pair of launches counts, per chunk, the pixels equal to the found pattern and writes S:
+// pixels above it are selected, and of those equal to it the first k in linear order.
+constexpr int SEL_CHUNK = 16384;
+constexpr int SEL_T = 512;
+constexpr int SEL_BINS = 2048;
+
+__host__ __device__ constexpr int sel_shift(int pass) { return pass == 0 ? 21 : pass == 1 ? 10 : 0; }
+__host__ __device__ constexpr int sel_width(int pass) { return pass == 2 ? 10 : 11; }
+
+struct SelScratch {
+  unsigned* ghist;  // [batch][SEL_BINS]
+  unsigned* state;  // [batch][4]: prefix, prefix mask, rank still to place, fill (0 none, 1 all 0, 2 all 1)
+  unsigned* eqcnt;  // [batch][chunks]
+};
+
+static int sel_chunks(long long nn) { return (int)((nn + SEL_CHUNK - 1) / SEL_CHUNK); }
+
+size_t select_area_scratch_bytes(int n, int batch) {
+  const long long nn = (long long)n * n;
+  return sizeof(unsigned) * (size_t)batch * (SEL_BINS + 4 + sel_chunks(nn));
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(SEL_T) k_sel_hist(const float* __restrict__ sm, const int64_t* __restrict__ alpha,
+                                                    int alpha_stride, int alpha_group, SelScratch sc, long long nn,
+                                                    int chunks) {
+  __shared__ unsigned hist[SEL_BINS];
+  constexpr int sh = sel_shift(PASS), nb = 1 << sel_width(PASS);
+  const int img = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+  unsigned prefix = 0, pmask = 0;
+  if (PASS == 0) {
+    const long long a = alpha[(long long)(img / alpha_group) * alpha_stride];
+    if (a <= 0 || a >= nn) return;  // filled by the write pass
+  } else {
+    if (sc.state[4 * img + 3]) return;
+    prefix = sc.state[4 * img + 0];
+    pmask = sc.state[4 * img + 1];
+  }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)img * nn;
+  const long long lo = (long long)ch * SEL_CHUNK, hi = min(nn, lo + SEL_CHUNK);
+  const int lane = threadIdx.x & 31;
+  for (long long i0 = lo; i0 < hi; i0 += blockDim.x) {  // every lane takes the same trips
+    const long long i = i0 + threadIdx.x;
+    const unsigned u = i < hi ? v[i] : 0u;
+    const bool take = i < hi && (u & pmask) == prefix;
+    const unsigned key = take ? (u >> sh) & (nb - 1) : 0xffffffffu;
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    if (take && lane == __ffs(same) - 1) atomicAdd(&hist[key], (unsigned)__popc(same));
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (hist[b]) atomicAdd(&sc.ghist[(long long)img * SEL_BINS + b], hist[b]);
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(SEL_THREADS) k_sel_digit(const int64_t* __restrict__ alpha, int alpha_stride,
+                                                          int alpha_group, SelScratch sc, long long nn) {
   __shared__ unsigned warp_tot[32];
   __shared__ unsigned total;
   __shared__ unsigned sel_digit, sel_above;
-  const long long nn = (long long)n * n;
-  const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)blockIdx.x * nn;
-  uint8_t* out = S + (long long)blockIdx.x * nn;
-  long long a = alpha[(long long)(blockIdx.x / alpha_group) * alpha_stride];
-  if (a <= 0 || a >= nn) {
-    const uint8_t fill = a <= 0 ? 0 : 1;
-    for (long long i = threadIdx.x; i < nn; i += blockDim.x) out[i] = fill;
+  constexpr int sh = sel_shift(PASS), nb = 1 << sel_width(PASS);
+  const int img = blockIdx.x;
+  unsigned* st = sc.state + 4 * img;
+  unsigned* gh = sc.ghist + (long long)img * SEL_BINS;
+  unsigned prefix = 0, pmask = 0, k = 0;
+  if (PASS == 0) {
+    const long long a = alpha[(long long)(img / alpha_group) * alpha_stride];
+    if (a <= 0 || a >= nn) {
+      if (threadIdx.x == 0) st[3] = a <= 0 ? 1u : 2u;
+      return;
+    }
+    k = (unsigned)a;
+  } else {
+    if (st[3]) return;
+    prefix = st[0];
+    pmask = st[1];
+    k = st[2];
+  }
+  // counts above each digit: scan over digits in decreasing order (two per thread)
+  const int d0 = nb - 1 - 2 * threadIdx.x, d1 = d0 - 1;
+  const unsigned c0 = (d0 >= 0) ? gh[d0] : 0u, c1 = (d1 >= 0) ? gh[d1] : 0u;
+  const unsigned above0 = block_excl_scan(c0 + c1, warp_tot, &total);
+  const unsigned above1 = above0 + c0;
+  if (d0 >= 0 && above0 < k && k <= above0 + c0) {
+    sel_digit = (unsigned)d0;
+    sel_above = above0;
+  }
+  if (d1 >= 0 && above1 < k && k <= above1 + c1) {
+    sel_digit = (unsigned)d1;
+    sel_above = above1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st[0] = prefix | (sel_digit << sh);
+    st[1] = pmask | ((unsigned)(nb - 1) << sh);
+    st[2] = k - sel_above;
+    st[3] = 0u;
+  }
+  for (int b = threadIdx.x; b < SEL_BINS; b += blockDim.x) gh[b] = 0u;  // clean for the next pass
+}
+
+// pixels equal to the found pattern, per chunk
+__global__ void __launch_bounds__(SEL_T) k_sel_eqcount(const float* __restrict__ sm, SelScratch sc, long long nn,
+                                                       int chunks) {
+  __shared__ unsigned cnt;
+  const int img = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+  if (sc.state[4 * img + 3]) return;
+  const unsigned prefix = sc.state[4 * img + 0];
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)img * nn;
+  const long long lo = (long long)ch * SEL_CHUNK, hi = min(nn, lo + SEL_CHUNK);
+  unsigned c = 0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) c += v[i] == prefix ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) sc.eqcnt[(long long)img * chunks + ch] = cnt;
+}
+
+__global__ void __launch_bounds__(SEL_T) k_sel_write(const float* __restrict__ sm, SelScratch sc,
+                                                     uint8_t* __restrict__ S, long long nn, int chunks) {
+  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned total;
+  const int img = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+  const long long lo = (long long)ch * SEL_CHUNK, hi = min(nn, lo + SEL_CHUNK);
+  uint8_t* out = S + (long long)img * nn;
+  const unsigned fill = sc.state[4 * img + 3];
+  if (fill) {
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) out[i] = fill == 2u ? 1 : 0;
     return;
   }
-  unsigned prefix = 0, pmask = 0;
-  unsigned k = (unsigned)a;  // rank still to place within the current prefix
-  const int shifts[3] = {21, 10, 0};
-  const int widths[3] = {11, 11, 10};
-  for (int pass = 0; pass < 3; ++pass) {
-    const int sh = shifts[pass], nb = 1 << widths[pass];
-    for (int b = threadIdx.x; b < 2048; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
-      const unsigned u = v[i];
-      if ((u & pmask) == prefix) atomicAdd(&hist[(u >> sh) & (nb - 1)], 1u);
-    }
-    __syncthreads();
-    // counts above each digit: scan over digits in decreasing order (two per thread)
-    const int d0 = nb - 1 - 2 * threadIdx.x, d1 = d0 - 1;
-    const unsigned c0 = (d0 >= 0) ? hist[d0] : 0u, c1 = (d1 >= 0) ? hist[d1] : 0u;
-    const unsigned above0 = block_excl_scan(c0 + c1, warp_tot, &total);
-    const unsigned above1 = above0 + c0;
-    if (d0 >= 0 && above0 < k && k <= above0 + c0) {
-      sel_digit = (unsigned)d0;
-      sel_above = above0;
-    }
-    if (d1 >= 0 && above1 < k && k <= above1 + c1) {
-      sel_digit = (unsigned)d1;
-      sel_above = above1;
-    }
-    __syncthreads();
-    prefix |= sel_digit << sh;
-    pmask |= (unsigned)(nb - 1) << sh;
-    k -= sel_above;
-    __syncthreads();
-  }
-  // prefix is the alpha-th largest pattern; k pixels equal to it are still to be taken
+  const unsigned prefix = sc.state[4 * img + 0], k = sc.state[4 * img + 2];
   unsigned eq_before = 0;
-  for (long long i0 = 0; i0 < nn; i0 += blockDim.x) {
+  for (int c = 0; c < ch; ++c) eq_before += sc.eqcnt[(long long)img * chunks + c];
+  const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)img * nn;
+  for (long long i0 = lo; i0 < hi; i0 += blockDim.x) {
     const long long i = i0 + threadIdx.x;
-    const unsigned u = (i < nn) ? v[i] : 0u;
-    const bool eq = (i < nn) && (u == prefix);
+    const unsigned u = (i < hi) ? v[i] : 0u;
+    const bool eq = (i < hi) && (u == prefix);
     const int any_eq = __syncthreads_count(eq);
     unsigned rank = 0;
     if (any_eq) rank = block_excl_scan(eq ? 1u : 0u, warp_tot, &total);
-    if (i < nn) out[i] = (u > prefix || (eq && eq_before + rank < k)) ? 1 : 0;
+    if (i < hi) out[i] = (u > prefix || (eq && eq_before + rank < k)) ? 1 : 0;
     eq_before += (unsigned)any_eq;
   }
 }
 
 spring_status launch_select_area(int n, const float* sm, const int64_t* alpha, int alpha_stride,
-                                 uint8_t* S, int batch, cudaStream_t s, int alpha_group) {
+                                 uint8_t* S, int batch, cudaStream_t s, int alpha_group, void* scratch) {
   if (batch < 1) return SPRING_OK;
   if (alpha_group < 1) return invalid("alpha_group must be >= 1");
+  if (!scratch) return invalid("select scratch missing");
+  const long long nn = (long long)n * n;
+  const int chunks = sel_chunks(nn);
+  SelScratch sc;
+  sc.ghist = static_cast<unsigned*>(scratch);
+  sc.state = sc.ghist + (size_t)batch * SEL_BINS;
+  sc.eqcnt = sc.state + (size_t)batch * 4;
+  SPRING_CUDA(cudaMemsetAsync(sc.ghist, 0, sizeof(unsigned) * (size_t)batch * SEL_BINS, s));
+  const int blocks = batch * chunks;
   launch_begin(SPRING_KC_OTHER, s);
-  k_select_area<<<batch, SEL_THREADS, 0, s>>>(sm, alpha, alpha_stride, alpha_group, S, n);
+  k_sel_hist<0><<<blocks, SEL_T, 0, s>>>(sm, alpha, alpha_stride, alpha_group, sc, nn, chunks);
   SPRING_CHECK_LAUNCH();
-  launch_end(SPRING_KC_OTHER, s, (double)batch * n * n * 13.0);
+  launch_end(SPRING_KC_OTHER, s, (double)nn * batch * 4.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_sel_digit<0><<<batch, SEL_THREADS, 0, s>>>(alpha, alpha_stride, alpha_group, sc, nn);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, 0.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_sel_hist<1><<<blocks, SEL_T, 0, s>>>(sm, alpha, alpha_stride, alpha_group, sc, nn, chunks);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)nn * batch * 4.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_sel_digit<1><<<batch, SEL_THREADS, 0, s>>>(alpha, alpha_stride, alpha_group, sc, nn);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, 0.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_sel_hist<2><<<blocks, SEL_T, 0, s>>>(sm, alpha, alpha_stride, alpha_group, sc, nn, chunks);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)nn * batch * 4.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_sel_digit<2><<<batch, SEL_THREADS, 0, s>>>(alpha, alpha_stride, alpha_group, sc, nn);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, 0.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_sel_eqcount<<<blocks, SEL_T, 0, s>>>(sm, sc, nn, chunks);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)nn * batch * 4.0);
+  launch_begin(SPRING_KC_OTHER, s);
+  k_sel_write<<<blocks, SEL_T, 0, s>>>(sm, sc, S, nn, chunks);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)nn * batch * 5.0);
   return SPRING_OK;
 }
 

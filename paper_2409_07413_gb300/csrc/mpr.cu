@@ -386,7 +386,7 @@ class Run {
     const Phase range("spring:update_support_size");
     SPRING_TRY(sync_x());
     SPRING_TRY(launch_smooth(n, x, sm0, sm1, NBT, sigma, nullptr, s));
-    return launch_select_area(n, sm1, alpha + k, 4, S, NBT, s, NB);
+    return launch_select_area(n, sm1, alpha + k, 4, S, NBT, s, NB, sm0);  // sm0 is free after the smoothing
   }
 
   spring_status errors() {

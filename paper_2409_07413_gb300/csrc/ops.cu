@@ -426,7 +426,7 @@ spring_status spring_update_support_size(const void* x, uint8_t* S, int batch, i
   float* t0 = tmp.as<float>();
   float* t1 = t0 + batch * nn;
   SPRING_TRY(launch_smooth(n, static_cast<const float2*>(x), t0, t1, batch, sigma, nullptr, s));
-  return launch_select_area(n, t1, alpha, 1, S, batch, s);
+  return launch_select_area(n, t1, alpha, 1, S, batch, s, 1, t0);  // t0 is free after the smoothing
 }
 
 spring_status spring_fourier_error(const void* x, const uint8_t* S, const float* M, int batch, int n,
