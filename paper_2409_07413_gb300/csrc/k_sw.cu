@@ -347,15 +347,22 @@ __global__ void __launch_bounds__(SEL_T) k_sel_hist(const float* __restrict__ sm
   for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)img * nn;
-  const long long lo = (long long)ch * SEL_CHUNK, hi = min(nn, lo + SEL_CHUNK);
+  const long long lo = (long long)ch * SEL_CHUNK, hi = min(nn, lo + SEL_CHUNK);  // multiples of 4
   const int lane = threadIdx.x & 31;
-  for (long long i0 = lo; i0 < hi; i0 += blockDim.x) {  // every lane takes the same trips
-    const long long i = i0 + threadIdx.x;
-    const unsigned u = i < hi ? v[i] : 0u;
-    const bool take = i < hi && (u & pmask) == prefix;
-    const unsigned key = take ? (u >> sh) & (nb - 1) : 0xffffffffu;
-    const unsigned same = __match_any_sync(0xffffffffu, key);
-    if (take && lane == __ffs(same) - 1) atomicAdd(&hist[key], (unsigned)__popc(same));
+  // four consecutive pixels per thread (one 16-byte load); every lane takes the same trips
+  for (long long b0 = lo; b0 < hi; b0 += 4LL * blockDim.x) {
+    const long long i = b0 + 4LL * threadIdx.x;
+    const uint4 q = i < hi ? *reinterpret_cast<const uint4*>(v + i) : make_uint4(0u, 0u, 0u, 0u);
+    const unsigned us[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const unsigned u = us[e];
+      const bool take = i < hi && (u & pmask) == prefix;
+      if (PASS > 0 && !__any_sync(0xffffffffu, take)) continue;  // later passes: few pixels match
+      const unsigned key = take ? (u >> sh) & (nb - 1) : 0xffffffffu;
+      const unsigned same = __match_any_sync(0xffffffffu, key);
+      if (take && lane == __ffs(same) - 1) atomicAdd(&hist[key], (unsigned)__popc(same));
+    }
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nb; b += blockDim.x)
@@ -445,15 +452,30 @@ __global__ void __launch_bounds__(SEL_T) k_sel_write(const float* __restrict__ s
   unsigned eq_before = 0;
   for (int c = 0; c < ch; ++c) eq_before += sc.eqcnt[(long long)img * chunks + c];
   const unsigned* v = reinterpret_cast<const unsigned*>(sm) + (long long)img * nn;
-  for (long long i0 = lo; i0 < hi; i0 += blockDim.x) {
-    const long long i = i0 + threadIdx.x;
-    const unsigned u = (i < hi) ? v[i] : 0u;
-    const bool eq = (i < hi) && (u == prefix);
-    const int any_eq = __syncthreads_count(eq);
-    unsigned rank = 0;
-    if (any_eq) rank = block_excl_scan(eq ? 1u : 0u, warp_tot, &total);
-    if (i < hi) out[i] = (u > prefix || (eq && eq_before + rank < k)) ? 1 : 0;
-    eq_before += (unsigned)any_eq;
+  // four consecutive pixels per thread; the rank of an equal pixel among the equal pixels
+  // of this step is the block's exclusive scan of the per-thread counts plus the equal
+  // pixels before it in the thread's four
+  for (long long b0 = lo; b0 < hi; b0 += 4LL * blockDim.x) {
+    const long long i = b0 + 4LL * threadIdx.x;
+    const bool in = i < hi;
+    const uint4 q = in ? *reinterpret_cast<const uint4*>(v + i) : make_uint4(0u, 0u, 0u, 0u);
+    const unsigned e0 = in && q.x == prefix, e1 = in && q.y == prefix, e2 = in && q.z == prefix,
+                   e3 = in && q.w == prefix;
+    const unsigned c = e0 + e1 + e2 + e3;
+    const int any_eq = __syncthreads_count(c > 0);
+    unsigned r = 0, step_total = 0;
+    if (any_eq) {
+      r = block_excl_scan(c, warp_tot, &total);
+      step_total = total;
+    }
+    const unsigned b = eq_before + r;
+    uchar4 o;
+    o.x = (q.x > prefix || (e0 && b < k)) ? 1 : 0;
+    o.y = (q.y > prefix || (e1 && b + e0 < k)) ? 1 : 0;
+    o.z = (q.z > prefix || (e2 && b + e0 + e1 < k)) ? 1 : 0;
+    o.w = (q.w > prefix || (e3 && b + e0 + e1 + e2 < k)) ? 1 : 0;
+    if (in) *reinterpret_cast<uchar4*>(out + i) = o;
+    eq_before += step_total;
   }
 }
 
