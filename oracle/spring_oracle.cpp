@@ -9,7 +9,7 @@
 // reconstruction in single-particle Coherent Diffraction Imaging" (arXiv 2409.07413).
 // Citations below name the paper's sections, equations and algorithms.
 //
-// Conventions (where the paper is silent; each reading is listed in the design doc):
+// Conventions (where the paper is silent, the reading taken):
 //  * Arrays are row-major N x N.  Fourier-space arrays (M, mask, spectra) are in DFT
 //    order (zero frequency at index 0); the top-level run takes detector-centred input
 //    and applies ifftshift once.  Real-space arrays are used as given.
@@ -515,7 +515,7 @@ extern "C" void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint
   philox_4x32_10(ctr, key, out);
 }
 
-// Counter layout of this build: (generation, individual, tag << 24 | a, b).
+// Counter layout: (generation, individual, tag << 24 | a, b).
 static void draw(uint64_t seed, uint32_t g, uint32_t p, uint32_t tag, uint32_t a, uint32_t b,
                  uint32_t out[4]) {
   uint32_t ctr[4] = {g, p, (tag << 24) | (a & 0xFFFFFFu), b};
