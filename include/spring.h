@@ -445,6 +445,15 @@ typedef struct {
 #define SPRING_KC_OTHER 2     /* every other kernel of the library */
 #define SPRING_KC_FUSED 3     /* on-chip whole iterations (spring_iterate_fused, N <= 256) */
 #define SPRING_KC_COUNT 4
+/* Failure detection.  Every device-side wait of the library is bounded: after its limit it
+ * records the timed-out wait in a per-device status word and its kernel returns; blocking
+ * runs read the word when their stream has completed and then return SPRING_E_TIMEOUT.
+ * This call exercises that path: one block waits on a barrier that nothing completes, with
+ * a limit of `cycles` clock cycles (1 .. 2^32), and the call returns SPRING_E_TIMEOUT when
+ * the timeout was detected and reported (SPRING_OK would mean it was not).  Blocking; the
+ * device stays usable.  INVALID for cycles outside the range. */
+spring_status spring_check_wait_timeout(long long cycles);
+
 void spring_stats_reset(void);
 /* on = 0: no timing; on = k >= 1: every k-th launch of each timed class (ROW_ITER,
  * COL_PM, FUSED) is bracketed by two events (k = 1: every launch).  A stride that is

@@ -63,6 +63,8 @@ spring_status encode_tmap_f32_3d(void* map, const void* base, int dim0, int dim1
                                  int box1);
 // read and clear the per-device status word (bit 2: a kernel's bounded wait timed out)
 spring_status take_device_status(int* out);
+// SPRING_E_TIMEOUT (and clears the word) if a bounded device-side wait timed out
+spring_status check_device_waits();
 
 // ---------------------------------------------------------------- composite transforms
 // unitary 2D transform of `batch` images: out = F x (dir -1) or F^-1 x (dir +1); in may

@@ -794,7 +794,8 @@ static void scheduler(spring_ctx* c) {
         r.rho_best = t->rho_best.data();
         r.support_avg = t->support_avg.data();
         r.gen_stats = t->gen_stats.data();
-        st = t->run->collect(&r);
+        st = check_device_waits();  // a bounded device-side wait that gave up
+        if (st == SPRING_OK) st = t->run->collect(&r);
         t->e_avg = r.final_error_avg;
         t->e_best = r.final_error_best;
         if (st != SPRING_OK) {
@@ -1082,6 +1083,7 @@ static spring_status run_blocking_k(spring_problem* const* probs, int K, const u
         }
       }
     }
+    if (st == SPRING_OK) st = check_device_waits();  // a bounded device-side wait that gave up
     if (st == SPRING_OK && save) st = run.download_population(save);
     if (st == SPRING_OK && out) {
       const double t0 = now_s();

@@ -9,6 +9,7 @@
 #include <cuda.h>
 
 #include "internal.h"
+#include "tma.cuh"
 
 namespace spring {
 
@@ -170,6 +171,27 @@ spring_status take_device_status(int* out) {
   return SPRING_OK;
 }
 
+spring_status check_device_waits() {
+  int v = 0;
+  SPRING_TRY(take_device_status(&v));
+  if (v & 2) {
+    set_error("a bounded device-side wait timed out (a TMA copy did not complete)");
+    return SPRING_E_TIMEOUT;
+  }
+  return SPRING_OK;
+}
+
+// One block waits on an mbarrier that expects two arrivals and gets none: the bounded
+// wait gives up after `cycles`, records the timed-out wait in the device status word
+// exactly as the TMA column pass does, and returns.
+__global__ void k_wait_check(int* status, long long cycles) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 2);
+  mbar_fence_init();
+  if (!mbar_wait_bounded(&bar, 0u, cycles)) atomicOr(status, 2);
+}
+
 // ------------------------------------------------------------------ TMA descriptors
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -251,6 +273,18 @@ using namespace spring;
 extern "C" {
 
 int spring_abi_version(void) { return SPRING_ABI_VERSION; }
+
+spring_status spring_check_wait_timeout(long long cycles) {
+  if (cycles < 1 || cycles > (1LL << 32)) return invalid("cycles must be in [1, 2^32]");
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  int stale = 0;
+  SPRING_TRY(take_device_status(&stale));  // start from a clear word
+  k_wait_check<<<1, 32>>>(tb.status, cycles);
+  SPRING_CHECK_LAUNCH();
+  SPRING_CUDA(cudaDeviceSynchronize());
+  return check_device_waits();
+}
 
 const char* spring_status_string(spring_status s) {
   switch (s) {

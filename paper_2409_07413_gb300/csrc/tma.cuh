@@ -38,11 +38,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// wait for the phase of the given parity; false after ~2^31 cycles without completion
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// wait for the phase of the given parity; false after `limit` cycles (default ~2^31, about
+// a second) without completion
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = 1LL << 31) {
   const long long start = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - start > (1LL << 31)) return false;
+    if (clock64() - start > limit) return false;
   return true;
 }
 

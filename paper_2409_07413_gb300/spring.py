@@ -64,6 +64,7 @@ _vp = C.c_void_p
 _i, _f, _u64 = C.c_int, C.c_float, C.c_uint64
 _SIGS = {
     "spring_abi_version": (_i, []),
+    "spring_check_wait_timeout": (_i, [C.c_longlong]),
     "spring_status_string": (C.c_char_p, [_i]),
     "spring_last_error": (C.c_char_p, []),
     "spring_params_default": (None, [C.POINTER(Params)]),
@@ -485,6 +486,12 @@ def stats_get(kc: int) -> KernelStat:
     s = KernelStat()
     lib().spring_stats_get(kc, C.byref(s))
     return s
+
+
+def check_wait_timeout(cycles: int = 1 << 20) -> int:
+    """Exercise the bounded-wait failure path (one block waits on a barrier nothing
+    completes); returns the library's status, E_TIMEOUT when the path works."""
+    return int(lib().spring_check_wait_timeout(int(cycles)))
 
 
 def launch_count() -> int:

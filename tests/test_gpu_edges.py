@@ -100,3 +100,24 @@ def test_nothing_measured_and_empty_support(sp, alg):
         assert not got.any()  # ER keeps nothing outside the support
     else:
         assert rel(got, ref) < TOL
+
+
+def test_bounded_wait_times_out_and_the_device_stays_usable(sp):
+    # failure detection without a fault: a block waits on a barrier that nothing completes,
+    # gives up after 2^20 cycles, records the timed-out wait, and the library reports it
+    assert sp.check_wait_timeout(1 << 20) == sp.E_TIMEOUT
+    assert "timed out" in sp.last_error()
+    assert sp.check_wait_timeout(0) == sp.E_INVALID
+    # the context is still usable and the status word was cleared: a transform afterwards
+    # matches the oracle, and a whole run completes without a timeout status
+    x, _ = synthetic.population_state(5, 2, 64)
+    xg = dev(c64(x))
+    sp.spring_fft2(xg)
+    assert rel(host(xg), oracle.fft2(c64(x))) < TOL
+    pat = synthetic.config_pattern("sphere64", 0)
+    ctx = sp.Context(0)
+    prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
+    r = prob.run(sp.params(pop=4, iters_per_gen=40, generations=2, er_tail=5, seed=1), want_arrays=False)
+    prob.destroy()
+    ctx.close()
+    assert np.isfinite(r["final_error_best"])
