@@ -35,13 +35,15 @@ WORKLOADS = {
 # comparison is over seeds)
 for _s in (1001, 1002, 1003):
     WORKLOADS[f"ell1024_g2_r{_s}"] = WORKLOADS["ell1024_g2"] + (_s,)
+for _s in range(1001, 1008):
     WORKLOADS[f"ell512_r{_s}"] = WORKLOADS["ell512"] + (_s,)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--only", default=None)
+    ap.add_argument("--only", default=None, help="workloads whose name starts with this")
+    ap.add_argument("--missing", action="store_true", help="only workloads not yet in the file")
     a = ap.parse_args()
     if a.threads:
         oracle.set_threads(a.threads)
@@ -49,6 +51,8 @@ def main():
     out = json.loads(out_path.read_text()) if out_path.exists() else {}
     for name, (recipe, pseed, prm, *rs) in WORKLOADS.items():
         if a.only and not name.startswith(a.only):
+            continue
+        if a.missing and name in out:
             continue
         run_seed = rs[0] if rs else RUN_SEED
         pat = synthetic.config_pattern(recipe, pseed)
