@@ -33,7 +33,7 @@ WORKLOADS = {
 # the reduced 1024 x 1024 run and the 512 x 512 run at further run seeds (a single
 # trajectory of HIO/RAAR and the GA varies by several percent with the rounding, so the
 # comparison is over seeds)
-for _s in (1001, 1002, 1003):
+for _s in range(1001, 1008):
     WORKLOADS[f"ell1024_g2_r{_s}"] = WORKLOADS["ell1024_g2"] + (_s,)
 for _s in range(1001, 1008):
     WORKLOADS[f"ell512_r{_s}"] = WORKLOADS["ell512"] + (_s,)
