@@ -67,6 +67,11 @@ class OrcResult(C.Structure):
     ]
 
 
+class OrcTrace(C.Structure):
+    _fields_ = [("err_parents", _dp), ("err_new", _dp), ("replaced", _u8p), ("parents", _ip),
+                ("areas", C.c_int64 * 3), ("best", C.c_int), ("gen_stats", C.c_double * 9)]
+
+
 _lib = None
 
 
@@ -117,6 +122,8 @@ def lib():
                                       C.POINTER(OrcResult)]),
             "orc_mpr_run_sat": (C.c_int, [_dp, _u8p, _u8p, _u8p, C.c_int, C.POINTER(OrcParams),
                                           C.POINTER(OrcResult)]),
+            "orc_mpr_step": (C.c_int, [_dp, _u8p, _u8p, C.c_int, C.POINTER(OrcParams), C.c_int,
+                                       _dp, _u8p, _dp, C.POINTER(OrcTrace)]),
             "orc_improve": (C.c_int, [_dp, _u8p, _dp, _u8p, C.c_int, C.c_int,
                                       C.POINTER(OrcParams), C.c_double, C.c_double, C.c_long,
                                       C.c_long, _dp]),
@@ -423,6 +430,34 @@ def improve(x, S, M, mask, params: OrcParams, sigma, tau, a_best, a_eval):
     if rc:
         raise ValueError("invalid arguments")
     return x, S, err
+
+
+def mpr_step(I_centred, mask_centred, state, saturated=None, **kw):
+    """One generation g = state["generation"] + 1 of Alg. mpr from a parent population
+    (pop_x P x n x n complex, pop_S, pop_err).  Returns (state after generation g, trace of
+    what it decided: improved errors of both populations, replacement flags, parents,
+    areas, the alpha_best individual and the gen_stats row)."""
+    I, mask = _f64(I_centred), _u8(mask_centred)
+    n = I.shape[0]
+    pr = make_params(**kw)
+    P = pr.pop
+    x = np.ascontiguousarray(state["pop_x"], np.complex128).copy()
+    S = np.ascontiguousarray(state["pop_S"], np.uint8).copy()
+    e = np.ascontiguousarray(state["pop_err"], np.float64).copy()
+    tr = {"err_parents": np.full(P, np.nan), "err_new": np.full(P, np.nan),
+          "replaced": np.zeros(P, np.uint8), "parents": np.full((P, 3), -1, np.int32)}
+    t = OrcTrace(_pd(tr["err_parents"]), _pd(tr["err_new"]), _pu8(tr["replaced"]),
+                 tr["parents"].ctypes.data_as(_ip))
+    sat = None if saturated is None else _u8(saturated)
+    g0 = int(state["generation"])
+    rc = lib().orc_mpr_step(_pd(I), _pu8(mask), None if sat is None else _pu8(sat), n, C.byref(pr), g0,
+                            _pd(x), _pu8(S), _pd(e), C.byref(t))
+    if rc:
+        raise ValueError("invalid MPR parameters or generation")
+    tr["areas"] = np.array(list(t.areas), np.int64)
+    tr["best"] = int(t.best)
+    tr["gen_stats"] = np.array(list(t.gen_stats))
+    return {"generation": g0 + 1, "pop_x": x, "pop_S": S, "pop_err": e}, tr
 
 
 def mpr_run(I_centred, mask_centred, S0, keep_population=False, saturated=None, **kw):

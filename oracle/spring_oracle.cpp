@@ -1037,37 +1037,43 @@ static void sequence(cd* x, const uint8_t* S, const double* M, const uint8_t* ma
   iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, er);
 }
 
+// Self-improvement of one individual (Alg. improve; Eq. sequence; App. "The modified
+// Shrink-wrap").  A generation's iterations fall into R blocks, each an iteration segment
+// followed by a support update.  The update after a block depends on its position: the
+// plain Shrink-wrap threshold after the first R - 2 blocks, the support resized to the best
+// parent's area after block R - 1, and to alpha_eval after block R.  Then come the ER
+// iterations of the evaluation sequence, the error (Eq. error_calc) and a last plain
+// Shrink-wrap.  The two schedules differ only in the segments:
+//   schedule 1 (the paper's Sequence): every block is seq(ia IA + er ER) with the counts
+//     of generation g, and the evaluation sequence has seq_eval ER iterations;
+//   schedule 0 (the configs: N_it iterations, support update every K, last er_tail ER):
+//     blocks of K IA iterations, the last block shortened to N_it - (R - 1) K - er_tail so
+//     that the er_tail ER iterations of the evaluation sequence complete N_it.
 static void improve_one(cd* x, uint8_t* S, const double* M, const uint8_t* mask, const double* U,
                         int n, const orc_params& pr, double sigma, double tau, long a_best, long a_eval,
                         double* err, int g, int G) {
-  if (pr.schedule == 1) {  // Alg. improve with the paper's Sequence
-    int ia, er;
+  int R, ia = 0, er = 0, eval_er;
+  if (pr.schedule == 1) {
+    R = pr.repetitions;
     sequence_counts(pr, g, G, &ia, &er);
-    for (int r = 1; r <= pr.repetitions - 2; r++) {
+    eval_er = pr.seq_eval;
+  } else {
+    R = pr.iters_per_gen / pr.sw_period;
+    eval_er = pr.er_tail;
+  }
+  for (int blk = 1; blk <= R; blk++) {
+    if (pr.schedule == 1) {
       sequence(x, S, M, mask, U, n, pr, ia, er);
-      update_support(x, S, n, sigma, tau);
+    } else {
+      const int len = blk < R ? pr.sw_period : pr.iters_per_gen - (R - 1) * pr.sw_period - pr.er_tail;
+      iterate_one(x, S, M, mask, U, n, pr.algorithm, pr.beta, pr.chi, len);
     }
-    sequence(x, S, M, mask, U, n, pr, ia, er);
-    update_support_size(x, S, n, sigma, a_best);
-    sequence(x, S, M, mask, U, n, pr, ia, er);
-    update_support_size(x, S, n, sigma, a_eval);
-    iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, pr.seq_eval);  // EvalSequence
-    *err = fourier_error(x, S, M, mask, n);
-    update_support(x, S, n, sigma, tau);
-    return;
+    if (blk <= R - 2)
+      update_support(x, S, n, sigma, tau);
+    else
+      update_support_size(x, S, n, sigma, blk == R - 1 ? a_best : a_eval);
   }
-  int K = pr.sw_period, R = pr.iters_per_gen / K;
-  int last = pr.iters_per_gen - (R - 1) * K;
-  int alg = pr.algorithm;
-  for (int blk = 1; blk <= R - 2; blk++) {
-    iterate_one(x, S, M, mask, U, n, alg, pr.beta, pr.chi, K);
-    update_support(x, S, n, sigma, tau);
-  }
-  iterate_one(x, S, M, mask, U, n, alg, pr.beta, pr.chi, K);
-  update_support_size(x, S, n, sigma, a_best);
-  iterate_one(x, S, M, mask, U, n, alg, pr.beta, pr.chi, last - pr.er_tail);
-  update_support_size(x, S, n, sigma, a_eval);
-  iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, pr.er_tail);
+  iterate_one(x, S, M, mask, U, n, 0, pr.beta, pr.chi, eval_er);  // EvalSequence: ER only
   *err = fourier_error(x, S, M, mask, n);
   update_support(x, S, n, sigma, tau);
 }
@@ -1107,162 +1113,278 @@ static void ifftshift2(const void* src, void* dst, int n, size_t esz) {
                   esz);
 }
 
+// Checks of a run's parameters; true if a run can be made with them.
+static bool valid_run_params(const orc_params& pr, int n) {
+  if (!valid_side(n) || pr.pop < 4 || pr.generations < 1) return false;
+  if (pr.mode != 0 && pr.mode != 1) return false;
+  if (pr.schedule == 0) {
+    if (pr.sw_period < 1) return false;
+    int R = pr.iters_per_gen / pr.sw_period;
+    if (R < 2) return false;
+    int last = pr.iters_per_gen - (R - 1) * pr.sw_period;
+    if (pr.er_tail < 0 || pr.er_tail > last) return false;
+  } else if (pr.schedule == 1) {
+    if (pr.repetitions < 2 || pr.seq_ia < 0 || pr.seq_er < 0 || pr.seq_eval < 0) return false;
+    if (pr.seq_ia + pr.seq_er < 1) return false;
+  } else {
+    return false;
+  }
+  return true;
+}
+
+// The pattern as a run uses it: moduli M = sqrt(I), the mask and (if enabled) the upper
+// bounds of the missing intensities (Eq. pm_bounds), all in DFT order.
+struct RunProblem {
+  int n = 0;
+  size_t nn = 0;
+  std::vector<double> M, U;
+  std::vector<uint8_t> mask;
+  const double* Up = nullptr;
+};
+
+static void make_problem(const double* I_c, const uint8_t* mask_c, const uint8_t* sat_c, int n,
+                         const orc_params& pr, RunProblem* pb) {
+  pb->n = n;
+  pb->nn = (size_t)n * n;
+  std::vector<double> I(pb->nn);
+  pb->M.resize(pb->nn);
+  pb->mask.resize(pb->nn);
+  ifftshift2(I_c, I.data(), n, sizeof(double));
+  ifftshift2(mask_c, pb->mask.data(), n, 1);
+  for (size_t i = 0; i < pb->nn; i++) pb->M[i] = std::sqrt(std::max(0.0, I[i]));
+  if (pr.ub_eta > 0.0) {
+    std::vector<double> Uc(pb->nn);
+    orc_upper_bounds(I_c, mask_c, sat_c, n, pr.ub_eta, pr.ub_max_missing, pr.ub_max_saturated, Uc.data());
+    pb->U.resize(pb->nn);
+    ifftshift2(Uc.data(), pb->U.data(), n, sizeof(double));
+    pb->Up = pb->U.data();
+  }
+}
+
+// The state of a run: the parent population (x, S, errors) and the new individuals that a
+// generation's crossover produces.
+struct RunPop {
+  std::vector<cd> px, nx;
+  std::vector<uint8_t> pS, nS;
+  std::vector<double> pe, ne;
+  void resize(int P, size_t nn) {
+    px.resize(P * nn);
+    nx.resize(P * nn);
+    pS.resize(P * nn);
+    nS.resize(P * nn);
+    pe.assign(P, std::numeric_limits<double>::infinity());
+    ne.assign(P, 0.0);
+  }
+};
+
+// What one generation decided (orc_mpr_step); pointer members may be null.
+struct orc_trace {
+  double* err_parents;  // P: errors of the improved parents, before Select
+  double* err_new;      // P: errors of the improved new individuals
+  uint8_t* replaced;    // P: 1 where Select took the new individual
+  int* parents;         // 3 P: (a, b, c) of new individual p at 3p .. 3p + 2
+  int64_t areas[3];     // alpha_best, alpha_all, alpha_eval of Alg. improve
+  int best;             // the parent whose area is alpha_best
+  double gen_stats[9];  // this generation's monitors (the gen_stats row)
+};
+
+// Per-generation monitors (Sec. "Monitoring the reconstruction process") of the parent
+// population after Select: best, mean and worst error, E(avg) (NaN unless monitored),
+// O_d, replacement fraction, mean Gamma, mean |sum rho| and its relative spread.
+static void monitors(const RunProblem& pb, const orc_params& pr, int g, int G, const RunPop& pop, int repl,
+                     double* st) {
+  const int P = pr.pop, n = pb.n;
+  const size_t nn = pb.nn;
+  int b = argmin_first(pop.pe);
+  double mn = 0.0, mx = pop.pe[0], gam = 0.0, sm = 0.0;
+  std::vector<double> sums(P);
+  for (int p = 0; p < P; p++) {
+    mn += pop.pe[p];
+    mx = std::max(mx, pop.pe[p]);
+    gam += complexity(&pop.px[p * nn], n, &sums[p]);
+    sm += sums[p];
+  }
+  st[0] = pop.pe[b];
+  st[1] = mn / P;
+  st[2] = mx;
+  st[3] = std::numeric_limits<double>::quiet_NaN();  // E(avg): final generation (set by the run)
+  if (pr.monitor_avg && g < G) {  // Sec. "Monitoring the reconstruction process"
+    std::vector<cd> av(nn);
+    std::vector<uint8_t> Sv(nn);
+    average(pop.px.data(), pop.pS.data(), pb.mask.data(), P, n, b, av.data(), Sv.data());
+    st[3] = fourier_error(av.data(), Sv.data(), pb.M.data(), pb.mask.data(), n);
+  }
+  st[4] = (double)nn / (double)std::max(1L, area(&pop.pS[b * nn], nn));
+  st[5] = (double)repl / P;
+  st[6] = gam / P;
+  st[7] = sm / P;
+  // spread of the density sums (Sec. "Crossover averaging"): population standard
+  // deviation relative to the mean, by the two-pass formula
+  double var = 0.0;
+  for (int p = 0; p < P; p++) var += (sums[p] - sm / P) * (sums[p] - sm / P);
+  st[8] = sm > 0.0 ? std::sqrt(var / P) / (sm / P) : 0.0;
+}
+
+// Linear parameter schedule over generations (App. "Changing values over generations")
+static void sw_params(const orc_params& pr, int g, int G, double* sigma, double* tau) {
+  double t = (G > 1) ? (double)(g - 1) / (double)(G - 1) : 0.0;
+  *sigma = pr.sw_sigma + (pr.sw_sigma_end - pr.sw_sigma) * t;
+  *tau = pr.sw_threshold + (pr.sw_threshold_end - pr.sw_threshold) * t;
+}
+
+// Generation g of the independent reconstructions (Alg. randomsearch): Improve only.
+static void independent_generation(const RunProblem& pb, const orc_params& pr, int g, RunPop& pop, double* st) {
+  const int P = pr.pop, G = pr.generations;
+  const size_t nn = pb.nn;
+  double sigma, tau;
+  sw_params(pr, g, G, &sigma, &tau);
+  parallel_for(P, [&](int p) {
+    improve_independent(&pop.px[p * nn], &pop.pS[p * nn], pb.M.data(), pb.mask.data(), pb.Up, pb.n, pr, sigma,
+                        tau, &pop.pe[p], g, G);
+  });
+  monitors(pb, pr, g, G, pop, 0, st);
+}
+
+// Generation g of MPR (Alg. mpr): Crossover of the parents into new individuals, the
+// areas of Alg. improve from the parents, Improve of both populations, Select.
+static void mpr_generation(const RunProblem& pb, const orc_params& pr, int g, RunPop& pop, orc_trace* tr,
+                           double* st) {
+  const int P = pr.pop, G = pr.generations, n = pb.n;
+  const size_t nn = pb.nn;
+  CrossCfg cf{pr.cw, pr.cp, pr.tile_min, pr.tile_max};
+  std::vector<double> Mavg;
+  if (pr.ca > 0.0) {  // the parents' average moduli for crossover averaging
+    Mavg.resize(nn);
+    orc_average_moduli(reinterpret_cast<const double*>(pop.px.data()), pop.pS.data(), pb.mask.data(), P, n,
+                       argmin_first(pop.pe), Mavg.data());
+    cf.ca = pr.ca;
+    cf.Mavg = Mavg.data();
+  }
+  // Crossover (Alg. crossover): new population from the parents
+  parallel_for(P, [&](int p) {
+    crossover_one(pop.px.data(), pop.pS.data(), pb.mask.data(), P, n, pr.seed, g, p, cf, pop.nx.data(),
+                  pop.nS.data(), nullptr);
+  });
+  // Areas (Alg. improve, first three steps), from the parent population
+  int best = (g == 1) ? 0 : argmin_first(pop.pe);
+  long a_best = area(&pop.pS[best * nn], nn);
+  std::vector<uint8_t> uni(nn, 0);
+  for (int p = 0; p < P; p++)
+    for (size_t i = 0; i < nn; i++) uni[i] |= pop.pS[p * nn + i];
+  long a_all = area(uni.data(), nn);
+  // alpha_eval = (g/G) alpha_best + (1 - g/G) alpha_all, rounded half up; evaluated
+  // exactly in integers so that no floating-point contraction can move a half-way case
+  long a_eval = (2L * ((long)g * a_best + (long)(G - g) * a_all) + G) / (2L * G);
+  double sigma, tau;
+  sw_params(pr, g, G, &sigma, &tau);
+  // Improve both populations
+  parallel_for(2 * P, [&](int q) {
+    bool old = q < P;
+    int p = old ? q : q - P;
+    cd* x = old ? &pop.px[p * nn] : &pop.nx[p * nn];
+    uint8_t* S = old ? &pop.pS[p * nn] : &pop.nS[p * nn];
+    double* e = old ? &pop.pe[p] : &pop.ne[p];
+    improve_one(x, S, pb.M.data(), pb.mask.data(), pb.Up, n, pr, sigma, tau, a_best, a_eval, e, g, G);
+  });
+  if (tr) {
+    if (tr->err_parents) std::copy(pop.pe.begin(), pop.pe.end(), tr->err_parents);
+    if (tr->err_new) std::copy(pop.ne.begin(), pop.ne.end(), tr->err_new);
+    if (tr->parents)
+      for (int p = 0; p < P; p++) random_choice(pr.seed, g, p, P, &tr->parents[3 * p]);
+    tr->areas[0] = a_best;
+    tr->areas[1] = a_all;
+    tr->areas[2] = a_eval;
+    tr->best = best;
+  }
+  // Select (Alg. select): strict <, ties keep the parent
+  int repl = 0;
+  for (int p = 0; p < P; p++) {
+    const bool r = pop.ne[p] < pop.pe[p];
+    if (r) {
+      std::copy(pop.nx.begin() + p * nn, pop.nx.begin() + (p + 1) * nn, pop.px.begin() + p * nn);
+      std::copy(pop.nS.begin() + p * nn, pop.nS.begin() + (p + 1) * nn, pop.pS.begin() + p * nn);
+      pop.pe[p] = pop.ne[p];
+      repl++;
+    }
+    if (tr && tr->replaced) tr->replaced[p] = r ? 1 : 0;
+  }
+  monitors(pb, pr, g, G, pop, repl, st);
+}
+
 // Returns 0 on success, 1 on invalid parameters.  I, mask: detector-centred; S0 real space.
 // sat_c: detector-centred saturation map (may be null), used by the upper bounds only
 extern "C" int orc_mpr_run_sat(const double* I_c, const uint8_t* mask_c, const uint8_t* sat_c,
                                const uint8_t* S0, int n, const orc_params* prm, orc_result* res) {
   const orc_params& pr = *prm;
-  if (!valid_side(n) || pr.pop < 4 || pr.generations < 1) return 1;
-  if (pr.mode != 0 && pr.mode != 1) return 1;
-  if (pr.schedule == 0) {
-    if (pr.sw_period < 1) return 1;
-    int R = pr.iters_per_gen / pr.sw_period;
-    if (R < 2) return 1;
-    int last = pr.iters_per_gen - (R - 1) * pr.sw_period;
-    if (pr.er_tail < 0 || pr.er_tail > last) return 1;
-  } else if (pr.schedule == 1) {
-    if (pr.repetitions < 2 || pr.seq_ia < 0 || pr.seq_er < 0 || pr.seq_eval < 0) return 1;
-    if (pr.seq_ia + pr.seq_er < 1) return 1;
-  } else {
-    return 1;
-  }
-  size_t nn = (size_t)n * n;
-  int P = pr.pop, G = pr.generations;
-  std::vector<double> I(nn), M(nn);
-  std::vector<uint8_t> mask(nn);
+  if (!valid_run_params(pr, n)) return 1;
+  RunProblem pb;
+  make_problem(I_c, mask_c, sat_c, n, pr, &pb);
+  const size_t nn = pb.nn;
+  const int P = pr.pop, G = pr.generations;
+  std::vector<double> I(nn);
   ifftshift2(I_c, I.data(), n, sizeof(double));
-  ifftshift2(mask_c, mask.data(), n, 1);
-  for (size_t i = 0; i < nn; i++) M[i] = std::sqrt(std::max(0.0, I[i]));
-  // upper bounds of the missing intensities (Eq. pm_bounds), in DFT order
-  std::vector<double> U;
-  const double* Up = nullptr;
-  if (pr.ub_eta > 0.0) {
-    std::vector<double> Uc(nn);
-    orc_upper_bounds(I_c, mask_c, sat_c, n, pr.ub_eta, pr.ub_max_missing, pr.ub_max_saturated, Uc.data());
-    U.resize(nn);
-    ifftshift2(Uc.data(), U.data(), n, sizeof(double));
-    Up = U.data();
+  RunPop pop;
+  pop.resize(P, nn);
+  orc_initialize(pr.seed, S0, I.data(), pb.mask.data(), n, P, pr.init_n_spheres, pr.init_gamma,
+                 pr.init_phi_max, reinterpret_cast<double*>(pop.px.data()));
+  for (int p = 0; p < P; p++) std::copy(S0, S0 + nn, pop.pS.begin() + p * nn);
+  double scratch[9];
+  for (int g = 1; g <= G; g++) {
+    double* st = res->gen_stats ? res->gen_stats + (size_t)(g - 1) * 9 : scratch;
+    if (pr.mode == 1)
+      independent_generation(pb, pr, g, pop, st);
+    else
+      mpr_generation(pb, pr, g, pop, nullptr, st);
   }
-
-  std::vector<cd> px(P * nn), nx(P * nn);
-  std::vector<uint8_t> pS(P * nn), nS(P * nn);
-  std::vector<double> pe(P, std::numeric_limits<double>::infinity()), ne(P);
-  orc_initialize(pr.seed, S0, I.data(), mask.data(), n, P, pr.init_n_spheres, pr.init_gamma,
-                 pr.init_phi_max, reinterpret_cast<double*>(px.data()));
-  for (int p = 0; p < P; p++) std::copy(S0, S0 + nn, pS.begin() + p * nn);
-  CrossCfg cf{pr.cw, pr.cp, pr.tile_min, pr.tile_max};
-  // per-generation monitors (Sec. "Monitoring the reconstruction process")
-  auto monitors = [&](int g, int repl) {
-    if (!res->gen_stats) return;
-    double* st = res->gen_stats + (size_t)(g - 1) * 9;
-    int b = argmin_first(pe);
-    double mn = 0.0, mx = pe[0], gam = 0.0, sm = 0.0;
-    std::vector<double> sums(P);
-    for (int p = 0; p < P; p++) {
-      mn += pe[p];
-      mx = std::max(mx, pe[p]);
-      gam += complexity(&px[p * nn], n, &sums[p]);
-      sm += sums[p];
-    }
-    st[0] = pe[b];
-    st[1] = mn / P;
-    st[2] = mx;
-    st[3] = std::numeric_limits<double>::quiet_NaN();  // E(avg): final generation (below)
-    if (pr.monitor_avg && g < G) {  // Sec. "Monitoring the reconstruction process"
-      std::vector<cd> av(nn);
-      std::vector<uint8_t> Sv(nn);
-      average(px.data(), pS.data(), mask.data(), P, n, b, av.data(), Sv.data());
-      st[3] = fourier_error(av.data(), Sv.data(), M.data(), mask.data(), n);
-    }
-    st[4] = (double)nn / (double)std::max(1L, area(&pS[b * nn], nn));
-    st[5] = (double)repl / P;
-    st[6] = gam / P;
-    st[7] = sm / P;
-    // spread of the density sums (Sec. "Crossover averaging"): population standard
-    // deviation relative to the mean, by the two-pass formula
-    double var = 0.0;
-    for (int p = 0; p < P; p++) var += (sums[p] - sm / P) * (sums[p] - sm / P);
-    st[8] = sm > 0.0 ? std::sqrt(var / P) / (sm / P) : 0.0;
-  };
-
-  for (int g = 1; g <= G && pr.mode == 1; g++) {
-    // independent reconstructions (Alg. randomsearch): Improve only
-    double t = (G > 1) ? (double)(g - 1) / (double)(G - 1) : 0.0;
-    double sigma = pr.sw_sigma + (pr.sw_sigma_end - pr.sw_sigma) * t;
-    double tau = pr.sw_threshold + (pr.sw_threshold_end - pr.sw_threshold) * t;
-    parallel_for(P, [&](int p) {
-      improve_independent(&px[p * nn], &pS[p * nn], M.data(), mask.data(), Up, n, pr, sigma, tau, &pe[p], g, G);
-    });
-    monitors(g, 0);
-  }
-
-  std::vector<double> Mavg;
-  for (int g = 1; g <= G && pr.mode == 0; g++) {
-    if (pr.ca > 0.0) {  // the parents' average moduli for crossover averaging
-      Mavg.resize(nn);
-      orc_average_moduli(reinterpret_cast<const double*>(px.data()), pS.data(), mask.data(), P, n,
-                         argmin_first(pe), Mavg.data());
-      cf.ca = pr.ca;
-      cf.Mavg = Mavg.data();
-    }
-    // Crossover (Alg. mpr): new population from the parents
-    parallel_for(P, [&](int p) {
-      crossover_one(px.data(), pS.data(), mask.data(), P, n, pr.seed, g, p, cf, nx.data(),
-                    nS.data(), nullptr);
-    });
-    // Areas (Alg. improve, first three steps), from the parent population
-    int best = (g == 1) ? 0 : argmin_first(pe);
-    long a_best = area(&pS[best * nn], nn);
-    std::vector<uint8_t> uni(nn, 0);
-    for (int p = 0; p < P; p++)
-      for (size_t i = 0; i < nn; i++) uni[i] |= pS[p * nn + i];
-    long a_all = area(uni.data(), nn);
-    // alpha_eval = (g/G) alpha_best + (1 - g/G) alpha_all, rounded half up; evaluated
-    // exactly in integers so that no floating-point contraction can move a half-way case
-    long a_eval = (2L * ((long)g * a_best + (long)(G - g) * a_all) + G) / (2L * G);
-    // Linear parameter schedule over generations (App. "Changing values over generations")
-    double t = (G > 1) ? (double)(g - 1) / (double)(G - 1) : 0.0;
-    double sigma = pr.sw_sigma + (pr.sw_sigma_end - pr.sw_sigma) * t;
-    double tau = pr.sw_threshold + (pr.sw_threshold_end - pr.sw_threshold) * t;
-    // Improve both populations
-    parallel_for(2 * P, [&](int q) {
-      bool old = q < P;
-      int p = old ? q : q - P;
-      cd* x = old ? &px[p * nn] : &nx[p * nn];
-      uint8_t* S = old ? &pS[p * nn] : &nS[p * nn];
-      double* e = old ? &pe[p] : &ne[p];
-      improve_one(x, S, M.data(), mask.data(), Up, n, pr, sigma, tau, a_best, a_eval, e, g, G);
-    });
-    // Select
-    int repl = 0;
-    for (int p = 0; p < P; p++)
-      if (ne[p] < pe[p]) {
-        std::copy(nx.begin() + p * nn, nx.begin() + (p + 1) * nn, px.begin() + p * nn);
-        std::copy(nS.begin() + p * nn, nS.begin() + (p + 1) * nn, pS.begin() + p * nn);
-        pe[p] = ne[p];
-        repl++;
-      }
-    monitors(g, repl);
-  }
-  int b = argmin_first(pe);
+  int b = argmin_first(pop.pe);
   std::vector<cd> avg(nn);
   std::vector<uint8_t> Savg(nn);
-  average(px.data(), pS.data(), mask.data(), P, n, b, avg.data(), Savg.data());
-  res->final_error_avg = fourier_error(avg.data(), Savg.data(), M.data(), mask.data(), n);
-  res->final_error_best = pe[b];
+  average(pop.px.data(), pop.pS.data(), pb.mask.data(), P, n, b, avg.data(), Savg.data());
+  res->final_error_avg = fourier_error(avg.data(), Savg.data(), pb.M.data(), pb.mask.data(), n);
+  res->final_error_best = pop.pe[b];
   if (res->gen_stats) res->gen_stats[(size_t)(G - 1) * 9 + 3] = res->final_error_avg;
   if (res->rho_avg) std::copy(avg.begin(), avg.end(), as_cd(res->rho_avg));
-  if (res->rho_best) std::copy(px.begin() + b * nn, px.begin() + (b + 1) * nn, as_cd(res->rho_best));
+  if (res->rho_best) std::copy(pop.px.begin() + b * nn, pop.px.begin() + (b + 1) * nn, as_cd(res->rho_best));
   if (res->support_avg) std::copy(Savg.begin(), Savg.end(), res->support_avg);
-  if (res->pop_x) std::copy(px.begin(), px.end(), as_cd(res->pop_x));
-  if (res->pop_S) std::copy(pS.begin(), pS.end(), res->pop_S);
-  if (res->pop_err) std::copy(pe.begin(), pe.end(), res->pop_err);
+  if (res->pop_x) std::copy(pop.px.begin(), pop.px.end(), as_cd(res->pop_x));
+  if (res->pop_S) std::copy(pop.pS.begin(), pop.pS.end(), res->pop_S);
+  if (res->pop_err) std::copy(pop.pe.begin(), pop.pe.end(), res->pop_err);
   return 0;
 }
 
 extern "C" int orc_mpr_run(const double* I_c, const uint8_t* mask_c, const uint8_t* S0, int n,
                            const orc_params* prm, orc_result* res) {
   return orc_mpr_run_sat(I_c, mask_c, nullptr, S0, n, prm, res);
+}
+
+// One generation g = g_from + 1 of the run (1 <= g <= G) from a given parent population
+// (pop_x: P x n x n interleaved complex, pop_S, pop_err; errors +inf before generation 1),
+// which it replaces by the population after that generation.  tr (may be null) receives
+// what the generation decided.  Returns 0 on success, 1 on invalid arguments.
+extern "C" int orc_mpr_step(const double* I_c, const uint8_t* mask_c, const uint8_t* sat_c, int n,
+                            const orc_params* prm, int g_from, double* pop_x, uint8_t* pop_S, double* pop_err,
+                            orc_trace* tr) {
+  const orc_params& pr = *prm;
+  if (!valid_run_params(pr, n) || g_from < 0 || g_from >= pr.generations) return 1;
+  RunProblem pb;
+  make_problem(I_c, mask_c, sat_c, n, pr, &pb);
+  const size_t nn = pb.nn;
+  const int P = pr.pop, g = g_from + 1;
+  RunPop pop;
+  pop.resize(P, nn);
+  std::copy(as_cd(pop_x), as_cd(pop_x) + P * nn, pop.px.begin());
+  std::copy(pop_S, pop_S + P * nn, pop.pS.begin());
+  std::copy(pop_err, pop_err + P, pop.pe.begin());
+  double scratch[9];
+  double* st = tr ? tr->gen_stats : scratch;
+  if (pr.mode == 1)
+    independent_generation(pb, pr, g, pop, st);
+  else
+    mpr_generation(pb, pr, g, pop, tr, st);
+  std::copy(pop.px.begin(), pop.px.end(), as_cd(pop_x));
+  std::copy(pop.pS.begin(), pop.pS.end(), pop_S);
+  std::copy(pop.pe.begin(), pop.pe.end(), pop_err);
+  return 0;
 }
 
 // Improve on an explicit batch (used by the CPU-baseline timing and by parity tests of
