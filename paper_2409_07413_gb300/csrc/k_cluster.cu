@@ -167,8 +167,8 @@ static spring_status cluster_launch(const ClusterArgs& a, long long batch, bool 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  // algorithmic HBM bytes: x and S in, x out, once per launch (M from L2)
-  const double bytes = (double)batch * N * N * 17.0;
+  // algorithmic HBM bytes: x and S (1 bit/px) in, x out, once per launch (M from L2)
+  const double bytes = (double)batch * N * N * 16.125;
   launch_begin(SPRING_KC_FUSED, s);
   SPRING_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
   launch_end(SPRING_KC_FUSED, s, bytes);

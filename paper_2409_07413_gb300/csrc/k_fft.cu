@@ -90,7 +90,9 @@ spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint8_
   op.ra.chi_on = chi < 1.0f;
   op.ra.cchi = (float)((chi == 0.5f) ? 0.0 : std::cos((double)chi * 3.14159265358979323846));
   op.ra.zout = zout ? 1 : 0;
-  op.bytes = (double)batch * n * n * (8.0 + (alg ? 8.0 : 0.0) + 8.0 + (zout ? 8.0 : 0.0) + 1.0);
+  // algorithmic bytes: w in, x_n in (not for ER), x_{n+1} out, w out, and the support at
+  // its information content of one bit per pixel (the kernel reads it as one byte)
+  op.bytes = (double)batch * n * n * (8.0 + (alg ? 8.0 : 0.0) + 8.0 + (zout ? 8.0 : 0.0) + 0.125);
   return dispatch(n, op, s);
 }
 
@@ -115,7 +117,7 @@ spring_status launch_row_fft(int n, int dir, const float2* in, float2* out, cons
   return launch_row_fft_tw(n, dir, in, out, Smul, batch, scale, tb.tw, s);
 }
 
-spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s, int m_group) {
+spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s, int m_group, int img0) {
   if (side_index(n) < 0) return invalid("unsupported pattern side");
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
@@ -128,6 +130,7 @@ spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStr
   op.ca.tw = tb.tw + tw_offset(n);
   op.ca.batch = batch;
   op.ca.m_group = m_group;
+  op.ca.img0 = img0;
   const double nm = m_group > 0 ? (double)((batch + m_group - 1) / m_group) : 1.0;
   op.bytes = (double)batch * n * n * 16.0 + nm * n * n * 4.0;
   return dispatch(n, op, s);
@@ -254,7 +257,7 @@ spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint8_
   op.ra.cchi = (float)((chi == 0.5f) ? 0.0 : std::cos((double)chi * 3.14159265358979323846));
   op.ra.zout = 1;
   op.ra.s16 = s16;
-  op.bytes = (double)batch * n * n * (4.0 + (alg ? 4.0 : 0.0) + 4.0 + 4.0 + 1.0);
+  op.bytes = (double)batch * n * n * (4.0 + (alg ? 4.0 : 0.0) + 4.0 + 4.0 + 0.125);  // support: 1 bit/px
   return dispatch(n, op, s);
 }
 
