@@ -218,6 +218,30 @@ spring_status spring_mpr_run_until(spring_problem* prob, const spring_params* p,
 spring_status spring_mpr_resume(spring_problem* prob, const spring_params* p, const spring_population* from,
                                 spring_result* out);
 
+/* What one generation decided (spring_mpr_step).  Pointer members are caller-owned host
+ * buffers and may be NULL; the rest is filled in.  For mode 1 (independent
+ * reconstructions) only err_parents and gen_stats are meaningful. */
+typedef struct {
+  double* err_parents;  /* P: errors (Eq. error_calc) of the parents after their Improve, before
+                           Select (Alg. mpr) */
+  double* err_new;      /* P: errors of the new individuals after their Improve */
+  uint8_t* replaced;    /* P: 1 where Select (Alg. select) took the new individual */
+  int32_t* parents;     /* 3 x P: parents (a, b, c) of new individual p at 3p .. 3p + 2 (Alg.
+                           crossover, RandomChoice) */
+  int64_t areas[3];     /* alpha_best, alpha_all, alpha_eval (Alg. improve) */
+  int32_t best;         /* the parent whose support area is alpha_best */
+  double gen_stats[SPRING_GEN_STATS_COLS]; /* this generation's row of spring_result.gen_stats */
+} spring_generation_trace;
+/* One generation g = from->generation + 1 (g <= p->generations) of the run spring_mpr_run
+ * would make, from the given parent population: Crossover, the areas, Improve of both
+ * populations, Select (Alg. mpr), with the schedules of generation g of G.  The population
+ * after it goes to *to (to->generation = g; may alias *from's buffers).  trace may be
+ * NULL.  Chaining steps from g = 0 (a population of initial densities with errors +inf)
+ * reproduces spring_mpr_run's population bit for bit.  Blocking.
+ * Errors: INVALID (arguments, generation), then as spring_mpr_run. */
+spring_status spring_mpr_step(spring_problem* prob, const spring_params* p, const spring_population* from,
+                              spring_population* to, spring_generation_trace* trace);
+
 /* Serving: queue a run; requests are admitted in arrival order while their footprint fits
  * the HBM budget and fewer than SPRING_MAX_ACTIVE (environment, default 2) are running;
  * running requests advance concurrently on the device, one generation per scheduler turn,

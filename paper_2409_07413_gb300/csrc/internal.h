@@ -12,7 +12,8 @@ spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint8_
                               long long batch, float beta, float chi, bool zout, cudaStream_t s);
 // iteration column pass: colFFT, masked modulus projection, colIFFT, in place on w.
 // m_group > 0: M holds one N x N array per m_group consecutive images (a batch of patterns)
-spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s, int m_group = 0);
+spring_status launch_col_pm(int n, float2* w, const float* M, int batch, cudaStream_t s, int m_group = 0,
+                           int img0 = 0);
 // plain row transform (dir -1 forward, +1 inverse), unnormalised times `scale`;
 // Smul (forward only, may be null) multiplies the input by the support first
 spring_status launch_row_fft(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,

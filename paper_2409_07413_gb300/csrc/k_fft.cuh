@@ -13,8 +13,9 @@
 //                                   w = colIFFT(Y / N)
 //
 // so the next row pass's inverse row transform completes F^-1 and yields P_M x_{n+1}.
-// Per iteration and pixel this moves 8 (w) + 8 (x_n) + 1 (S) + 8 (x_{n+1}) + 8 (w) bytes
-// in the row pass and 8 + 8 in the column pass: 49 B (ER: 41 B, x_n unread).
+// Per iteration and pixel this moves 8 (w) + 8 (x_n) + 1 (S, one byte per pixel; its
+// information content is one bit) + 8 (x_{n+1}) + 8 (w) bytes in the row pass and 8 + 8 in
+// the column pass: 49 B (ER: 41 B, x_n unread); counting the support at 1/8 B, 48.125 B.
 //
 // Launch-shape variants (bit-identical results within a plan):
 //   row:    0 = state loads before the inverse transform, 1 block/SM of registers;
@@ -145,11 +146,12 @@ struct ColArgs {
   double* partials;   // ERR: [batch][N / ERR_W][2] (sum Xi (|X| - M)^2, sum Xi M^2)
   const float* s16;   // FP16 storage: device scalar s16 (power of two)
   int m_group;        // > 0: M holds one N x N array per m_group consecutive images
+  int img0;           // index of data's first image in the m_group numbering
 };
 
 // the modulus array of image img
 __device__ __forceinline__ const float* m_of(const ColArgs& a, int img, int n) {
-  return a.m_group > 0 ? a.M + (size_t)(img / a.m_group) * n * n : a.M;
+  return a.m_group > 0 ? a.M + (size_t)((a.img0 + img) / a.m_group) * n * n : a.M;
 }
 
 struct FftOp {
@@ -203,8 +205,10 @@ __device__ __forceinline__ float2 update_pixel(int alg, float2 xo, float2 pm, bo
 template <class P>
 __host__ __device__ constexpr int stage_elems() { return P::N + P::N / 8; }
 
-template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false, class ST = float2>
-__global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
+// The row pass of the blocks blk, blk + nblk, ... (G rows each) of a launch of
+// ROW_THREADS threads per block (k_row runs it over its grid).
+template <class P, int MODE, int ALG, bool LATE, bool STAGE = false, class ST = float2>
+__device__ __forceinline__ void row_pass(const RowArgs& a, long long blk, long long nblk) {
   constexpr int N = P::N, E = P::E, T = P::T, G = ROW_THREADS / T, SME = pad_elems_p<P>();
   extern __shared__ float2 smem[];
   const int grp = threadIdx.x / T, t = threadIdx.x % T;
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
   float2* xs = smem + G * SME + grp * stage_elems<P>();  // STAGE: x row, then S row
   uint8_t* ss = reinterpret_cast<uint8_t*>(xs + N);
   const auto sync = GroupSync<T>::make();
-  for (long long row = (long long)blockIdx.x * G + grp; row < a.nrows; row += (long long)gridDim.x * G) {
+  for (long long row = blk * G + grp; row < a.nrows; row += nblk * G) {
     const long long base = row * N + t;
     float2 v[E];
     if constexpr (MODE == ROW_ITER && STAGE) {
@@ -311,14 +315,21 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
   }
 }
 
+template <class P, int MODE, int ALG, bool LATE, int MINB, bool STAGE = false, class ST = float2>
+__global__ void __launch_bounds__(ROW_THREADS, MINB) k_row(RowArgs a) {
+  row_pass<P, MODE, ALG, LATE, STAGE, ST>(a, blockIdx.x, gridDim.x);
+}
+
+// The column pass of tile `tile` (image tile / (N / W), strip of W columns) by a block of
+// W * P::T threads (k_col runs one tile per block).
 template <class P, int W, int MODE, class ST = float2>
-__global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(ColArgs a) {
+__device__ __forceinline__ void col_pass(const ColArgs& a, int tile) {
   constexpr int N = P::N, E = P::E, T = P::T, STRIPS = N / W;
   constexpr bool H = std::is_same<ST, __half2>::value;
   const float ws = H ? w16_scale(N) * __ldg(a.s16) : 1.0f, iws = 1.0f / ws;
   extern __shared__ float2 smem[];
   const int c = threadIdx.x % W, t = threadIdx.x / W;
-  const int img = blockIdx.x / STRIPS, strip = blockIdx.x % STRIPS;
+  const int img = tile / STRIPS, strip = tile % STRIPS;
   const int col = strip * W + c;
   ST* base = reinterpret_cast<ST*>(a.data) + (size_t)img * N * N + col;
   const BlockSync sync;
@@ -400,6 +411,11 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(Col
       a.partials[((size_t)img * STRIPS + strip) * 2 + 1] = sd;
     }
   }
+}
+
+template <class P, int W, int MODE, class ST = float2>
+__global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(ColArgs a) {
+  col_pass<P, W, MODE, ST>(a, blockIdx.x);
 }
 
 // Column pass (COL_PM) with transposed tiles.  The block's W columns are read with
@@ -560,7 +576,7 @@ __global__ void __launch_bounds__(W * P::T, (W * P::T <= 256 ? 2 : 1))
 #pragma unroll
     for (int k = 0; k < NBOX; ++k) {
       tma_load_3d(dst + k * BOXR * W, &tmap, strip * 2 * W, k * BOXR, img, &mbar[b]);
-      tma_load_3d(mdst + k * BOXR * W, &mmap, strip * W, k * BOXR, a.m_group > 0 ? img / a.m_group : 0,
+      tma_load_3d(mdst + k * BOXR * W, &mmap, strip * W, k * BOXR, a.m_group > 0 ? (a.img0 + img) / a.m_group : 0,
                   &mbar[b]);
     }
   };

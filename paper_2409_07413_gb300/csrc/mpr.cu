@@ -170,6 +170,10 @@ class Run {
   unsigned* imgmax = nullptr;
   int* status = nullptr;
   float* mavg = nullptr;  // crossover averaging: (M-dot + M-double-dot) / 2
+  // spring_mpr_step's trace (single-pattern runs): the improved parents' errors before
+  // Select, and the parent whose area is alpha_best (device buffers owned by the caller)
+  double* tr_err = nullptr;
+  int32_t* tr_best = nullptr;
   void *peaks = nullptr, *init_sc = nullptr;
   bool z_valid = false;
   // precision 1: the iteration blocks keep x and w as half2 inside the w buffer
@@ -488,6 +492,7 @@ class Run {
     const float tau = (float)(prm.sw_threshold + (prm.sw_threshold_end - prm.sw_threshold) * t);
     if (prm.mode == 1) {  // independent reconstructions (Alg. randomsearch)
       SPRING_TRY(improve_independent(g, sigma, tau));
+      if (tr_err) SPRING_CUDA(cudaMemcpyAsync(tr_err, err_pop(), sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
       SPRING_CUDA(cudaMemsetAsync(repl, 0, P, s));
       SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
       SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + SPRING_GEN_STATS_COLS * (g - 1), s));
@@ -498,6 +503,7 @@ class Run {
       SPRING_TRY(crossover(g));
       SPRING_TRY(launch_argmin(g == 1 ? nullptr : err_pop(), P, bestq(), s));
       SPRING_TRY(launch_area_stats(n, S_pop(), bestq(), P, g, G, alphaq(), s));
+      if (tr_best) SPRING_CUDA(cudaMemcpyAsync(tr_best, bestq(), sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
     cq = 0;
     if (prm.schedule == 1)
@@ -505,6 +511,7 @@ class Run {
     else
       SPRING_TRY(improve(sigma, tau));
     for (cq = 0; cq < K; ++cq) {
+      if (tr_err) SPRING_CUDA(cudaMemcpyAsync(tr_err, err_pop(), sizeof(double) * P, cudaMemcpyDeviceToDevice, s));
       SPRING_TRY(launch_select(n, x_pop(), S_pop(), err_pop(), x_new(), S_new(), err_new(), P, repl, s));
       SPRING_TRY(launch_density_sums(n, x_pop(), P, part_dens, dens, s));
       SPRING_TRY(launch_gen_stats(n, err_pop(), S_pop(), repl, dens, P, statsq() + SPRING_GEN_STATS_COLS * (g - 1), s));
@@ -563,7 +570,21 @@ class Run {
     SPRING_CUDA(cudaMemcpy(to->pop_x, x_pop(), sizeof(float2) * P * nn(), cudaMemcpyDeviceToHost));
     SPRING_CUDA(cudaMemcpy(to->pop_S, S_pop(), (size_t)P * nn(), cudaMemcpyDeviceToHost));
     SPRING_CUDA(cudaMemcpy(to->pop_err, err_pop(), sizeof(double) * P, cudaMemcpyDeviceToHost));
-    to->generation = next_gen - 1;
+    to->generation = next_gen - 1 < G ? next_gen - 1 : G;  // next_gen passes G + 1 once the average ran
+    return SPRING_OK;
+  }
+
+  // after the stream has completed: what generation g decided (spring_mpr_step)
+  spring_status download_trace(int g, spring_generation_trace* tr) {
+    SPRING_CUDA(cudaMemcpy(tr->gen_stats, statsq() + SPRING_GEN_STATS_COLS * (g - 1),
+                           sizeof(double) * SPRING_GEN_STATS_COLS, cudaMemcpyDeviceToHost));
+    if (tr->err_parents) SPRING_CUDA(cudaMemcpy(tr->err_parents, tr_err, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    if (prm.mode == 1) return SPRING_OK;
+    if (tr->err_new) SPRING_CUDA(cudaMemcpy(tr->err_new, err_new(), sizeof(double) * P, cudaMemcpyDeviceToHost));
+    if (tr->replaced) SPRING_CUDA(cudaMemcpy(tr->replaced, repl, P, cudaMemcpyDeviceToHost));
+    if (tr->parents) SPRING_CUDA(cudaMemcpy(tr->parents, abc, sizeof(int32_t) * 3 * P, cudaMemcpyDeviceToHost));
+    SPRING_CUDA(cudaMemcpy(tr->areas, alphaq(), sizeof(int64_t) * 3, cudaMemcpyDeviceToHost));
+    SPRING_CUDA(cudaMemcpy(&tr->best, tr_best, sizeof(int32_t), cudaMemcpyDeviceToHost));
     return SPRING_OK;
   }
 
@@ -1028,7 +1049,8 @@ spring_status spring_problem_destroy(spring_problem* pr) {
 // (0 = all, then the averages into out[0..K)), saving the population if asked.
 static spring_status run_blocking_k(spring_problem* const* probs, int K, const uint64_t* seeds,
                                     const spring_params* p, const spring_population* from, int stop,
-                                    spring_population* save, spring_result* out) {
+                                    spring_population* save, spring_result* out,
+                                    spring_generation_trace* trace = nullptr) {
   spring_problem* pr = probs[0];
   SPRING_TRY(validate_params(pr->n, *p));
   spring_ctx* c = pr->ctx;
@@ -1050,6 +1072,13 @@ static spring_status run_blocking_k(spring_problem* const* probs, int K, const u
     if (st == SPRING_OK) st = run.setup_batch(probs, K, seeds, *p, s);
     if (st == SPRING_OK && from) st = run.upload_population(*from);
     run.stop_after = stop;
+    void* trace_mem = nullptr;
+    if (st == SPRING_OK && trace) {
+      e = cudaMalloc(&trace_mem, sizeof(double) * p->pop + 64);
+      if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+      run.tr_err = static_cast<double*>(trace_mem);
+      run.tr_best = reinterpret_cast<int32_t*>(static_cast<char*>(trace_mem) + sizeof(double) * p->pop);
+    }
     if (st == SPRING_OK) {
       if (p->use_graph) {
         cudaGraph_t graph = nullptr;
@@ -1084,6 +1113,8 @@ static spring_status run_blocking_k(spring_problem* const* probs, int K, const u
       }
     }
     if (st == SPRING_OK) st = check_device_waits();  // a bounded device-side wait that gave up
+    if (st == SPRING_OK && trace) st = run.download_trace(stop, trace);
+    if (trace_mem) cudaFree(trace_mem);
     if (st == SPRING_OK && save) st = run.download_population(save);
     if (st == SPRING_OK && out) {
       const double t0 = now_s();
@@ -1143,6 +1174,18 @@ spring_status spring_mpr_resume(spring_problem* pr, const spring_params* p, cons
   if (from->generation < 0 || from->generation >= p->generations)
     return invalid("the saved generation must be in [0, generations)");
   return run_blocking(pr, p, from, 0, nullptr, out);
+}
+
+spring_status spring_mpr_step(spring_problem* pr, const spring_params* p, const spring_population* from,
+                              spring_population* to, spring_generation_trace* trace) {
+  if (!pr || !p || !from || !to || !from->pop_x || !from->pop_S || !from->pop_err || !to->pop_x ||
+      !to->pop_S || !to->pop_err)
+    return invalid("null argument");
+  if (from->generation < 0 || from->generation >= p->generations)
+    return invalid("the starting generation must be in [0, generations)");
+  if (p->use_graph) return invalid("a single generation is not captured in a graph (use_graph = 0)");
+  const int g = from->generation + 1;
+  return run_blocking_k(&pr, 1, &p->seed, p, from, g, to, nullptr, trace);
 }
 
 spring_status spring_submit(spring_ctx* c, spring_problem* pr, const spring_params* p, uint64_t* ticket) {

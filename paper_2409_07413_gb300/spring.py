@@ -51,6 +51,12 @@ class Population(C.Structure):
                 ("pop_err", C.c_void_p)]
 
 
+class GenerationTrace(C.Structure):
+    _fields_ = [("err_parents", C.c_void_p), ("err_new", C.c_void_p), ("replaced", C.c_void_p),
+                ("parents", C.c_void_p), ("areas", C.c_int64 * 3), ("best", C.c_int32),
+                ("gen_stats", C.c_double * 9)]
+
+
 class Bounds(C.Structure):
     _fields_ = [("eta", C.c_float), ("max_missing", C.c_float), ("max_saturated", C.c_float)]
 
@@ -66,6 +72,8 @@ _SIGS = {
     "spring_abi_version": (_i, []),
     "spring_check_wait_timeout": (_i, [C.c_longlong]),
     "spring_status_string": (C.c_char_p, [_i]),
+    "spring_mpr_step": (_i, [_vp, C.POINTER(Params), C.POINTER(Population), C.POINTER(Population),
+                             C.POINTER(GenerationTrace)]),
     "spring_last_error": (C.c_char_p, []),
     "spring_params_default": (None, [C.POINTER(Params)]),
     "spring_init": (_i, [_i, C.c_size_t, C.POINTER(_vp)]),
@@ -625,6 +633,29 @@ class Problem:
         r, keep = _result_buffers(self.n if want_arrays else None, p.generations)
         _call("spring_mpr_resume", self.handle, C.byref(p), C.byref(pop), C.byref(r))
         return _result_dict(r, keep)
+
+    def step(self, p: Params, state):
+        """One generation from a population state (generation g - 1): returns the state after
+        generation g and what it decided (spring_mpr_step)."""
+        import numpy as np
+        P, n = p.pop, self.n
+        x = np.ascontiguousarray(state["pop_x"], np.complex64)
+        S = np.ascontiguousarray(state["pop_S"], np.uint8)
+        e = np.ascontiguousarray(state["pop_err"], np.float64)
+        src = Population(int(state["generation"]), x.ctypes.data, S.ctypes.data, e.ctypes.data)
+        out = {"pop_x": np.empty((P, n, n), np.complex64), "pop_S": np.empty((P, n, n), np.uint8),
+               "pop_err": np.empty(P, np.float64)}
+        dst = Population(0, out["pop_x"].ctypes.data, out["pop_S"].ctypes.data, out["pop_err"].ctypes.data)
+        tr = {"err_parents": np.full(P, np.nan), "err_new": np.full(P, np.nan),
+              "replaced": np.zeros(P, np.uint8), "parents": np.full((P, 3), -1, np.int32)}
+        t = GenerationTrace(tr["err_parents"].ctypes.data, tr["err_new"].ctypes.data,
+                            tr["replaced"].ctypes.data, tr["parents"].ctypes.data)
+        _call("spring_mpr_step", self.handle, C.byref(p), C.byref(src), C.byref(dst), C.byref(t))
+        out["generation"] = dst.generation
+        tr["areas"] = np.array(list(t.areas), np.int64)
+        tr["best"] = int(t.best)
+        tr["gen_stats"] = np.array(list(t.gen_stats))
+        return out, tr
 
     def submit(self, p: Params) -> int:
         t = self.ctx.submit(self, p)
