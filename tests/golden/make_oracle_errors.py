@@ -2,7 +2,7 @@
 the benchmark workloads (synthetic patterns from paper_2409_07413_gb300.synthetic).
 
 Calls only the oracle.  Run from the repository root:
-    python tests/golden/make_oracle_errors.py [--threads T]
+    python tests/golden/make_oracle_errors.py [--threads T] [--only PREFIX] [--missing] [--seeds]
 The 512 x 512 run (P = 64, 10 x 200 iterations) takes ~20 min on 8 cores, each reduced
 1024 x 1024 run ~12 min.
 """
@@ -33,10 +33,32 @@ WORKLOADS = {
 # the reduced 1024 x 1024 run and the 512 x 512 run at further run seeds (a single
 # trajectory of HIO/RAAR and the GA varies by several percent with the rounding, so the
 # comparison is over seeds)
-for _s in range(1001, 1008):
+for _s in range(1001, 1024):
     WORKLOADS[f"ell1024_g2_r{_s}"] = WORKLOADS["ell1024_g2"] + (_s,)
-for _s in range(1001, 1008):
+for _s in range(1001, 1040):
     WORKLOADS[f"ell512_r{_s}"] = WORKLOADS["ell512"] + (_s,)
+
+# The 64 x 64 workload over many run seeds (one pattern): its error of the average scatters
+# by about 19% of the mean from seed to seed, so a 2% comparison of means needs thousands of
+# runs a side.  Written to oracle_sphere64_seeds.json (--seeds).
+SEEDS_FILE = "oracle_sphere64_seeds.json"
+SEEDS_RANGE = (0, 2000)
+
+
+def write_seed_sweep():
+    recipe, pseed, prm = WORKLOADS["sphere64"]
+    pat = synthetic.config_pattern(recipe, pseed)
+    t0 = time.time()
+    avg, best = [], []
+    for s in range(*SEEDS_RANGE):
+        r = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=s, **prm)
+        avg.append(r["final_error_avg"])
+        best.append(r["final_error_best"])
+    out = {"workload": "sphere64", "pattern_seed": pseed, "params": prm, "run_seeds": list(SEEDS_RANGE),
+           "final_error_avg": avg, "final_error_best": best, "seconds": time.time() - t0,
+           "threads": oracle.get_threads()}
+    (Path(__file__).resolve().parent / SEEDS_FILE).write_text(json.dumps(out))
+    print("sphere64 seeds", len(avg), sum(avg) / len(avg), sum(best) / len(best), flush=True)
 
 
 def main():
@@ -44,9 +66,13 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--only", default=None, help="workloads whose name starts with this")
     ap.add_argument("--missing", action="store_true", help="only workloads not yet in the file")
+    ap.add_argument("--seeds", action="store_true", help="write the 64 x 64 seed sweep only")
     a = ap.parse_args()
     if a.threads:
         oracle.set_threads(a.threads)
+    if a.seeds:
+        write_seed_sweep()
+        return
     out_path = Path(__file__).resolve().parent / "oracle_errors.json"
     out = json.loads(out_path.read_text()) if out_path.exists() else {}
     for name, (recipe, pseed, prm, *rs) in WORKLOADS.items():
