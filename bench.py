@@ -207,6 +207,89 @@ def run_reference(args, wl):
     print(json.dumps(out), flush=True)
 
 
+def production_legs(spring, ctx, args):
+    """The three production forms of the path, each a short leg (reported beside the headline,
+    not part of it):
+      precision (1024 x 1024 two-panel pattern, P = 128, 20 x 300): one reconstruction with
+        FP32 storage and one with FP16 storage; and the same pattern and schedule at P = 32,
+        2 generations, at the run seeds whose FP64-oracle results are stored, in both
+        storages, against the oracle's mean;
+      batched uneven (patterns of sides drawn from {128, 192, 256, 512}, P = 32, 5 x 200):
+        same-side batches (spring_mpr_run_batch), served (all submitted at once) and plain
+        (one after another);
+      serving stream (Poisson arrivals at 200/s, sides {128, 256, 512, 1024} weighted
+        0.4/0.3/0.2/0.1, P = 32, 5 x 200): served (spring_submit / spring_poll) against plain
+        (one at a time in arrival order), with latency percentiles."""
+    import torch
+
+    from paper_2409_07413_gb300 import batchbench, servebench, synthetic
+    out = {}
+    # ---- precision
+    t_leg = time.perf_counter()
+    pat = synthetic.config_pattern("ell1024", 0)
+    prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
+    prm4 = dict(pop=128, iters_per_gen=300, generations=20, algorithm=2, beta=0.9, sw_sigma=1.5,
+                sw_threshold=0.2, sw_period=20, er_tail=10)
+    px4 = pixels_per_reconstruction(1024, prm4)
+    runs = {}
+    for prec in (0, 1):
+        prob.run(spring.params(**dict(prm4, generations=1), seed=1, precision=prec), want_arrays=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = prob.run(spring.params(**prm4, seed=1000, precision=prec), want_arrays=False)
+        dt = time.perf_counter() - t0
+        runs["fp16_storage" if prec else "fp32"] = {
+            "seconds": dt, "reconstructions_per_s": 1.0 / dt, "iteration_pixels_per_s": px4 / dt,
+            "final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"]}
+    golden = json.loads(GOLDEN_ORACLE.read_text()) if GOLDEN_ORACLE.exists() else {}
+    orc = {g["run_seed"]: g for k, g in golden.items() if k == "ell1024_g2" or k.startswith("ell1024_g2_r")}
+    red = dict(prm4, pop=32, generations=2)
+    cmp = {"params": red, "run_seeds": sorted(orc)}
+    if orc:
+        cmp["oracle_fp64"] = {k: float(np.mean([orc[sd][k] for sd in orc])) for k in ("final_error_avg", "final_error_best")}
+        for prec in (0, 1):
+            ea, eb = [], []
+            for sd in sorted(orc):
+                r = prob.run(spring.params(**red, seed=sd, precision=prec), want_arrays=False)
+                ea.append(r["final_error_avg"])
+                eb.append(r["final_error_best"])
+            m = {"final_error_avg": float(np.mean(ea)), "final_error_best": float(np.mean(eb))}
+            m["vs_oracle_rel"] = {k: (m[k] - cmp["oracle_fp64"][k]) / cmp["oracle_fp64"][k] for k in m}
+            cmp["fp16_storage" if prec else "fp32"] = m
+    prob.destroy()
+    out["precision_1024"] = {"workload": "ell1024: 1024x1024, P=128, G=20 x 300 RAAR", "runs": runs,
+                             "reduced_vs_oracle": cmp, "leg_seconds": time.perf_counter() - t_leg}
+    # ---- batched uneven workload (a subset of the 256 patterns)
+    t_leg = time.perf_counter()
+    prm3 = dict(pop=32, iters_per_gen=200, generations=5, algorithm=2, beta=0.9, sw_sigma=1.5,
+                sw_threshold=0.2, sw_period=20, er_tail=10)
+    jobs = batchbench.make_set(0, args.batch_patterns)
+    for n in batchbench.SIDES:
+        spring.autotune(n, 2 * prm3["pop"])
+    b = batchbench.run_set(ctx, spring, jobs, prm3, ("batched", "served", "plain"))
+    b["leg_seconds"] = time.perf_counter() - t_leg
+    b["batched_over_plain"] = b["batched"]["reconstructions_per_s"] / b["plain"]["reconstructions_per_s"]
+    b["served_over_plain"] = b["served"]["reconstructions_per_s"] / b["plain"]["reconstructions_per_s"]
+    out["batched_uneven"] = b
+    # ---- serving stream
+    t_leg = time.perf_counter()
+    reqs = servebench.make_stream(0, 200.0, args.serve_seconds)
+    for n in servebench.SIDES:
+        spring.autotune(n, 2 * servebench.PARAMS["pop"])
+    sv = {"rate_hz": 200.0, "arrivals_s": args.serve_seconds, "requests": len(reqs),
+          "sizes": {str(n): int(sum(1 for r in reqs if r[1] == n)) for n in servebench.SIDES},
+          "params": servebench.PARAMS}
+    for mode, fn in (("served", servebench.run_served), ("plain", servebench.run_plain)):
+        lat, svc, errs, sizes, span = fn(ctx, spring, reqs)
+        sv[mode] = {"reconstructions_per_s": len(lat) / span, "makespan_s": span,
+                    "latency": servebench.percentiles(lat), "service": servebench.percentiles(svc),
+                    "mean_final_error_best": float(np.mean(errs))}
+    sv["served_over_plain"] = sv["served"]["reconstructions_per_s"] / sv["plain"]["reconstructions_per_s"]
+    sv["leg_seconds"] = time.perf_counter() - t_leg
+    out["serving_stream"] = sv
+    return out
+
+
 def run_ours(args, wl):
     import torch
 
@@ -353,6 +436,8 @@ def run_ours(args, wl):
             "graph_capture": graph_out,
             "clocks": clk,
         }
+        if ws == 1 and not args.no_production:
+            out["production"] = production_legs(spring, ctx, args)
         print(json.dumps(out), flush=True)
     prob.destroy()
     ctx.close()
@@ -372,6 +457,12 @@ def main():
                     help="capture each run as one CUDA graph (per-kernel roofline timing is then "
                          "unavailable: launches inside a capture carry no events)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-production", action="store_true",
+                    help="skip the precision, batched-uneven and serving legs (reported beside the headline)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="arrival window of the serving leg at 200 requests/s")
+    ap.add_argument("--batch-patterns", type=int, default=64,
+                    help="patterns in the batched-uneven leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -243,19 +243,27 @@ spring_status spring_mpr_step(spring_problem* prob, const spring_params* p, cons
                               spring_population* to, spring_generation_trace* trace);
 
 /* Serving: queue a run; requests are admitted in arrival order while their footprint fits
- * the HBM budget and fewer than SPRING_MAX_ACTIVE (environment, default 2) are running;
- * running requests advance concurrently on the device, one generation per scheduler turn,
- * on streams whose priority is higher for smaller requests (continuous batching).
- * *ticket identifies the request.  The problem must stay alive until the ticket is polled
- * or cancelled. */
+ * the HBM budget.  An admitted request takes along the queued requests of the same side and
+ * the same parameters (seeds aside; FP32 storage, mode 0) into a cohort: one set of launches
+ * over all their populations, as spring_mpr_run_batch, up to SPRING_MAX_COHORT requests
+ * (environment, default 32) and 2^26 pixels per launch.  Up to SPRING_MAX_ACTIVE cohorts
+ * (environment, default 4) advance concurrently on the device, one generation per scheduler
+ * turn, on streams whose priority is higher for smaller requests (continuous batching).  A
+ * request's result is the same bit for bit alone or in a cohort.  *ticket identifies the
+ * request.  The problem must stay alive until the ticket is polled or cancelled. */
 spring_status spring_submit(spring_ctx* ctx, spring_problem* prob, const spring_params* p,
                             uint64_t* ticket);
 /* Wait up to timeout_us (0 = do not wait, < 0 = wait forever) for a ticket.  SPRING_OK
  * fills *out (buffers as for spring_mpr_run) and retires the ticket; BUSY = not done yet;
  * NOT_FOUND = unknown or already retired; CANCELLED; or the run's own error. */
 spring_status spring_poll(spring_ctx* ctx, uint64_t ticket, int timeout_us, spring_result* out);
-/* Cancel a queued or running ticket (it stops at its next generation boundary). */
+/* Cancel a queued or running ticket.  A queued ticket is dropped at once; a running one stops
+ * at its cohort's next generation boundary when every member of the cohort is cancelled, and
+ * otherwise when the cohort completes (its result is discarded). */
 spring_status spring_cancel(spring_ctx* ctx, uint64_t ticket);
+/* Serving statistics of a context since spring_init: cohorts formed and requests admitted
+ * (their ratio is the mean cohort size).  Either pointer may be NULL. */
+spring_status spring_serving_stats(spring_ctx* ctx, uint64_t* cohorts, uint64_t* admitted);
 
 /* ---------------------------------------------------------------- operators
  * The steps of the hot path on caller device buffers.  The run above is composed of

@@ -47,6 +47,51 @@ def make_set(seed, count, variants=4, sides_from=SIDES):
     return out
 
 
+def run_set(ctx, spring, jobs, prm, modes=("served", "plain", "batched"), batch_pixels=2.0 ** 26, graph=0):
+    """Reconstruct the set `jobs` ((side, pattern, seed) triples) once per mode; returns the
+    result dict (per mode: seconds, reconstructions/s, iteration-pixels/s, mean error)."""
+    import torch
+    sides = sorted({n for n, _, _ in jobs})
+    work_px = sum(2 * prm["pop"] * prm["iters_per_gen"] * prm["generations"] * n * n for n, _, _ in jobs)
+    out = {"benchmark": "batched uneven", "patterns": len(jobs), "graph": graph,
+           "sides": {str(n): int(sum(1 for j in jobs if j[0] == n)) for n in sides}, "params": prm,
+           "iteration_pixels": work_px}
+    per_mode = {}
+    for mode in modes:
+        probs = [ctx.problem(p.intensities, p.mask, p.support0) for _, p, _ in jobs]
+        torch.cuda.synchronize()
+        errs = [None] * len(jobs)
+        t0 = time.perf_counter()
+        if mode == "batched":
+            for n in sides:
+                idx = [i for i, j in enumerate(jobs) if j[0] == n]
+                K = max(1, int(batch_pixels // (2 * prm["pop"] * n * n)))
+                for c in range(0, len(idx), K):
+                    part = idx[c:c + K]
+                    rs = ctx.run_batch([probs[i] for i in part], spring.params(**prm, use_graph=graph),
+                                       [jobs[i][2] for i in part], want_arrays=False)
+                    for i, r in zip(part, rs):
+                        errs[i] = r["final_error_best"]
+        elif mode == "served":
+            tickets = [pr.submit(spring.params(**prm, seed=sd)) for pr, (_, _, sd) in zip(probs, jobs)]
+            for i, t in enumerate(tickets):
+                st, r = ctx.poll(t, -1, want_arrays=False)
+                errs[i] = r["final_error_best"]
+        else:
+            for i, (pr, (_, _, sd)) in enumerate(zip(probs, jobs)):
+                errs[i] = pr.run(spring.params(**prm, seed=sd, use_graph=graph),
+                                 want_arrays=False)["final_error_best"]
+        span = time.perf_counter() - t0
+        for pr in probs:
+            pr.destroy()
+        per_mode[mode] = errs
+        out[mode] = {"seconds": span, "reconstructions_per_s": len(jobs) / span,
+                     "iteration_pixels_per_s": work_px / span, "mean_final_error_best": float(np.mean(errs))}
+    ms = list(per_mode)
+    out["errors_identical_across_modes"] = all(per_mode[m] == per_mode[ms[0]] for m in ms)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--patterns", type=int, default=256)
@@ -66,43 +111,7 @@ def main():
     ctx = spring.Context(0)
     for n in sides:  # tune each side once, outside the timed region
         spring.autotune(n, 2 * prm["pop"])
-    work_px = sum(2 * prm["pop"] * prm["iters_per_gen"] * prm["generations"] * n * n for n, _, _ in jobs)
-    out = {"benchmark": "batched uneven", "patterns": len(jobs), "graph": a.graph,
-           "sides": {str(n): int(sum(1 for j in jobs if j[0] == n)) for n in sides}, "params": prm,
-           "iteration_pixels": work_px}
-    per_mode = {}
-    for mode in a.modes.split(","):
-        probs = [ctx.problem(p.intensities, p.mask, p.support0) for _, p, _ in jobs]
-        torch.cuda.synchronize()
-        errs = [None] * len(jobs)
-        t0 = time.perf_counter()
-        if mode == "batched":
-            for n in sides:
-                idx = [i for i, j in enumerate(jobs) if j[0] == n]
-                K = max(1, int(a.batch_pixels // (2 * prm["pop"] * n * n)))
-                for c in range(0, len(idx), K):
-                    part = idx[c:c + K]
-                    rs = ctx.run_batch([probs[i] for i in part], spring.params(**prm, use_graph=a.graph),
-                                       [jobs[i][2] for i in part], want_arrays=False)
-                    for i, r in zip(part, rs):
-                        errs[i] = r["final_error_best"]
-        elif mode == "served":
-            tickets = [pr.submit(spring.params(**prm, seed=sd)) for pr, (_, _, sd) in zip(probs, jobs)]
-            for i, t in enumerate(tickets):
-                st, r = ctx.poll(t, -1, want_arrays=False)
-                errs[i] = r["final_error_best"]
-        else:
-            for i, (pr, (_, _, sd)) in enumerate(zip(probs, jobs)):
-                errs[i] = pr.run(spring.params(**prm, seed=sd, use_graph=a.graph),
-                                 want_arrays=False)["final_error_best"]
-        span = time.perf_counter() - t0
-        for pr in probs:
-            pr.destroy()
-        per_mode[mode] = errs
-        out[mode] = {"seconds": span, "reconstructions_per_s": len(jobs) / span,
-                     "iteration_pixels_per_s": work_px / span, "mean_final_error_best": float(np.mean(errs))}
-    modes = list(per_mode)
-    out["errors_identical_across_modes"] = all(per_mode[m] == per_mode[modes[0]] for m in modes)
+    out = run_set(ctx, spring, jobs, prm, a.modes.split(","), a.batch_pixels, a.graph)
     ctx.close()
     print(json.dumps(out), flush=True)
 

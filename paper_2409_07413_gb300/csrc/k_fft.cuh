@@ -32,7 +32,8 @@
 //           6 / 7 = transposed tiles, one lane group per column (16 / 32 columns; 8 at
 //           N >= 1024 / 512); 8 / 9 = two adjacent columns per thread (16-byte accesses
 //           throughout), 16 / 32-column tiles, plans of at most 8 elements per thread
-//           (16 at N = 1024)
+//           (16 at N = 1024); 10 = default plan, 4-column tiles (32-byte row segments,
+//           the smallest blocks: most blocks per SM)
 #pragma once
 
 #include <cuda_fp16.h>
@@ -52,7 +53,7 @@ enum { OP_ROW_ITER = 0, OP_ROW_FWD, OP_ROW_INV, OP_COL_PM, OP_COL_FWD, OP_COL_IN
 
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_VARIANTS = 7;
-constexpr int COL_VARIANTS = 10;
+constexpr int COL_VARIANTS = 11;
 constexpr int ERR_W = 16;  // column tile of the error pass (layout of its partial sums)
 
 // alternative column-pass plans
@@ -753,9 +754,11 @@ inline spring_status col_variant(const FftOp& op, cudaStream_t s, bool prep) {
     case 8:
       if constexpr (MODE == COL_PM) return col2_launch<Col2Plan<N>, 16>(op, s, prep);
       return col_launch<Plan<N>, 16, MODE>(op, s, prep);
-    default:
+    case 9:
       if constexpr (MODE == COL_PM) return col2_launch<Col2Plan<N>, fit_w2<N, 32>()>(op, s, prep);
       return col_launch<Plan<N>, 16, MODE>(op, s, prep);
+    default:  // 4-column tiles: the most independent blocks (barrier domains) per SM
+      return col_launch<Plan<N>, 4, MODE>(op, s, prep);
   }
 }
 

@@ -15,6 +15,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <nvtx3/nvToolsExt.h>
 #include <memory>
@@ -665,11 +666,8 @@ struct Ticket {
   spring_params prm{};
   TState state = T_QUEUED;
   bool cancel = false;
-  size_t footprint = 0;
-  std::unique_ptr<Run> run;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev = nullptr;
-  bool ev_pending = false;
+  size_t footprint = 0;       // of the request alone (the admission check at submission)
+  struct Cohort* cohort = nullptr;  // while admitted: the requests it advances with
   spring_status status = SPRING_OK;
   std::string message;
   // host staging of the results
@@ -680,13 +678,29 @@ struct Ticket {
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
 };
 
+// Requests that advance together: one Run over K problems of the same side and the same
+// parameters (seeds aside), whose launches cover all K populations (K = 1: one request).
+// Each member's result equals its run alone bit for bit (see spring_mpr_run_batch).
+struct Cohort {
+  std::unique_ptr<Run> run;
+  std::vector<Ticket*> members;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool ev_pending = false;
+  size_t footprint = 0;
+};
+
 }  // namespace
 
 struct spring_ctx {
   int device = 0;
   size_t budget = 0;
   size_t used = 0;
-  int max_active = 2;             // requests advancing concurrently (SPRING_MAX_ACTIVE)
+  int max_active = 4;             // cohorts advancing concurrently (SPRING_MAX_ACTIVE)
+  int max_cohort = 32;            // requests per cohort (SPRING_MAX_COHORT; 1 = no batching)
+  double cohort_pixels = 67108864.0;  // a cohort's pixels per launch at most (2P N^2 per member)
+  std::list<std::unique_ptr<Cohort>> cohorts;
+  uint64_t n_cohorts = 0, n_admitted = 0;  // statistics: cohorts formed, requests admitted
   int prio_lo = 0, prio_hi = 0;   // stream priority range of the device
   std::mutex mu;
   std::condition_variable cv;       // scheduler wake-ups
@@ -706,39 +720,93 @@ static bool reserve(spring_ctx* c, size_t bytes) {
   return true;
 }
 
-static void finish_ticket(spring_ctx* c, Ticket* t, TState st) {
+// a member leaves: its state, time and the reference to its problem (resources stay with
+// its cohort)
+static void finish_member(spring_ctx* c, Ticket* t, TState st) {
   t->state = st;
   t->t_done = now_s();
-  if (t->run) {
-    t->run->release();
-    t->run.reset();
-  }
-  if (t->stream) {
-    cudaStreamSynchronize(t->stream);
-    cudaStreamDestroy(t->stream);
-    t->stream = nullptr;
-  }
-  if (t->ev) {
-    cudaEventDestroy(t->ev);
-    t->ev = nullptr;
-  }
-  c->used -= t->footprint;
-  t->footprint = 0;
+  t->cohort = nullptr;
   t->prob->refs.fetch_sub(1);
+  c->done_cv.notify_all();
 }
 
-// scheduler: admit queued tickets while their footprint fits, then keep every running
-// ticket's stream fed with one generation at a time (continuous batching: requests
-// arriving while others run are admitted as memory frees up, and their kernels overlap
-// on the device through separate streams)
+static void release_cohort(spring_ctx* c, Cohort* k) {
+  if (k->run) {
+    k->run->release();
+    k->run.reset();
+  }
+  if (k->stream) {
+    cudaStreamSynchronize(k->stream);
+    cudaStreamDestroy(k->stream);
+    k->stream = nullptr;
+  }
+  if (k->ev) {
+    cudaEventDestroy(k->ev);
+    k->ev = nullptr;
+  }
+  c->used -= k->footprint;
+  k->footprint = 0;
+}
+
+// every member of k fails with status st (k's resources are released by the caller)
+static void fail_cohort(spring_ctx* c, Cohort* k, spring_status st, const std::string& msg) {
+  for (Ticket* t : k->members)
+    if (t->cohort == k) {
+      t->status = st;
+      t->message = msg;
+      finish_member(c, t, T_FAILED);
+    }
+}
+
+// requests that may share a cohort: same side, same parameters apart from the seed, and a
+// form that batched runs support (FP32 storage, MPR mode)
+static bool cohort_key_equal(const Ticket* a, const Ticket* b) {
+  if (a->prob->n != b->prob->n) return false;
+  spring_params pa = a->prm, pb = b->prm;
+  pa.seed = pb.seed = 0;
+  pa.use_graph = pb.use_graph = 0;
+  return std::memcmp(&pa, &pb, sizeof(pa)) == 0;
+}
+static bool batchable(const Ticket* t) { return t->prm.precision == 0 && t->prm.mode == 0; }
+
+// the cohort that starts with the queue's head: the head, then queued requests with the same
+// key in arrival order, while the batch stays within max_cohort and cohort_pixels and its
+// footprint fits the budget (reserved here).  Returns the members' queue positions, empty
+// if the head does not fit.
+static std::vector<size_t> form_cohort(spring_ctx* c, size_t* footprint) {
+  Ticket* head = c->tickets[c->queue.front()].get();
+  std::vector<size_t> pos{0};
+  if (batchable(head)) {
+    const double px = 2.0 * head->prm.pop * (double)head->prob->n * head->prob->n;
+    const size_t kmax = (size_t)std::max(1.0, std::min((double)c->max_cohort, c->cohort_pixels / px));
+    for (size_t i = 1; i < c->queue.size() && pos.size() < kmax; ++i) {
+      Ticket* u = c->tickets[c->queue[i]].get();
+      if (!u->cancel && cohort_key_equal(head, u)) pos.push_back(i);
+    }
+  }
+  while (!pos.empty()) {
+    const size_t fp = make_layout(head->prob->n, head->prm, (int)pos.size()).total;
+    if (reserve(c, fp)) {
+      *footprint = fp;
+      return pos;
+    }
+    pos.pop_back();
+  }
+  return pos;
+}
+
+// scheduler: admit queued requests in arrival order while their footprint fits, grouping
+// each admitted request with queued ones of the same side and parameters into a cohort
+// (one set of launches over all their populations); then keep every cohort's stream fed
+// with one generation at a time.  Requests arriving while others run are admitted as
+// memory frees up, and the cohorts' kernels overlap on the device through separate
+// streams (continuous batching).
 static void scheduler(spring_ctx* c) {
   cudaSetDevice(c->device);
   std::unique_lock<std::mutex> lk(c->mu);
   while (!c->stop) {
     bool progress = false;
     // admission in arrival order, while memory and the concurrency cap allow
-    int running = 0;
-    for (auto& kv : c->tickets) running += kv.second->state == T_RUNNING ? 1 : 0;
     while (!c->queue.empty()) {
       Ticket* t = c->tickets[c->queue.front()].get();
       if (t->cancel) {
@@ -750,86 +818,118 @@ static void scheduler(spring_ctx* c) {
         c->done_cv.notify_all();
         continue;
       }
-      if (running >= c->max_active || !reserve(c, t->footprint)) break;
-      c->queue.pop_front();
-      ++running;
-      t->t_admit = now_s();
-      t->state = T_RUNNING;
+      if ((int)c->cohorts.size() >= c->max_active) break;
+      size_t fp = 0;
+      std::vector<size_t> pos = form_cohort(c, &fp);
+      if (pos.empty()) break;
+      std::unique_ptr<Cohort> k(new Cohort());
+      k->footprint = fp;
+      for (size_t i : pos) k->members.push_back(c->tickets[c->queue[i]].get());
+      for (size_t j = pos.size(); j-- > 0;) c->queue.erase(c->queue.begin() + (long)pos[j]);
+      const double t_admit = now_s();
+      std::vector<const spring_problem*> probs;
+      std::vector<uint64_t> seeds;
+      for (Ticket* m : k->members) {
+        m->t_admit = t_admit;
+        m->state = T_RUNNING;
+        m->cohort = k.get();
+        probs.push_back(m->prob);
+        seeds.push_back(m->prm.seed);
+      }
+      ++c->n_cohorts;
+      c->n_admitted += k->members.size();
       // smaller requests get higher stream priority: short jobs do not queue behind long ones
-      const int prio = t->footprint < (64u << 20) ? c->prio_hi
-                       : t->footprint < (512u << 20) ? (c->prio_hi + c->prio_lo) / 2 : c->prio_lo;
-      cudaStreamCreateWithPriority(&t->stream, cudaStreamNonBlocking, prio);
-      cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming);
-      t->run.reset(new Run());
-      spring_status st = t->run->setup(t->prob, t->prm, t->stream);
+      const size_t each = t->footprint;
+      const int prio = each < (64u << 20) ? c->prio_hi
+                       : each < (512u << 20) ? (c->prio_hi + c->prio_lo) / 2 : c->prio_lo;
+      cudaStreamCreateWithPriority(&k->stream, cudaStreamNonBlocking, prio);
+      cudaEventCreateWithFlags(&k->ev, cudaEventDisableTiming);
+      k->run.reset(new Run());
+      spring_status st = k->run->setup_batch(probs.data(), (int)probs.size(), seeds.data(), t->prm, k->stream);
       if (st != SPRING_OK) {
-        t->status = st;
-        t->message = spring_last_error();
-        finish_ticket(c, t, T_FAILED);
-        c->done_cv.notify_all();
+        fail_cohort(c, k.get(), st, spring_last_error());
+        release_cohort(c, k.get());
+      } else {
+        c->cohorts.push_back(std::move(k));
       }
       progress = true;
     }
-    // feed running tickets
-    for (auto& kv : c->tickets) {
-      Ticket* t = kv.second.get();
-      if (t->state != T_RUNNING) continue;
-      if (t->ev_pending) {
-        cudaError_t q = cudaEventQuery(t->ev);
-        if (q == cudaErrorNotReady) continue;
-        t->ev_pending = false;
-        if (q != cudaSuccess) {
-          t->status = SPRING_E_CUDA;
-          t->message = cudaGetErrorString(q);
-          finish_ticket(c, t, T_FAILED);
-          c->done_cv.notify_all();
-          progress = true;
+    // feed running cohorts
+    for (auto it = c->cohorts.begin(); it != c->cohorts.end();) {
+      Cohort* k = it->get();
+      bool retire = false;
+      if (k->ev_pending) {
+        cudaError_t q = cudaEventQuery(k->ev);
+        if (q == cudaErrorNotReady) {
+          ++it;
           continue;
         }
-      }
-      if (t->cancel) {
-        finish_ticket(c, t, T_CANCELLED);
-        c->done_cv.notify_all();
-        progress = true;
-        continue;
-      }
-      bool done = false;
-      spring_status st = t->run->step(&done);
-      if (st != SPRING_OK) {
-        t->status = st;
-        t->message = spring_last_error();
-        finish_ticket(c, t, T_FAILED);
-        c->done_cv.notify_all();
-        progress = true;
-        continue;
-      }
-      if (done) {
-        const int n = t->run->n, G = t->run->G;
-        const size_t nn = (size_t)n * n;
-        t->rho_avg.resize(2 * nn);
-        t->rho_best.resize(2 * nn);
-        t->support_avg.resize(nn);
-        t->gen_stats.resize(SPRING_GEN_STATS_COLS * (size_t)G);
-        spring_result r{};
-        r.rho_avg = t->rho_avg.data();
-        r.rho_best = t->rho_best.data();
-        r.support_avg = t->support_avg.data();
-        r.gen_stats = t->gen_stats.data();
-        st = check_device_waits();  // a bounded device-side wait that gave up
-        if (st == SPRING_OK) st = t->run->collect(&r);
-        t->e_avg = r.final_error_avg;
-        t->e_best = r.final_error_best;
-        if (st != SPRING_OK) {
-          t->status = st;
-          t->message = spring_last_error();
+        k->ev_pending = false;
+        if (q != cudaSuccess) {
+          fail_cohort(c, k, SPRING_E_CUDA, cudaGetErrorString(q));
+          retire = true;
         }
-        finish_ticket(c, t, st == SPRING_OK ? T_DONE : T_FAILED);
-        c->done_cv.notify_all();
-      } else {
-        cudaEventRecord(t->ev, t->stream);
-        t->ev_pending = true;
+      }
+      if (!retire) {
+        bool all_cancelled = true;
+        for (Ticket* m : k->members) all_cancelled = all_cancelled && m->cancel;
+        if (all_cancelled) {
+          for (Ticket* m : k->members) finish_member(c, m, T_CANCELLED);
+          retire = true;
+        }
+      }
+      if (!retire) {
+        bool done = false;
+        spring_status st = k->run->step(&done);
+        if (st != SPRING_OK) {
+          fail_cohort(c, k, st, spring_last_error());
+          retire = true;
+        } else if (done) {
+          const int n = k->run->n, G = k->run->G, K = (int)k->members.size();
+          const size_t nn = (size_t)n * n;
+          std::vector<spring_result> rs(K);
+          for (int q = 0; q < K; ++q) {
+            Ticket* m = k->members[q];
+            m->rho_avg.resize(2 * nn);
+            m->rho_best.resize(2 * nn);
+            m->support_avg.resize(nn);
+            m->gen_stats.resize(SPRING_GEN_STATS_COLS * (size_t)G);
+            rs[q] = spring_result{};
+            rs[q].rho_avg = m->rho_avg.data();
+            rs[q].rho_best = m->rho_best.data();
+            rs[q].support_avg = m->support_avg.data();
+            rs[q].gen_stats = m->gen_stats.data();
+          }
+          st = check_device_waits();  // a bounded device-side wait that gave up
+          if (st == SPRING_OK) st = k->run->collect(rs.data());
+          const std::string msg = st == SPRING_OK ? std::string() : std::string(spring_last_error());
+          for (int q = 0; q < K; ++q) {
+            Ticket* m = k->members[q];
+            m->e_avg = rs[q].final_error_avg;
+            m->e_best = rs[q].final_error_best;
+            if (m->cancel) {
+              finish_member(c, m, T_CANCELLED);
+            } else if (st != SPRING_OK) {
+              m->status = st;
+              m->message = msg;
+              finish_member(c, m, T_FAILED);
+            } else {
+              finish_member(c, m, T_DONE);
+            }
+          }
+          retire = true;
+        } else {
+          cudaEventRecord(k->ev, k->stream);
+          k->ev_pending = true;
+        }
       }
       progress = true;
+      if (retire) {
+        release_cohort(c, k);
+        it = c->cohorts.erase(it);
+      } else {
+        ++it;
+      }
     }
     if (!progress) c->cv.wait_for(lk, std::chrono::microseconds(200));
   }
@@ -901,6 +1001,10 @@ spring_status spring_init(int device, size_t hbm_budget_bytes, spring_ctx** out)
   if (const char* e = std::getenv("SPRING_MAX_ACTIVE")) {
     const int v = std::atoi(e);
     if (v > 0) c->max_active = v;
+  }
+  if (const char* e = std::getenv("SPRING_MAX_COHORT")) {
+    const int v = std::atoi(e);
+    if (v > 0) c->max_cohort = v;
   }
   cudaDeviceGetStreamPriorityRange(&c->prio_lo, &c->prio_hi);
   c->worker = std::thread(scheduler, c);
@@ -1251,6 +1355,14 @@ spring_status spring_poll(spring_ctx* c, uint64_t ticket, int timeout_us, spring
   }
   c->tickets.erase(it);
   return st;
+}
+
+spring_status spring_serving_stats(spring_ctx* c, uint64_t* cohorts, uint64_t* admitted) {
+  if (!c) return invalid("null context");
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (cohorts) *cohorts = c->n_cohorts;
+  if (admitted) *admitted = c->n_admitted;
+  return SPRING_OK;
 }
 
 spring_status spring_cancel(spring_ctx* c, uint64_t ticket) {

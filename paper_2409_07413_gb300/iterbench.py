@@ -116,7 +116,7 @@ def sweep(n, batch, iters, alg):
     res = []
     try:
         for rv in range(7):
-            for cv in range(10):
+            for cv in range(11):
                 spring.set_kernel_variant(n, rv, cv)
                 r = run(n, batch, iters, alg)
                 r["variant"] = [rv, cv]
@@ -136,7 +136,13 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="time every launch variant")
     ap.add_argument("--fused", action="store_true", help="also time the on-chip kernel (N <= 256)")
     ap.add_argument("--cufft", action="store_true", help="also time the cuFFT reference (torch.fft)")
+    ap.add_argument("--variant", type=int, nargs=2, default=None, metavar=("ROW", "COL"),
+                    help="launch-shape variants of the two passes (default: the built-in defaults)")
     a = ap.parse_args()
+    if a.variant:
+        from paper_2409_07413_gb300 import spring
+        for n in a.n:
+            spring.set_kernel_variant(n, *a.variant)
     for n in a.n:
         b = a.batch if a.batch > 0 else max(1, (128 * 512 * 512) // (n * n))
         if a.sweep:

@@ -93,6 +93,7 @@ _SIGS = {
     "spring_mpr_resume": (_i, [_vp, C.POINTER(Params), C.POINTER(Population), C.POINTER(Result)]),
     "spring_poll": (_i, [_vp, _u64, _i, C.POINTER(Result)]),
     "spring_cancel": (_i, [_vp, _u64]),
+    "spring_serving_stats": (_i, [_vp, C.POINTER(_u64), C.POINTER(_u64)]),
     "spring_fft2": (_i, [_vp, _i, _i, _i, _vp]),
     "spring_project_modulus": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "spring_iterate": (_i, [_vp, _vp, _vp, _i, _i, _i, _f, _f, _i, _vp]),
@@ -525,6 +526,12 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def serving_stats(self):
+        """(cohorts formed, requests admitted) since the context was opened."""
+        k, r = C.c_uint64(), C.c_uint64()
+        _call("spring_serving_stats", self.handle, C.byref(k), C.byref(r))
+        return k.value, r.value
 
     def problem(self, intensities, mask, support0, saturated=None, bounds=None):
         """Host numpy arrays (detector-centred I and mask, real-space support); with

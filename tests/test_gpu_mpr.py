@@ -165,6 +165,29 @@ def test_serving_alone_equals_in_mix(sp, ctx):
     assert in_mix["t_submit_s"] <= in_mix["t_admit_s"] <= in_mix["t_done_s"]
 
 
+def test_serving_batches_same_side_requests(sp, monkeypatch):
+    # one cohort at a time: a first request runs while five requests of one side and one set
+    # of parameters (different patterns and seeds) queue behind it; they are then admitted
+    # together as one cohort, and each result equals the request's run alone bit for bit
+    monkeypatch.setenv("SPRING_MAX_ACTIVE", "1")
+    jobs = [("ell256", 9, dict(C1, pop=16, seed=90))] + \
+        [("ell128", q, dict(C1, pop=6, seed=100 + q)) for q in range(5)]
+    with sp.Context(0) as c:
+        res = _serve(c, sp, jobs)
+        cohorts, admitted = c.serving_stats()
+    assert admitted == 6 and cohorts <= 3, (cohorts, admitted)
+    monkeypatch.delenv("SPRING_MAX_ACTIVE")
+    with sp.Context(0) as c:
+        for (name, seed, prm), got in zip(jobs, res):
+            pat = synthetic.config_pattern(name, seed)
+            pr = c.problem(pat.intensities, pat.mask, pat.support0)
+            alone = pr.run(sp.params(**prm))
+            pr.destroy()
+            for k in ("rho_avg", "rho_best", "support_avg", "gen_stats"):
+                assert np.array_equal(alone[k], got[k], equal_nan=True), (name, seed, k)
+            assert alone["final_error_avg"] == got["final_error_avg"]
+
+
 def test_serving_admits_by_footprint(sp):
     p = sp.params(**C1, seed=1)
     fp = sp.footprint_bytes(64, p)

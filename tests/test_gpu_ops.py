@@ -381,7 +381,7 @@ def test_kernel_variants_parity(sp, n):
     out = {}
     try:
         for rv in range(7):
-            for cv in range(10):
+            for cv in range(11):
                 sp.set_kernel_variant(n, rv, cv)
                 xg = dev(c64(x))
                 sp.spring_iterate(xg, dev(S), dev(menc(M, mask)), 2, 0.9, 1.0, 1)
@@ -391,13 +391,13 @@ def test_kernel_variants_parity(sp, n):
     finally:
         sp.set_kernel_variant(n, *saved)
     # same plans give the same bits: row variants 0-4 share the default plan, 5-6 the
-    # alternative row plan; column variants 0 and 2-7 the default column plan; the paired
+    # alternative row plan; column variants 0, 2-7 and 10 the default column plan; the paired
     # variants 8-9 share their own plan, which has the default's radices at 64 and 512 and
     # the alternative's at 1024
     paired_like = {64: 0, 512: 0, 1024: 1}.get(n, 8)
     for rv in range(7):
         r0 = 0 if rv < 5 else 5
-        for cv in (0, 2, 3, 4, 5, 6, 7):
+        for cv in (0, 2, 3, 4, 5, 6, 7, 10):
             assert np.array_equal(out[(rv, cv)], out[(r0, 0)]), (rv, cv)
         assert np.array_equal(out[(rv, 1)], out[(r0, 1)]), rv
         for cv in (8, 9):
@@ -408,6 +408,6 @@ def test_autotune_picks_a_valid_variant(sp):
     saved = sp.get_kernel_variant(256)
     try:
         rv, cv = sp.autotune(256, 8)
-        assert 0 <= rv < 7 and 0 <= cv < 10
+        assert 0 <= rv < 7 and 0 <= cv < 11
     finally:
         sp.set_kernel_variant(256, *saved)
