@@ -32,8 +32,8 @@
 //           6 / 7 = transposed tiles, one lane group per column (16 / 32 columns; 8 at
 //           N >= 1024 / 512); 8 / 9 = two adjacent columns per thread (16-byte accesses
 //           throughout), 16 / 32-column tiles, plans of at most 8 elements per thread
-//           (16 at N = 1024); 10 = default plan, 4-column tiles (32-byte row segments,
-//           the smallest blocks: most blocks per SM)
+//           (16 at N = 1024); 10 = alternative plan, 512-thread blocks held to three per
+//           SM (40 registers, 48 warps per SM), where such a tile divides the side
 #pragma once
 
 #include <cuda_fp16.h>
@@ -336,7 +336,8 @@ __device__ __forceinline__ void col_pass(const ColArgs& a, int tile) {
   const BlockSync sync;
   // PM / ERR: the strip's modulus values (N x W floats) arrive in shared memory by
   // cp.async while the tile is read and transformed, so no global latency is exposed
-  // between the forward and the inverse transform
+  // between the forward and the inverse transform.  The transform's exchange area holds
+  // the W columns interleaved (element i of column c at i W + c)
   float* Ms = reinterpret_cast<float*>(smem + (size_t)N * W);
   if constexpr (MODE == COL_PM || MODE == COL_ERR) {
     constexpr int CH = W / 4;  // 16-byte chunks per row
@@ -414,8 +415,8 @@ __device__ __forceinline__ void col_pass(const ColArgs& a, int tile) {
   }
 }
 
-template <class P, int W, int MODE, class ST = float2>
-__global__ void __launch_bounds__(W * P::T, (W * P::T <= 512 ? 2 : 1)) k_col(ColArgs a) {
+template <class P, int W, int MODE, class ST = float2, int MINB = (W * P::T <= 512 ? 2 : 1)>
+__global__ void __launch_bounds__(W * P::T, MINB) k_col(ColArgs a) {
   col_pass<P, W, MODE, ST>(a, blockIdx.x);
 }
 
@@ -647,14 +648,28 @@ inline spring_status row_launch(const FftOp& op, cudaStream_t s, bool prepare_on
   return SPRING_OK;
 }
 
+// shared memory of a column tile of W columns with its modulus strip
+template <class P>
+__host__ __device__ constexpr size_t col_tile_bytes(int w) {
+  return (size_t)P::N * w * (sizeof(float2) + sizeof(float));
+}
+
+// columns per tile for a block of `threads` threads on plan P, if that tile is usable (whole
+// 16-byte chunks of the modulus strip, whole tiles per image, within shared memory); else 0
+template <class P>
+constexpr int col_w_for(int threads) {
+  const int w = threads / P::T;
+  return (w >= 4 && w % 4 == 0 && P::N % w == 0 && col_tile_bytes<P>(w) <= 216 * 1024) ? w : 0;
+}
+
 template <int N, int W>
 constexpr int fit_w() {  // keep the column tile and its modulus strip within shared memory and 1024 threads
-  return ((size_t)N * W * 12 > 216 * 1024 || W * Plan<N>::T > 1024) ? W / 2 : W;
+  return (col_tile_bytes<Plan<N>>(W) > 216 * 1024 || W * Plan<N>::T > 1024) ? W / 2 : W;
 }
 
 template <int N>
 constexpr int fit_w_pair() {  // 16-column tiles while two blocks (tile + modulus strip) fit an SM
-  return (size_t)N * 16 * 12 > 100 * 1024 ? 8 : 16;
+  return col_tile_bytes<AltPlan<N>>(16) > 108 * 1024 ? 8 : 16;
 }
 
 template <int N>
@@ -664,12 +679,12 @@ constexpr int tma_w() {  // the TMA pass holds two tiles and two modulus strips
 
 template <int N, int W>
 constexpr int fit_w2() {  // paired tile: shared memory and at most 1024 threads
-  return ((size_t)N * W * 12 > 216 * 1024 || (W / 2) * Col2Plan<N>::T > 1024) ? W / 2 : W;
+  return (col_tile_bytes<Col2Plan<N>>(W) > 216 * 1024 || (W / 2) * Col2Plan<N>::T > 1024) ? W / 2 : W;
 }
 
 template <class P, int W>
 inline spring_status col2_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
-  const size_t smem = (size_t)P::N * W * (sizeof(float2) + sizeof(float));
+  const size_t smem = col_tile_bytes<P>(W);
   if (prepare_only) return allow_smem(k_col2<P, W>, smem);
   if (op.ca.batch < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
@@ -679,14 +694,15 @@ inline spring_status col2_launch(const FftOp& op, cudaStream_t s, bool prepare_o
   return SPRING_OK;
 }
 
-template <class P, int W, int MODE, class ST = float2>
+template <class P, int W, int MODE, class ST = float2, int MINB = (W * P::T <= 512 ? 2 : 1)>
 inline spring_status col_launch(const FftOp& op, cudaStream_t s, bool prepare_only) {
   const size_t smem = (size_t)P::N * W * sizeof(float2) +
                       ((MODE == COL_PM || MODE == COL_ERR) ? (size_t)P::N * W * sizeof(float) : 0);
-  if (prepare_only) return allow_smem(k_col<P, W, MODE, ST>, smem);
+  auto kern = k_col<P, W, MODE, ST, MINB>;
+  if (prepare_only) return allow_smem(kern, smem);
   if (op.ca.batch < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
-  k_col<P, W, MODE, ST><<<op.ca.batch * (P::N / W), W * P::T, smem, s>>>(op.ca);
+  kern<<<op.ca.batch * (P::N / W), W * P::T, smem, s>>>(op.ca);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;
@@ -757,8 +773,12 @@ inline spring_status col_variant(const FftOp& op, cudaStream_t s, bool prep) {
     case 9:
       if constexpr (MODE == COL_PM) return col2_launch<Col2Plan<N>, fit_w2<N, 32>()>(op, s, prep);
       return col_launch<Plan<N>, 16, MODE>(op, s, prep);
-    default:  // 4-column tiles: the most independent blocks (barrier domains) per SM
-      return col_launch<Plan<N>, 4, MODE>(op, s, prep);
+    default:  // the alternative plan in 512-thread blocks held to 3 per SM (48 warps: 40 registers)
+      if constexpr (MODE == COL_PM) {
+        constexpr int W = col_w_for<AltPlan<N>>(512);
+        if constexpr (W > 0) return col_launch<AltPlan<N>, W, MODE, float2, 3>(op, s, prep);
+      }
+      return col_launch<Plan<N>, 16, MODE>(op, s, prep);
   }
 }
 
