@@ -215,8 +215,8 @@ def production_legs(spring, ctx, args):
         2 generations, at the run seeds whose FP64-oracle results are stored, in both
         storages, against the oracle's mean;
       batched uneven (patterns of sides drawn from {128, 192, 256, 512}, P = 32, 5 x 200):
-        same-side batches (spring_mpr_run_batch), served (all submitted at once) and plain
-        (one after another);
+        same-side batches (spring_mpr_run_batch), the whole set in one call (one group per
+        side, one CUDA graph), served (all submitted at once) and plain (one after another);
       serving stream (Poisson arrivals at 200/s, sides {128, 256, 512, 1024} weighted
         0.4/0.3/0.2/0.1, P = 32, 5 x 200): served (spring_submit / spring_poll) against plain
         (one at a time in arrival order), with latency percentiles."""
@@ -266,9 +266,10 @@ def production_legs(spring, ctx, args):
     jobs = batchbench.make_set(0, args.batch_patterns)
     for n in batchbench.SIDES:
         spring.autotune(n, 2 * prm3["pop"])
-    b = batchbench.run_set(ctx, spring, jobs, prm3, ("batched", "served", "plain"))
+    b = batchbench.run_set(ctx, spring, jobs, prm3, ("batched", "mixed", "served", "plain"))
     b["leg_seconds"] = time.perf_counter() - t_leg
     b["batched_over_plain"] = b["batched"]["reconstructions_per_s"] / b["plain"]["reconstructions_per_s"]
+    b["mixed_over_plain"] = b["mixed"]["reconstructions_per_s"] / b["plain"]["reconstructions_per_s"]
     b["served_over_plain"] = b["served"]["reconstructions_per_s"] / b["plain"]["reconstructions_per_s"]
     out["batched_uneven"] = b
     # ---- serving stream

@@ -185,15 +185,18 @@ size_t spring_footprint_bytes(int n, const spring_params* p);
  * Errors: INVALID (parameters), NOMEM (budget), CUDA, NUMERIC. */
 spring_status spring_mpr_run(spring_problem* prob, const spring_params* p, spring_result* out);
 
-/* K independent MPR reconstructions of K problems of the same side, run together so that
- * each iteration, shrink-wrap and error launch covers all K x 2P images (problem q's
- * moduli serve images q 2P .. q 2P + 2P - 1); the GA steps (Alg. crossover, Alg. select,
- * the average) run problem by problem.  probs[0..K) share one context; seeds[q] replaces
- * p->seed for problem q; out[q] receives problem q's result, equal bit for bit to
- * spring_mpr_run(probs[q]) with p->seed = seeds[q].  p->precision and p->mode must be 0
- * when K > 1.  Blocking; the footprint is K times a single run's.
- * Errors: INVALID (arguments, mixed sides or contexts), then as spring_mpr_run; NUMERIC
- * if any problem's error is non-finite. */
+/* K independent MPR reconstructions run together.  Problems of the same side share every
+ * iteration, shrink-wrap and error launch, which covers all their populations (problem q's
+ * moduli serve its own 2P images); the GA steps (Alg. crossover, Alg. select, the average)
+ * run problem by problem.  Problems of different sides form one such group per side, and
+ * the groups advance concurrently on their own streams — with p->use_graph, as parallel
+ * branches of one CUDA graph, so that a single graph launch runs the whole batch.
+ * probs[0..K) share one context; seeds[q] replaces p->seed for problem q; out[q] receives
+ * problem q's result, equal bit for bit to spring_mpr_run(probs[q]) with p->seed = seeds[q].
+ * p->precision and p->mode must be 0 when K > 1.  Blocking; the footprint is the sum of the
+ * groups' (about K times a single run's).
+ * Errors: INVALID (arguments, mixed contexts), then as spring_mpr_run; NUMERIC if any
+ * problem's error is non-finite. */
 spring_status spring_mpr_run_batch(spring_problem* const* probs, int K, const spring_params* p,
                                    const uint64_t* seeds, spring_result* out);
 

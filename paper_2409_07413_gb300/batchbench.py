@@ -12,7 +12,9 @@ G generations x 200 RAAR iterations.  Two ways to run the same set:
   plain:  spring_mpr_run one pattern after another;
   batched: the patterns grouped by side, each group run K at a time with
           spring_mpr_run_batch (one launch per iteration pass over K x 2P images; K such
-          that a launch covers about --batch-pixels pixels).
+          that a launch covers about --batch-pixels pixels);
+  mixed:  the whole set in one spring_mpr_run_batch call: one group per side sharing its
+          launches, the groups as parallel branches of one CUDA graph.
 
 --graph 1 captures each plain and batched run as one CUDA graph (instantiated and
 launched inside the timed region).
@@ -47,7 +49,7 @@ def make_set(seed, count, variants=4, sides_from=SIDES):
     return out
 
 
-def run_set(ctx, spring, jobs, prm, modes=("served", "plain", "batched"), batch_pixels=2.0 ** 26, graph=0):
+def run_set(ctx, spring, jobs, prm, modes=("served", "plain", "batched", "mixed"), batch_pixels=2.0 ** 26, graph=0):
     """Reconstruct the set `jobs` ((side, pattern, seed) triples) once per mode; returns the
     result dict (per mode: seconds, reconstructions/s, iteration-pixels/s, mean error)."""
     import torch
@@ -62,7 +64,12 @@ def run_set(ctx, spring, jobs, prm, modes=("served", "plain", "batched"), batch_
         torch.cuda.synchronize()
         errs = [None] * len(jobs)
         t0 = time.perf_counter()
-        if mode == "batched":
+        if mode == "mixed":  # the whole set in one call: one group per side, one CUDA graph
+            rs = ctx.run_batch(probs, spring.params(**prm, use_graph=1), [j[2] for j in jobs],
+                               want_arrays=False)
+            for i, r in enumerate(rs):
+                errs[i] = r["final_error_best"]
+        elif mode == "batched":
             for n in sides:
                 idx = [i for i, j in enumerate(jobs) if j[0] == n]
                 K = max(1, int(batch_pixels // (2 * prm["pop"] * n * n)))
@@ -97,7 +104,7 @@ def main():
     ap.add_argument("--patterns", type=int, default=256)
     ap.add_argument("--generations", type=int, default=5)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--modes", default="served,plain,batched")
+    ap.add_argument("--modes", default="served,plain,batched,mixed")
     ap.add_argument("--batch-pixels", type=float, default=2.0 ** 26)
     ap.add_argument("--sides", default=",".join(map(str, SIDES)))
     ap.add_argument("--graph", type=int, default=0, help="1: plain and batched runs captured as CUDA graphs")

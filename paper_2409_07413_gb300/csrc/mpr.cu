@@ -1250,17 +1250,164 @@ spring_status spring_mpr_run(spring_problem* pr, const spring_params* p, spring_
   return run_blocking(pr, p, nullptr, 0, nullptr, out);
 }
 
+// A blocking batch of problems of several sides: one batched Run per side (the side's
+// problems share every launch), the sides advancing concurrently on their own streams —
+// as parallel branches of one CUDA graph when p->use_graph — so one launch covers all of
+// them.  Results go to out[] in the callers' order.
+static spring_status run_blocking_mixed(spring_problem* const* probs, int K, const uint64_t* seeds,
+                                        const spring_params* p, spring_result* out) {
+  std::vector<int> sides;
+  std::vector<std::vector<int>> idx;
+  for (int q = 0; q < K; ++q) {
+    int gi = -1;
+    for (size_t g = 0; g < sides.size(); ++g)
+      if (sides[g] == probs[q]->n) gi = (int)g;
+    if (gi < 0) {
+      sides.push_back(probs[q]->n);
+      idx.emplace_back();
+      gi = (int)sides.size() - 1;
+    }
+    idx[gi].push_back(q);
+  }
+  const int NG = (int)sides.size();
+  for (int g = 0; g < NG; ++g) SPRING_TRY(validate_params(sides[g], *p));
+  spring_ctx* c = probs[0]->ctx;
+  SPRING_CUDA(cudaSetDevice(c->device));
+  size_t fp = 0;
+  for (int g = 0; g < NG; ++g) fp += make_layout(sides[g], *p, (int)idx[g].size()).total;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!reserve(c, fp)) {
+      set_error("batch footprint " + std::to_string(fp) + " B exceeds the context's HBM budget");
+      return SPRING_E_NOMEM;
+    }
+  }
+  spring_status st = SPRING_OK;
+  {
+    std::vector<std::unique_ptr<Run>> runs(NG);
+    std::vector<cudaStream_t> ss(NG, nullptr);
+    std::vector<cudaEvent_t> done(NG, nullptr);
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int g = 0; g < NG && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&ss[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[g], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "stream set-up", __FILE__, __LINE__);
+    for (int g = 0; g < NG && st == SPRING_OK; ++g) {
+      std::vector<const spring_problem*> pg;
+      std::vector<uint64_t> sg;
+      for (int q : idx[g]) {
+        pg.push_back(probs[q]);
+        sg.push_back(seeds[q]);
+      }
+      runs[g].reset(new Run());
+      st = runs[g]->setup_batch(pg.data(), (int)pg.size(), sg.data(), *p, ss[g]);
+    }
+    if (st == SPRING_OK) {
+      // the origin stream first waits for every side's set-up (the graph is launched on it);
+      // then every side's stream starts after a fork from the origin, and the origin waits
+      // for all of them at the end (join)
+      for (int g = 0; g < NG && e == cudaSuccess; ++g) {
+        e = cudaEventRecord(done[g], ss[g]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, done[g], 0);
+      }
+      if (e != cudaSuccess) st = cuda_fail(e, "stream join", __FILE__, __LINE__);
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      if (st == SPRING_OK && p->use_graph) {
+        e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+      }
+      if (st == SPRING_OK) {
+        e = cudaEventRecord(fork, origin);
+        for (int g = 0; g < NG && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(ss[g], fork, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "stream fork", __FILE__, __LINE__);
+      }
+      if (st != SPRING_OK) {
+      } else if (p->use_graph) {
+        for (int g = 0; g < NG && st == SPRING_OK; ++g) st = runs[g]->enqueue_all();
+      } else {  // one generation of every side in turn, so that the sides' work interleaves
+        std::vector<bool> fin(NG, false);
+        for (int left = NG; left > 0 && st == SPRING_OK;)
+          for (int g = 0; g < NG && st == SPRING_OK; ++g) {
+            if (fin[g]) continue;
+            bool d = false;
+            st = runs[g]->step(&d);
+            if (d) {
+              fin[g] = true;
+              --left;
+            }
+          }
+      }
+      for (int g = 0; g < NG && st == SPRING_OK; ++g) {
+        e = cudaEventRecord(done[g], ss[g]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, done[g], 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "stream join", __FILE__, __LINE__);
+      }
+      if (p->use_graph && graph == nullptr) {
+        e = cudaStreamEndCapture(origin, &graph);
+        if (st == SPRING_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        if (st == SPRING_OK) {
+          e = cudaGraphInstantiate(&exec, graph, 0);
+          if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        }
+        if (st == SPRING_OK) {
+          e = cudaGraphLaunch(exec, origin);
+          if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
+        }
+      }
+      if (st == SPRING_OK) {
+        e = cudaStreamSynchronize(origin);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch execution", __FILE__, __LINE__);
+      }
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    if (st == SPRING_OK) st = check_device_waits();
+    if (st == SPRING_OK) {
+      const double t = now_s();
+      for (int g = 0; g < NG && st == SPRING_OK; ++g) {
+        std::vector<spring_result> rs(idx[g].size());
+        for (size_t j = 0; j < idx[g].size(); ++j) rs[j] = out[idx[g][j]];
+        st = runs[g]->collect(rs.data());
+        for (size_t j = 0; j < idx[g].size(); ++j) {
+          out[idx[g][j]] = rs[j];
+          out[idx[g][j]].t_submit_s = out[idx[g][j]].t_admit_s = out[idx[g][j]].t_done_s = t;
+        }
+      }
+    }
+    for (int g = 0; g < NG; ++g) {
+      if (runs[g]) runs[g]->release();
+      if (ss[g]) {
+        cudaStreamSynchronize(ss[g]);
+        cudaStreamDestroy(ss[g]);
+      }
+      if (done[g]) cudaEventDestroy(done[g]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (origin) cudaStreamDestroy(origin);
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->used -= fp;
+  return st;
+}
+
 spring_status spring_mpr_run_batch(spring_problem* const* probs, int K, const spring_params* p,
                                    const uint64_t* seeds, spring_result* out) {
   if (!probs || !p || !seeds || !out) return invalid("null argument");
   if (K <= 0) return invalid("batch size must be positive");
+  bool mixed = false;
   for (int q = 0; q < K; ++q) {
     if (!probs[q]) return invalid("null problem in the batch");
-    if (probs[q]->n != probs[0]->n) return invalid("the problems of a batch must have the same side");
     if (probs[q]->ctx != probs[0]->ctx) return invalid("the problems of a batch must share a context");
+    mixed = mixed || probs[q]->n != probs[0]->n;
   }
   if (K > 1 && p->precision != 0) return invalid("batched runs keep FP32 storage (precision 0)");
   if (K > 1 && p->mode != 0) return invalid("batched runs are memetic (mode 0)");
+  if (mixed) return run_blocking_mixed(probs, K, seeds, p, out);
   return run_blocking_k(probs, K, seeds, p, nullptr, 0, nullptr, out);
 }
 

@@ -1,6 +1,7 @@
-"""Batched runs of several same-side patterns (one launch per iteration pass over all
-patterns' populations, the GA steps pattern by pattern): each pattern's result equals its
-own single run with the same seed bit for bit, in every iteration path and schedule."""
+"""Batched runs of several patterns (same-side patterns share one launch per iteration pass
+over all their populations, the GA steps pattern by pattern; patterns of different sides
+run as concurrent groups, in one CUDA graph when captured): each pattern's result equals
+its own single run with the same seed bit for bit, in every iteration path and schedule."""
 import numpy as np
 import pytest
 
@@ -81,12 +82,37 @@ def test_batch_of_one_is_a_run(sp, ctx):
     pr.destroy()
 
 
+@pytest.mark.parametrize("graph", [0, 1])
+def test_mixed_side_batch_equals_single_runs(sp, ctx, graph):
+    # problems of four sides in one call: one group per side sharing its launches, the groups
+    # concurrent on their own streams (with use_graph, parallel branches of one CUDA graph);
+    # every result is the problem's single run bit for bit, in the callers' order
+    names = ["ell128", "sphere64", "ell192", "ell128", "ell96", "sphere64"]
+    probs = []
+    for q, name in enumerate(names):
+        pat = synthetic.config_pattern(name, 30 + q)
+        probs.append(ctx.problem(pat.intensities, pat.mask, pat.support0))
+    seeds = [11, 12, 13, 14, 15, 16]
+    batch = ctx.run_batch(probs, sp.params(**BASE, use_graph=graph), seeds)
+    for q in range(len(names)):
+        same(batch[q], probs[q].run(sp.params(**BASE, seed=seeds[q])))
+    for pr in probs:
+        pr.destroy()
+
+
 def test_batch_invalid_arguments(sp, ctx):
     a = problems(ctx, "sphere64", 2)
     b = problems(ctx, "ell128", 1)
-    with pytest.raises(sp.SpringError) as e:
-        ctx.run_batch([a[0], b[0]], sp.params(**BASE), [1, 2])  # mixed sides
+    with pytest.raises(sp.SpringError) as e:  # mixed sides keep the batch's restrictions
+        ctx.run_batch([a[0], b[0]], sp.params(**BASE, precision=1), [1, 2])
     assert e.value.status == sp.E_INVALID
+    with sp.Context(0) as other:  # problems of another context
+        pat = synthetic.config_pattern("sphere64", 3)
+        c = other.problem(pat.intensities, pat.mask, pat.support0)
+        with pytest.raises(sp.SpringError) as e:
+            ctx.run_batch([a[0], c], sp.params(**BASE), [1, 2])
+        assert e.value.status == sp.E_INVALID
+        c.destroy()
     for bad in (dict(precision=1), dict(mode=1)):
         with pytest.raises(sp.SpringError) as e:
             ctx.run_batch(a, sp.params(**BASE, **bad), [1, 2])
