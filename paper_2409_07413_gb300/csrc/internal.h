@@ -8,7 +8,9 @@ namespace spring {
 
 // ---------------------------------------------------------------- k_fft.cu
 // iteration row pass: w (column-pass output) -> P_M x -> update -> x, rowFFT(x) -> w
-spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint8_t* S,
+// Sb: the supports packed to one bit per pixel (launch_pack_support)
+spring_status launch_pack_support(const uint8_t* S, uint32_t* Sb, long long npix, cudaStream_t s);
+spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint32_t* Sb,
                               long long batch, float beta, float chi, bool zout, cudaStream_t s);
 // iteration column pass: colFFT, masked modulus projection, colIFFT, in place on w.
 // m_group > 0: M holds one N x N array per m_group consecutive images (a batch of patterns)
@@ -37,7 +39,7 @@ spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, dou
 // scaled by the device scalar s16 (a power of two from launch_fp16_scale), w by s16 times a
 // power of two near 1/sqrt(N)
 spring_status launch_fp16_scale(int n, const float* M, float* s16, cudaStream_t s);
-spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint8_t* S, long long batch,
+spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint32_t* Sb, long long batch,
                                 float beta, float chi, const float* s16, cudaStream_t s);
 spring_status launch_col_pm16(int n, void* wh, const float* M, int batch, const float* s16, cudaStream_t s);
 spring_status launch_row_init16(int n, const float2* x, void* xh, void* wh, long long batch, const float* s16,

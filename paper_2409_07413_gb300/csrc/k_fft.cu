@@ -69,7 +69,7 @@ static int col_variant_of(int n) {
 }
 
 // ------------------------------------------------------------------ launchers
-spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint8_t* S, long long batch,
+spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint32_t* Sb, long long batch,
                               float beta, float chi, bool zout, cudaStream_t s) {
   if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
   if (side_index(n) < 0) return invalid("unsupported pattern side");
@@ -83,15 +83,14 @@ spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint8_
   op.ra.in = w;
   op.ra.out = w;
   op.ra.x = x;
-  op.ra.S = S;
+  op.ra.Sb = Sb;
   op.ra.tw = tb.tw + tw_offset(n);
   op.ra.nrows = batch * n;
   op.ra.beta = beta;
   op.ra.chi_on = chi < 1.0f;
   op.ra.cchi = (float)((chi == 0.5f) ? 0.0 : std::cos((double)chi * 3.14159265358979323846));
   op.ra.zout = zout ? 1 : 0;
-  // algorithmic bytes: w in, x_n in (not for ER), x_{n+1} out, w out, and the support at
-  // its information content of one bit per pixel (the kernel reads it as one byte)
+  // algorithmic bytes: w in, x_n in (not for ER), x_{n+1} out, w out, and the support bits
   op.bytes = (double)batch * n * n * (8.0 + (alg ? 8.0 : 0.0) + 8.0 + (zout ? 8.0 : 0.0) + 0.125);
   return dispatch(n, op, s);
 }
@@ -237,7 +236,7 @@ spring_status launch_fp16_scale(int n, const float* M, float* s16, cudaStream_t 
   return SPRING_OK;
 }
 
-spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint8_t* S, long long batch,
+spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint32_t* Sb, long long batch,
                                 float beta, float chi, const float* s16, cudaStream_t s) {
   if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
   DeviceTables tb;
@@ -249,7 +248,7 @@ spring_status launch_row_iter16(int n, int alg, void* wh, void* xh, const uint8_
   op.ra.in = static_cast<const float2*>(wh);
   op.ra.out = static_cast<float2*>(wh);
   op.ra.x = static_cast<float2*>(xh);
-  op.ra.S = S;
+  op.ra.Sb = Sb;
   op.ra.tw = tb.tw + tw_offset(n);
   op.ra.nrows = batch * n;
   op.ra.beta = beta;
@@ -290,6 +289,44 @@ spring_status launch_row_init16(int n, const float2* x, void* xh, void* wh, long
   op.ra.s16 = s16;
   op.bytes = (double)batch * n * n * 16.0;
   return dispatch(n, op, s);
+}
+
+// Supports to one bit per pixel: thread k packs pixels 32k .. 32k + 31 (two 16-byte loads)
+// into word k, pixel 32k + b at bit b.  npix is a multiple of 32 (every supported N^2 is).
+template <bool ALIGNED>
+__global__ void k_pack_support(const uint8_t* __restrict__ S, uint32_t* __restrict__ Sb, long long nwords) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nwords;
+       k += (long long)gridDim.x * blockDim.x) {
+    uint32_t wbits = 0u;
+    if constexpr (ALIGNED) {
+      const uint4 lo = *reinterpret_cast<const uint4*>(S + 32 * k);
+      const uint4 hi = *reinterpret_cast<const uint4*>(S + 32 * k + 16);
+      const uint32_t q[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) wbits |= (((q[i] >> (8 * b)) & 0xffu) != 0u ? 1u : 0u) << (4 * i + b);
+    } else {  // a support array that does not start on a 16-byte boundary
+#pragma unroll 4
+      for (int b = 0; b < 32; ++b) wbits |= (S[32 * k + b] != 0 ? 1u : 0u) << b;
+    }
+    Sb[k] = wbits;
+  }
+}
+
+spring_status launch_pack_support(const uint8_t* S, uint32_t* Sb, long long npix, cudaStream_t s) {
+  if (npix % 32) return invalid("support size must be a multiple of 32 pixels");
+  const long long nw = npix / 32;
+  if (nw < 1) return SPRING_OK;
+  const long long blocks = div_up(nw, 256) < 16LL * sm_count() ? div_up(nw, 256) : 16LL * sm_count();
+  launch_begin(SPRING_KC_OTHER, s);
+  if ((reinterpret_cast<uintptr_t>(S) & 15u) == 0)
+    k_pack_support<true><<<(int)blocks, 256, 0, s>>>(S, Sb, nw);
+  else
+    k_pack_support<false><<<(int)blocks, 256, 0, s>>>(S, Sb, nw);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)npix * 1.125);
+  return SPRING_OK;
 }
 
 __global__ void k_half_to_float(const __half2* __restrict__ xh, float2* __restrict__ x, long long total,
@@ -394,6 +431,9 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
   uint8_t* S = reinterpret_cast<uint8_t*>(M + nn);
   k_fill_state<<<div_up(total, 256), 256, 0, s>>>(x, S, M, total, nn);
   SPRING_CHECK_LAUNCH();
+  Scratch bits;
+  SPRING_TRY(bits.alloc(sizeof(uint32_t) * (size_t)(total / 32 + 1), s));
+  SPRING_TRY(launch_pack_support(S, bits.as<uint32_t>(), total, s));
   SPRING_CUDA(cudaMemcpyAsync(w, x, sizeof(float2) * total, cudaMemcpyDeviceToDevice, s));
   FftOp op;
   op.kind = OP_ROW_ITER;
@@ -401,7 +441,7 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
   op.ra.in = w;
   op.ra.out = w;
   op.ra.x = x;
-  op.ra.S = S;
+  op.ra.Sb = bits.as<uint32_t>();
   op.ra.tw = tb.tw + tw_offset(n);
   op.ra.nrows = (long long)batch * n;
   op.ra.beta = 0.9f;

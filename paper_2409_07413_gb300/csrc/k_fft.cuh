@@ -13,9 +13,9 @@
 //                                   w = colIFFT(Y / N)
 //
 // so the next row pass's inverse row transform completes F^-1 and yields P_M x_{n+1}.
-// Per iteration and pixel this moves 8 (w) + 8 (x_n) + 1 (S, one byte per pixel; its
-// information content is one bit) + 8 (x_{n+1}) + 8 (w) bytes in the row pass and 8 + 8 in
-// the column pass: 49 B (ER: 41 B, x_n unread); counting the support at 1/8 B, 48.125 B.
+// Per iteration and pixel this moves 8 (w) + 8 (x_n) + 1/8 (S, one bit per pixel, packed
+// before each block of iterations) + 8 (x_{n+1}) + 8 (w) bytes in the row pass and 8 + 8
+// in the column pass: 48.125 B (ER: 40.125 B, x_n unread).
 //
 // Launch-shape variants (bit-identical results within a plan):
 //   row:    0 = state loads before the inverse transform, 1 block/SM of registers;
@@ -129,7 +129,8 @@ struct RowArgs {
   const float2* in;   // ITER: w (column-pass output); FWD/INV: input rows
   float2* out;        // ITER: w (forward row FFT of x_{n+1}); FWD/INV: output rows
   float2* x;          // ITER: state x_n -> x_{n+1}
-  const uint8_t* S;   // ITER: support; FWD: optional multiplier (S x); else unused
+  const uint8_t* S;   // FWD: optional multiplier (S x); else unused
+  const uint32_t* Sb; // ITER: support, one bit per pixel (pixel i: bit i & 31 of word i >> 5)
   const float2* tw;
   long long nrows;
   float beta, cchi, scale;
@@ -202,9 +203,17 @@ __device__ __forceinline__ float2 update_pixel(int alg, float2 xo, float2 pm, bo
   return make_float2(beta * xo.x + c * pm.x, beta * xo.y + c * pm.y);
 }
 
-// row-pass staging area of one lane group: x row (N float2) and S row (N bytes)
+// row-pass staging area of one lane group: the x row (N float2) and the row's support
+// words (N / 32 words, rounded up to whole 16-byte units), so that every group's area
+// starts on a 16-byte boundary (the x row arrives by 16-byte cp.async)
 template <class P>
-__host__ __device__ constexpr int stage_elems() { return P::N + P::N / 8; }
+__host__ __device__ constexpr int stage_elems() { return P::N + 2 * ((P::N / 32 + 3) / 4); }
+
+// support bit of column j of a row from the word that holds it (packed by
+// launch_pack_support: rows of N pixels, N a multiple of 32, so column j of a row is bit
+// j & 31 of the row's word j >> 5); the words are loaded apart from the test, so that the
+// loads of a thread stay independent of one another
+__device__ __forceinline__ bool support_bit(uint32_t word, int j) { return (word & (1u << (j & 31))) != 0u; }
 
 // The row pass of the blocks blk, blk + nblk, ... (G rows each) of a launch of
 // ROW_THREADS threads per block (k_row runs it over its grid).
@@ -214,19 +223,23 @@ __device__ __forceinline__ void row_pass(const RowArgs& a, long long blk, long l
   extern __shared__ float2 smem[];
   const int grp = threadIdx.x / T, t = threadIdx.x % T;
   float2* sm = smem + grp * SME;
-  float2* xs = smem + G * SME + grp * stage_elems<P>();  // STAGE: x row, then S row
-  uint8_t* ss = reinterpret_cast<uint8_t*>(xs + N);
+  float2* xs = smem + G * SME + grp * stage_elems<P>();  // STAGE: x row, then the support words
+  uint32_t* sws = reinterpret_cast<uint32_t*>(xs + N);
+  static_assert(!STAGE || ((G * SME) % 2 == 0 && stage_elems<P>() % 2 == 0 && N % 2 == 0),
+                "staging rows on 16-byte boundaries (16-byte cp.async of x)");
+  static_assert(!STAGE || 2 * (stage_elems<P>() - N) >= N / 32, "room for the row's support words");
   const auto sync = GroupSync<T>::make();
   for (long long row = blk * G + grp; row < a.nrows; row += nblk * G) {
     const long long base = row * N + t;
     float2 v[E];
     if constexpr (MODE == ROW_ITER && STAGE) {
-      // x_n and S of this row stream into shared memory while the row is transformed
+      // x_n and the support words of this row stream into shared memory while the row is
+      // transformed
       const float2* xr = a.x + row * N;
-      const uint8_t* sr = a.S + row * N;
+      const uint32_t* sr = a.Sb + row * (N / 32);
       if (ALG != 0)
         for (int k = t; k < N / 2; k += T) cp_async16(xs + 2 * k, xr + 2 * k);
-      for (int k = t; k < N / 16; k += T) cp_async16(ss + 16 * k, sr + 16 * k);
+      for (int k = t; k < N / 32; k += T) cp_async4(sws + k, sr + k);
       cp_async_commit();
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = a.in[base + m * T];
@@ -236,7 +249,7 @@ __device__ __forceinline__ void row_pass(const RowArgs& a, long long blk, long l
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const float2 pm = v[m];
-        bool in_c = ss[t + m * T] != 0;
+        bool in_c = support_bit(sws[(t + m * T) >> 5], t + m * T);
         if (a.chi_on) in_c = in_c && (pm.x >= a.cchi * sqrtf(pm.x * pm.x + pm.y * pm.y));
         const float2 xn = update_pixel(ALG, ALG ? xs[t + m * T] : pm, pm, in_c, a.beta);
         v[m] = xn;
@@ -255,12 +268,13 @@ __device__ __forceinline__ void row_pass(const RowArgs& a, long long blk, long l
       constexpr bool H = std::is_same<ST, __half2>::value;
       const float sx = H ? __ldg(a.s16) : 1.0f, ws = H ? w16_scale(N) * sx : 1.0f;
       const float isx = 1.0f / sx, iws = 1.0f / ws;  // exact: powers of two
-      uint8_t s[E];
+      uint32_t s[E];  // the support word of each element
       float2 xo[E];
+      const uint32_t* srow = a.Sb + row * (N / 32);  // this row's support words
       if constexpr (!LATE) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-          s[m] = a.S[base + m * T];
+          s[m] = srow[(t + m * T) >> 5];
           if (ALG != 0) xo[m] = ld_st(xs_, base + m * T, isx);
         }
       }
@@ -270,14 +284,14 @@ __device__ __forceinline__ void row_pass(const RowArgs& a, long long blk, long l
       if constexpr (LATE) {
 #pragma unroll
         for (int m = 0; m < E; ++m) {
-          s[m] = a.S[base + m * T];
+          s[m] = srow[(t + m * T) >> 5];
           if (ALG != 0) xo[m] = ld_st(xs_, base + m * T, isx);
         }
       }
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const float2 pm = v[m];
-        bool in_c = s[m] != 0;
+        bool in_c = support_bit(s[m], t + m * T);
         if (a.chi_on) in_c = in_c && (pm.x >= a.cchi * sqrtf(pm.x * pm.x + pm.y * pm.y));
         const float2 xn = update_pixel(ALG, ALG ? xo[m] : pm, pm, in_c, a.beta);
         v[m] = xn;

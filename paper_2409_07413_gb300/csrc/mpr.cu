@@ -79,7 +79,7 @@ static spring_status validate_params(int n, const spring_params& p) {
 
 // ------------------------------------------------------------------ device layout of a run
 struct Layout {
-  size_t x, w, S, sm0, sm1, err, abc, ix, ir, info, best, ph, alpha, repl, dens, part_err,
+  size_t x, w, S, Sb, sm0, sm1, err, abc, ix, ir, info, best, ph, alpha, repl, dens, part_err,
       part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, mall, total;
 };
 
@@ -99,6 +99,7 @@ static Layout make_layout(int n, const spring_params& p, int K = 1) {
   L.x = take(sizeof(float2) * B * nn);
   L.w = take(sizeof(float2) * B * nn);
   L.S = take(B * nn);
+  L.Sb = take(B * nn / 8);  // the supports packed to one bit per pixel for the row pass
   L.sm0 = take(sizeof(float) * B * nn);
   L.sm1 = take(sizeof(float) * B * nn);
   L.err = take(sizeof(double) * B);
@@ -162,6 +163,7 @@ class Run {
 
   float2 *x = nullptr, *w = nullptr, *avg = nullptr;
   uint8_t *S = nullptr, *repl = nullptr, *Savg = nullptr;
+  uint32_t* Sb = nullptr;  // S packed to bits (before each block of iterations)
   float *sm0 = nullptr, *sm1 = nullptr;
   double *err = nullptr, *dens = nullptr, *part_err = nullptr, *part_norm = nullptr,
          *part_dens = nullptr, *stats = nullptr, *err_avg = nullptr;
@@ -230,6 +232,7 @@ class Run {
     x = reinterpret_cast<float2*>(mem + L.x);
     w = reinterpret_cast<float2*>(mem + L.w);
     S = reinterpret_cast<uint8_t*>(mem + L.S);
+    Sb = reinterpret_cast<uint32_t*>(mem + L.Sb);
     sm0 = reinterpret_cast<float*>(mem + L.sm0);
     sm1 = reinterpret_cast<float*>(mem + L.sm1);
     err = reinterpret_cast<double*>(mem + L.err);
@@ -351,6 +354,8 @@ class Run {
 
   spring_status iterations(int alg, int k) {
     if (k <= 0) return SPRING_OK;
+    if (fp16 || iteration_path(n) != 1)  // the row passes read the supports as bits
+      SPRING_TRY(launch_pack_support(S, Sb, (long long)NBT * nn(), s));
     if (fp16) {
       if (!z16_valid) {
         SPRING_TRY(launch_row_init16(n, x, xh(), wh(), NB, s16, s));
@@ -358,7 +363,7 @@ class Run {
       }
       for (int it = 0; it < k; ++it) {
         SPRING_TRY(launch_col_pm16(n, wh(), Mall, NB, s16, s));
-        SPRING_TRY(launch_row_iter16(n, alg, wh(), xh(), S, NB, prm.beta, prm.chi, s16, s));
+        SPRING_TRY(launch_row_iter16(n, alg, wh(), xh(), Sb, NB, prm.beta, prm.chi, s16, s));
       }
       x16_newer = true;
       return SPRING_OK;
@@ -374,7 +379,7 @@ class Run {
     }
     for (int it = 0; it < k; ++it) {
       SPRING_TRY(launch_col_pm(n, w, Mall, NBT, s, mgroup));
-      SPRING_TRY(launch_row_iter(n, alg, w, x, S, NBT, prm.beta, prm.chi, true, s));
+      SPRING_TRY(launch_row_iter(n, alg, w, x, Sb, NBT, prm.beta, prm.chi, true, s));
     }
     return SPRING_OK;
   }

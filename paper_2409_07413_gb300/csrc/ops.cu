@@ -359,12 +359,15 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
   if (!x || !S || !M) return invalid("null pointer");
   cudaStream_t s = ST(stream);
   Scratch w;
-  SPRING_TRY(w.alloc(sizeof(float2) * (size_t)batch * n * n, s));
+  const size_t wbytes = sizeof(float2) * (size_t)batch * n * n;
+  SPRING_TRY(w.alloc(wbytes + (size_t)batch * n * n / 8, s));
+  uint32_t* Sb = reinterpret_cast<uint32_t*>(static_cast<char*>(w.p) + wbytes);
+  SPRING_TRY(launch_pack_support(S, Sb, (long long)batch * n * n, s));
   float2* xs = static_cast<float2*>(x);
   SPRING_TRY(launch_row_fft(n, -1, xs, w.as<float2>(), nullptr, batch, 1.0f, s));
   for (int it = 0; it < n_iter; ++it) {
     SPRING_TRY(launch_col_pm(n, w.as<float2>(), M, batch, s));
-    SPRING_TRY(launch_row_iter(n, algorithm, w.as<float2>(), xs, S, batch, beta, chi,
+    SPRING_TRY(launch_row_iter(n, algorithm, w.as<float2>(), xs, Sb, batch, beta, chi,
                                it + 1 < n_iter, s));
   }
   return SPRING_OK;
@@ -408,16 +411,18 @@ spring_status spring_iterate_ex(void* x, const uint8_t* S, const float* M, int b
   cudaStream_t s = ST(stream);
   const long long total = (long long)batch * n * n;
   Scratch w;
-  SPRING_TRY(w.alloc(sizeof(float2) * total + 256, s));
+  SPRING_TRY(w.alloc(sizeof(float2) * total + 256 + total / 8, s));
   void* wh = w.p;
   void* xh = static_cast<char*>(w.p) + total * 4;
   float* s16 = reinterpret_cast<float*>(static_cast<char*>(w.p) + total * 8);
+  uint32_t* Sb = reinterpret_cast<uint32_t*>(static_cast<char*>(w.p) + total * 8 + 256);
+  SPRING_TRY(launch_pack_support(S, Sb, total, s));
   float2* xs = static_cast<float2*>(x);
   SPRING_TRY(launch_fp16_scale(n, M, s16, s));
   SPRING_TRY(launch_row_init16(n, xs, xh, wh, batch, s16, s));
   for (int it = 0; it < n_iter; ++it) {
     SPRING_TRY(launch_col_pm16(n, wh, M, batch, s16, s));
-    SPRING_TRY(launch_row_iter16(n, algorithm, wh, xh, S, batch, beta, chi, s16, s));
+    SPRING_TRY(launch_row_iter16(n, algorithm, wh, xh, Sb, batch, beta, chi, s16, s));
   }
   return launch_half_to_float(xh, xs, total, s16, s);
 }
