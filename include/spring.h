@@ -296,7 +296,9 @@ spring_status spring_project_modulus(const void* x, void* out, const float* M, i
  * C = {S = 1 and |arg m| <= chi pi} (App. "Real-space constraints"):
  *   ER: x' = m on C, 0 elsewhere;  HIO: x' = m on C, x - beta m elsewhere;
  *   RAAR: x' = m on C, beta x + (1 - 2 beta) m elsewhere.
- * S: batch supports.  Scratch: one batch x N x N complex64 work buffer. */
+ * S: batch supports.  x must be 16-byte aligned (the row passes stream it into shared memory
+ * in 16-byte copies; every device allocation is); INVALID otherwise.  Scratch: one
+ * batch x N x N complex64 work buffer and the supports packed to bits. */
 spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batch, int n,
                              int algorithm, float beta, float chi, int n_iter, void* stream);
 

@@ -49,7 +49,8 @@ static int g_row_var[N_SIDES] = {0, 6, 5, 6, 0, 6, 6, 6, 5};
 static int g_col_var[N_SIDES] = {0, 1, 2, 1, 0, 0, 0, 1, 1};
 static bool g_tuned[N_SIDES] = {};
 // iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
-// (N <= 256, k_cluster.cu); chosen by the autotuner, the two-pass path until then
+// (N <= 256, k_cluster.cu), 2 = the split passes (N = 512, 1024: the column transform's
+// first stage in the row pass); chosen by the autotuner, the two-pass path until then
 static int g_path[N_SIDES] = {};
 
 int iteration_path(int n) {
@@ -291,6 +292,85 @@ spring_status launch_row_init16(int n, const float2* x, void* xh, void* wh, long
   return dispatch(n, op, s);
 }
 
+// ------------------------------------------------------------------ split passes (N = 512, 1024)
+bool split_supported(int n) { return split_side(n); }
+
+// the modulus in the split column pass's chunked layout: row k2 L + k1 of Mp is row
+// Q k1 + k2 of M (K arrays of n x n)
+__global__ void k_split_modulus(const float* __restrict__ M, float* __restrict__ Mp, int n, long long total) {
+  const int L = n / SPLIT_Q;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long nn = (long long)n * n, q = i / nn, r = (i / n) % n, c = i % n;
+    const long long k2 = r / L, k1 = r % L;
+    Mp[i] = M[q * nn + (SPLIT_Q * k1 + k2) * n + c];
+  }
+}
+
+spring_status launch_split_modulus(int n, const float* M, float* Mp, int K, cudaStream_t s) {
+  if (!split_side(n)) return invalid("the split passes cover sides 512 and 1024");
+  const long long total = (long long)K * n * n;
+  const long long blocks = div_up(total, 256) < 16LL * sm_count() ? div_up(total, 256) : 16LL * sm_count();
+  launch_begin(SPRING_KC_OTHER, s);
+  k_split_modulus<<<(int)blocks, 256, 0, s>>>(M, Mp, n, total);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, (double)total * 8.0);
+  return SPRING_OK;
+}
+
+// the split row pass: fwd_only = the forward row transforms and first stage from x alone
+spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2* x, const uint32_t* Sb,
+                               long long batch, float beta, float chi, cudaStream_t s) {
+  if (!split_side(n)) return invalid("the split passes cover sides 512 and 1024");
+  if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  FftOp op;
+  op.kind = fwd_only ? OP_ROW_SPLIT_FWD : OP_ROW_SPLIT;
+  op.alg = alg;
+  op.kclass = fwd_only ? SPRING_KC_OTHER : SPRING_KC_ROW_ITER;
+  op.sa.w = w;
+  op.sa.x = x;
+  op.sa.Sb = Sb;
+  op.sa.tw = tb.tw + tw_offset(n);
+  op.sa.nsets = batch * (n / SPLIT_Q);
+  op.sa.beta = beta;
+  op.sa.chi_on = chi < 1.0f;
+  op.sa.cchi = (float)((chi == 0.5f) ? 0.0 : std::cos((double)chi * 3.14159265358979323846));
+  op.bytes = fwd_only ? (double)batch * n * n * 16.0
+                      : (double)batch * n * n * (8.0 + (alg ? 8.0 : 0.0) + 16.0 + 0.125);
+  return dispatch(n, op, s);
+}
+
+spring_status launch_col_split(int n, float2* w, const float* Mp, int batch, cudaStream_t s, int m_group) {
+  if (!split_side(n)) return invalid("the split passes cover sides 512 and 1024");
+  DeviceTables tb;
+  SPRING_TRY(device_tables(&tb));
+  FftOp op;
+  op.kind = OP_COL_SPLIT;
+  op.kclass = SPRING_KC_COL_PM;
+  op.ca.data = w;
+  op.ca.M = Mp;
+  op.ca.tw = tb.tw + tw_offset(n / SPLIT_Q);
+  op.ca.batch = batch;
+  op.ca.m_group = m_group;
+  const double nm = m_group > 0 ? (double)((batch + m_group - 1) / m_group) : 1.0;
+  op.bytes = (double)batch * n * n * 16.0 + nm * n * n * 4.0;
+  return dispatch(n, op, s);
+}
+
+// k iterations (column pass, then row pass) in the split form; w must hold the chunked
+// forward spectra of x (launch_row_split with fwd_only) on entry and holds them on exit
+spring_status iterate_split(int n, int alg, float2* w, float2* x, const uint32_t* Sb, const float* Mp,
+                            long long batch, int m_group, float beta, float chi, int k, cudaStream_t s) {
+  if (batch > INT32_MAX) return invalid("batch too large");
+  for (int it = 0; it < k; ++it) {
+    SPRING_TRY(launch_col_split(n, w, Mp, (int)batch, s, m_group));
+    SPRING_TRY(launch_row_split(n, alg, false, w, x, Sb, batch, beta, chi, s));
+  }
+  return SPRING_OK;
+}
+
 // Supports to one bit per pixel: thread k packs pixels 32k .. 32k + 31 (two 16-byte loads)
 // into word k, pixel 32k + b at bit b.  npix is a multiple of 32 (every supported N^2 is).
 template <bool ALIGNED>
@@ -354,10 +434,11 @@ spring_status launch_half_to_float(const void* xh, float2* x, long long total, c
 spring_status prepare_fft_kernels(int n) {
   if (side_index(n) < 0) return invalid("unsupported pattern side");
   FftOp op;
-  for (int kind = OP_ROW_ITER; kind <= OP_ROW_INIT16; ++kind) {
+  const int last_kind = split_side(n) ? OP_COL_SPLIT : OP_ROW_INIT16;
+  for (int kind = OP_ROW_ITER; kind <= last_kind; ++kind) {
     op.kind = kind;
     const int nv = kind == OP_ROW_ITER ? ROW_VARIANTS : kind == OP_COL_PM ? COL_VARIANTS : 1;
-    const bool algs = kind == OP_ROW_ITER || kind == OP_ROW_ITER16;
+    const bool algs = kind == OP_ROW_ITER || kind == OP_ROW_ITER16 || kind == OP_ROW_SPLIT;
     for (int v = 0; v < nv; ++v)
       for (int alg = 0; alg < (algs ? 3 : 1); ++alg) {
         op.variant = v;
@@ -511,6 +592,41 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
     SPRING_TRY(st);
     path = one < two ? 1 : 0;
   }
+  // the split passes (N = 512, 1024) against the two passes with the chosen variants over a
+  // block of 20 iterations
+  if (split_side(n)) {
+    constexpr int K = 20;
+    op.variant = best_r;
+    cop.variant = best_c;
+    Scratch mp;
+    SPRING_TRY(mp.alloc(sizeof(float) * nn, s));
+    SPRING_TRY(launch_split_modulus(n, M, mp.as<float>(), 1, s));
+    cudaEvent_t e0, e1, e2;
+    SPRING_CUDA(cudaEventCreate(&e0));
+    SPRING_CUDA(cudaEventCreate(&e1));
+    SPRING_CUDA(cudaEventCreate(&e2));
+    spring_status st = dispatch(n, cop, s);  // warm-up of both forms
+    if (st == SPRING_OK) st = dispatch(n, op, s);
+    if (st == SPRING_OK) st = launch_row_split(n, 2, true, w, x, nullptr, batch, 0.9f, 0.5f, s);
+    if (st == SPRING_OK) st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, 1, s);
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < K && st == SPRING_OK; ++k) {
+      st = dispatch(n, cop, s);
+      if (st == SPRING_OK) st = dispatch(n, op, s);
+    }
+    cudaEventRecord(e1, s);
+    if (st == SPRING_OK) st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, K, s);
+    cudaEventRecord(e2, s);
+    cudaEventSynchronize(e2);
+    float two = 0.f, split = 0.f;
+    cudaEventElapsedTime(&two, e0, e1);
+    cudaEventElapsedTime(&split, e1, e2);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    SPRING_TRY(st);
+    if (split < two) path = 2;
+  }
   std::lock_guard<std::mutex> lk(g_var_mu);
   g_row_var[si] = best_r;
   g_col_var[si] = best_c;
@@ -568,7 +684,8 @@ spring_status spring_autotune(int n, int batch, void* stream) {
 spring_status spring_set_iteration_path(int n, int path) {
   const int si = side_index(n);
   if (si < 0) return invalid("unsupported pattern side");
-  if (path != 0 && path != 1) return invalid("path must be 0 (two passes) or 1 (on chip)");
+  if (path < 0 || path > 2) return invalid("path must be 0 (two passes), 1 (on chip) or 2 (split passes)");
+  if (path == 2 && !split_side(n)) return invalid("the split passes cover sides 512 and 1024");
   if (path == 1) {
     bool ok = false;
     SPRING_TRY(cluster_supported(n, &ok));

@@ -49,7 +49,7 @@ namespace spring {
 enum { ROW_ITER = 0, ROW_FWD = 1, ROW_INV = 2, ROW_INIT16 = 3 };
 enum { COL_PM = 0, COL_FWD = 1, COL_INV = 2, COL_ERR = 3 };
 enum { OP_ROW_ITER = 0, OP_ROW_FWD, OP_ROW_INV, OP_COL_PM, OP_COL_FWD, OP_COL_INV, OP_COL_ERR,
-       OP_ROW_ITER16, OP_COL_PM16, OP_ROW_INIT16 };
+       OP_ROW_ITER16, OP_COL_PM16, OP_ROW_INIT16, OP_ROW_SPLIT, OP_ROW_SPLIT_FWD, OP_COL_SPLIT };
 
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_VARIANTS = 7;
@@ -156,12 +156,7 @@ __device__ __forceinline__ const float* m_of(const ColArgs& a, int img, int n) {
   return a.m_group > 0 ? a.M + (size_t)((a.img0 + img) / a.m_group) * n * n : a.M;
 }
 
-struct FftOp {
-  int kind = 0, alg = 0, variant = 0, kclass = SPRING_KC_OTHER;
-  double bytes = 0.0;
-  RowArgs ra{};
-  ColArgs ca{};
-};
+
 
 // synchronisation of the T threads that own one row transform: a lane group inside a
 // warp (T <= 32) or a named barrier over T / 32 whole warps (T = 64, 128)
@@ -434,6 +429,206 @@ __global__ void __launch_bounds__(W * P::T, MINB) k_col(ColArgs a) {
   col_pass<P, W, MODE, ST>(a, blockIdx.x);
 }
 
+// ------------------------------------------------------------------ split passes
+// The column transform of length N = Q L (Q = 8) by decimation in frequency over the rows,
+// n = n1 + L n2: its first radix-Q stage combines the Q rows n1, n1 + L, ..., n1 + (Q - 1) L,
+// y[n1][k2] = W_N^{n1 k2} sum_{n2} x[n1 + L n2] W_Q^{n2 k2}, and the L-point transform of
+// y[.][k2] over n1 gives the full transform at the rows Q k1 + k2.  So the row pass of an
+// iteration, which holds the Q rows of a set n1 anyway, also runs that first stage (and,
+// on its way in, the inverse one), and the column pass transforms L-row chunks: chunk k2
+// holds y[n1][k2] at rows k2 L + n1 (the chunked layout of w), and its modulus values
+// come from a copy of M permuted to the same layout (row k2 L + k1 of it holds row
+// Q k1 + k2 of M).  The arithmetic is the same unnormalised 2D transform pair as the two
+// passes', in another order of summation.  This moves a third of the column pass's
+// transform work into the row pass, whose time is set by HBM rather than by issue.
+constexpr int SPLIT_Q = 8;
+
+template <int N> struct SplitRowPlan : RowAltPlan<N> {};  // row transforms of a split row pass
+// blocks of a split row pass per SM the register budget is sized for (512: 2, 64 registers;
+// 1024's 16-element rows keep one block and their registers)
+template <int N> constexpr int split_row_minb() { return N <= 512 ? 2 : 1; }
+constexpr bool split_side(int n) { return n == 512 || n == 1024; }
+constexpr int SPLIT_COL_W = 32;  // columns per tile of the split column pass
+
+struct SplitArgs {
+  float2* w;           // chunked spectra of the batch (N x N per image)
+  float2* x;           // ITER: state x_n -> x_{n+1}; FWD: input
+  const uint32_t* Sb;  // ITER: support bits (pixel i: bit i & 31 of word i >> 5)
+  const float2* tw;    // e^{-2 pi i k / N}
+  long long nsets;     // batch x L sets of Q rows
+  float beta, cchi;
+  int chi_on;
+};
+
+struct FftOp {
+  int kind = 0, alg = 0, variant = 0, kclass = SPRING_KC_OTHER;
+  double bytes = 0.0;
+  RowArgs ra{};
+  ColArgs ca{};
+  SplitArgs sa{};
+};
+
+// shared-memory float2 elements of a split row pass block: the Q rows' exchange areas and,
+// staged, the next set's Q spectra rows, the set's Q x rows and its Q rows of support words
+template <class P, bool STAGE>
+__host__ __device__ constexpr size_t split_row_elems() {
+  return (size_t)SPLIT_Q * pad_elems_p<P>() + (STAGE ? (size_t)2 * SPLIT_Q * P::N + SPLIT_Q * P::N / 64 : 0);
+}
+
+// A block of Q T threads per set of Q rows n1 + L n2: lane group n2 transforms row
+// n1 + L n2.  MODE ROW_ITER: inverse first stage (chunked w -> rows), inverse row
+// transforms (P_M x_n), update, forward row transforms, forward first stage (-> chunked w).
+// MODE ROW_FWD: from x, forward row transforms and first stage only.  STAGE (ROW_ITER):
+// blocks are persistent and their loads asynchronous 16-byte copies into shared memory --
+// the next set's spectra rows are in flight while a set is transformed, and a set's x rows
+// and support words while its inverse row transforms run -- so no load waits in line with
+// the arithmetic.
+template <class P, int MODE, int ALG, bool STAGE>
+__global__ void __launch_bounds__(SPLIT_Q * P::T, split_row_minb<P::N>()) k_row_split(SplitArgs a) {
+  constexpr int N = P::N, E = P::E, T = P::T, Q = SPLIT_Q, L = N / Q, TH = Q * T, RS = pad_elems_p<P>();
+  constexpr int CPT = N / TH;  // columns per thread in the first stages
+  static_assert(N % TH == 0 && RS >= N, "a column per thread group, rows fit their exchange areas");
+  static_assert(!STAGE || MODE == ROW_ITER, "staging serves the iteration");
+  static_assert(!STAGE || ((Q * RS) % 2 == 0 && N % 128 == 0 && (Q * N / 2) % TH == 0),
+                "16-byte aligned staging areas, whole copies per thread");
+  extern __shared__ __align__(16) float2 smem[];
+  float2* R = smem;                 // Q rows of RS: the set's rows, and each row's exchange area
+  float2* Ws = smem + Q * RS;       // STAGE: spectra rows k2 L + n1 of the set, k2 = 0..Q-1
+  float2* Xs = Ws + Q * N;          // STAGE: the set's x rows, one per lane group
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(Xs + Q * N);  // STAGE: their support words
+  const int tid = threadIdx.x, grp = tid / T, t = tid % T;
+  const auto gsync = GroupSync<T>::make();
+  // STAGE: the Q spectra rows of set `set` into Ws (an empty group past the last set)
+  auto stage_w = [&](long long set) {
+    if (set < a.nsets) {
+      const float2* src = a.w + (set / L) * N * N + (set % L) * N;
+#pragma unroll
+      for (int i = 0; i < Q * N / 2 / TH; ++i) {
+        const int k = tid + i * TH, k2 = k / (N / 2), q = k % (N / 2);
+        cp_async16(Ws + k2 * N + 2 * q, src + (long long)k2 * L * N + 2 * q);
+      }
+    }
+    cp_async_commit();
+  };
+  if constexpr (STAGE) {
+    stage_w(blockIdx.x);
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  for (long long set = blockIdx.x; set < a.nsets; set += gridDim.x) {
+    const long long img = set / L;
+    const int n1 = (int)(set % L);
+    float2* wi = a.w + img * N * N;
+    float2* xi = a.x + img * N * N;
+    const long long xrow = (long long)(n1 + L * grp) * N;  // the row this lane group owns
+    float2 v[E];
+    if constexpr (MODE == ROW_ITER) {
+      const uint32_t* srow = a.Sb + (img * N * N + xrow) / 32;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {  // inverse first stage of column c
+        const int c = tid + j * TH;
+        float2 z[Q];
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) z[k2] = STAGE ? Ws[k2 * N + c] : wi[(long long)(k2 * L + n1) * N + c];
+#pragma unroll
+        for (int k2 = 1; k2 < Q; ++k2) z[k2] = cmul(z[k2], cconj(__ldg(&a.tw[n1 * k2])));
+        DFT<Q, +1>::run(z);
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) R[n2 * RS + c] = z[n2];
+      }
+      __syncthreads();
+      if constexpr (STAGE) {  // the group's own x row and support words, then the next set's spectra
+        if constexpr (ALG != 0) {
+#pragma unroll
+          for (int i = 0; i < N / 2 / T; ++i) cp_async16(Xs + grp * N + 2 * (t + i * T), xi + xrow + 2 * (t + i * T));
+        }
+        if (t < N / 128) cp_async16(Bs + grp * (N / 32) + 4 * t, srow + 4 * t);
+        cp_async_commit();
+        stage_w(set + gridDim.x);
+      }
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = R[grp * RS + t + m * T];
+      gsync();                                                    // before the exchange writes
+      fft_plan<P, +1, true, 1>(v, R + grp * RS, t, a.tw, gsync);  // m = P_M x_n
+      if constexpr (STAGE) {  // this set's group of copies (the next set's may still fly)
+        cp_async_wait_group<1>();
+        gsync();
+      }
+      uint32_t sw[E];
+      float2 xo[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        sw[m] = STAGE ? Bs[grp * (N / 32) + ((t + m * T) >> 5)] : srow[(t + m * T) >> 5];
+        if (ALG != 0) xo[m] = STAGE ? Xs[grp * N + t + m * T] : xi[xrow + t + m * T];
+      }
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const float2 pm = v[m];
+        bool in_c = support_bit(sw[m], t + m * T);
+        if (a.chi_on) in_c = in_c && (pm.x >= a.cchi * sqrtf(pm.x * pm.x + pm.y * pm.y));
+        const float2 xn = update_pixel(ALG, ALG ? xo[m] : pm, pm, in_c, a.beta);
+        v[m] = xn;
+        xi[xrow + t + m * T] = xn;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = xi[xrow + t + m * T];
+    }
+    fft_plan<P, -1, true, 1>(v, R + grp * RS, t, a.tw, gsync);  // ends with the group's barrier
+#pragma unroll
+    for (int m = 0; m < E; ++m) R[grp * RS + t + m * T] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {  // forward first stage of column c
+      const int c = tid + j * TH;
+      float2 y[Q];
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) y[n2] = R[n2 * RS + c];
+      DFT<Q, -1>::run(y);
+#pragma unroll
+      for (int k2 = 1; k2 < Q; ++k2) y[k2] = cmul(y[k2], __ldg(&a.tw[n1 * k2]));
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) wi[(long long)(k2 * L + n1) * N + c] = y[k2];
+    }
+    if constexpr (STAGE) cp_async_wait_all();  // the next set's spectra rows
+    __syncthreads();  // R (and Ws, Xs, Bs) are written again for the next set
+  }
+}
+
+// Split column pass: L-point transforms of the chunks (plan PL of side L), P_M against the
+// permuted modulus (a.M in the chunked layout; its unnormalised scale is the full N-point
+// transform's), inverse L-point transforms.  Tile = (image, chunk k2, strip of W columns).
+template <class PL, int N, int W>
+__global__ void __launch_bounds__(W * PL::T, 2) k_col_split(ColArgs a) {
+  constexpr int L = PL::N, E = PL::E, T = PL::T, Q = N / L, STRIPS = N / W, CH = W / 4;
+  static_assert(Q == SPLIT_Q && W % 4 == 0 && N % W == 0, "split column tile");
+  extern __shared__ float2 smem[];
+  float* Ms = reinterpret_cast<float*>(smem + (size_t)L * W);
+  const int c = threadIdx.x % W, t = threadIdx.x / W;
+  const int img = blockIdx.x / (Q * STRIPS), rem = blockIdx.x % (Q * STRIPS);
+  const int k2 = rem / STRIPS, strip = rem % STRIPS;
+  float2* base = a.data + (size_t)img * N * N + (size_t)k2 * L * N + strip * W + c;
+  const float* Mb = m_of(a, img, N) + (size_t)k2 * L * N + strip * W;
+  for (int k = threadIdx.x; k < L * CH; k += blockDim.x) {
+    const int row = k / CH, q = k % CH;
+    cp_async16(Ms + row * W + 4 * q, Mb + (size_t)row * N + 4 * q);
+  }
+  cp_async_commit();
+  const BlockSync sync;
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = base[(size_t)(t + m * T) * N];
+  fft_plan<PL, -1, false, W, false>(v, smem + c, t, a.tw, sync);
+  cp_async_wait_all();
+  sync();  // also ends the transform's shared-memory reads
+  constexpr float inv_n = 1.0f / N;
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = pm_value(v[m], Ms[(t + m * T) * W + c], inv_n);
+  fft_plan<PL, +1, false, W, false>(v, smem + c, t, a.tw, sync);  // no shared-memory use after it
+#pragma unroll
+  for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * N] = v[m];
+}
+
 // Column pass (COL_PM) with transposed tiles.  The block's W columns are read with
 // coalesced row segments and written transposed into shared memory (one region per
 // column, odd stride: conflict-free); each lane group of T threads then transforms one
@@ -651,6 +846,8 @@ inline spring_status row_launch(const FftOp& op, cudaStream_t s, bool prepare_on
   constexpr int G = ROW_THREADS / P::T;
   const size_t smem = (size_t)G * (pad_elems_p<P>() + (STAGE ? stage_elems<P>() : 0)) * sizeof(float2);
   if (prepare_only) return allow_smem(k_row<P, MODE, ALG, LATE, MINB, STAGE, ST>, smem);
+  if (STAGE && (reinterpret_cast<uintptr_t>(op.ra.x) & 15u))
+    return invalid("the staged row pass copies x in 16-byte pieces: x must be 16-byte aligned");
   long long blocks = (op.ra.nrows + G - 1) / G;
   const long long cap = 64LL * sm_count();
   if (blocks > cap) blocks = cap;
@@ -749,6 +946,45 @@ inline spring_status col_pm_tma_launch(const FftOp& op, cudaStream_t s, bool pre
   return SPRING_OK;
 }
 
+template <int N, int MODE, int ALG>
+inline spring_status row_split_launch(const FftOp& op, cudaStream_t s, bool prep) {
+  using P = SplitRowPlan<N>;
+  constexpr bool STAGE = MODE == ROW_ITER;
+  const size_t smem = split_row_elems<P, STAGE>() * sizeof(float2);
+  auto kern = k_row_split<P, MODE, ALG, STAGE>;
+  if (prep) return allow_smem(kern, smem);
+  const long long sets = op.sa.nsets;
+  if (sets < 1) return SPRING_OK;
+  if (STAGE && ((reinterpret_cast<uintptr_t>(op.sa.w) | reinterpret_cast<uintptr_t>(op.sa.x) |
+                 reinterpret_cast<uintptr_t>(op.sa.Sb)) & 15u))
+    return invalid("the split row pass stages from 16-byte aligned w, x and support bits");
+  int per_sm = 0;
+  SPRING_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPLIT_Q * P::T, smem));
+  if (per_sm < 1) return invalid("split row pass does not fit an SM");
+  const long long cap = (long long)per_sm * sm_count() * (STAGE ? 1 : 4);  // staged: persistent
+  const int blocks = (int)(sets < cap ? sets : cap);
+  launch_begin(op.kclass, s);
+  kern<<<blocks, SPLIT_Q * P::T, smem, s>>>(op.sa);
+  SPRING_CHECK_LAUNCH();
+  launch_end(op.kclass, s, op.bytes);
+  return SPRING_OK;
+}
+
+template <int N>
+inline spring_status col_split_launch(const FftOp& op, cudaStream_t s, bool prep) {
+  using PL = Plan<N / SPLIT_Q>;
+  constexpr int W = SPLIT_COL_W;
+  const size_t smem = (size_t)PL::N * W * (sizeof(float2) + sizeof(float));
+  auto kern = k_col_split<PL, N, W>;
+  if (prep) return allow_smem(kern, smem);
+  if (op.ca.batch < 1) return SPRING_OK;
+  launch_begin(op.kclass, s);
+  kern<<<op.ca.batch * SPLIT_Q * (N / W), W * PL::T, smem, s>>>(op.ca);
+  SPRING_CHECK_LAUNCH();
+  launch_end(op.kclass, s, op.bytes);
+  return SPRING_OK;
+}
+
 template <int N, int ALG>
 inline spring_status row_iter_variant(const FftOp& op, cudaStream_t s, bool prep) {
   switch (op.variant) {
@@ -817,6 +1053,17 @@ spring_status run_fft_op(const FftOp& op, cudaStream_t s, bool prep) {
       return row_launch<Row16Plan<N>, ROW_ITER, 2, true, 2, false, __half2>(op, s, prep);
     case OP_COL_PM16: return col_launch<Col16Plan<N>, (N >= 1024 ? 8 : 16), COL_PM, __half2>(op, s, prep);
     case OP_ROW_INIT16: return row_launch<Plan<N>, ROW_INIT16, 0, false, 1>(op, s, prep);
+    case OP_ROW_SPLIT:
+    case OP_ROW_SPLIT_FWD:
+    case OP_COL_SPLIT:
+      if constexpr (split_side(N)) {
+        if (op.kind == OP_COL_SPLIT) return col_split_launch<N>(op, s, prep);
+        if (op.kind == OP_ROW_SPLIT_FWD) return row_split_launch<N, ROW_FWD, 0>(op, s, prep);
+        if (op.alg == 0) return row_split_launch<N, ROW_ITER, 0>(op, s, prep);
+        if (op.alg == 1) return row_split_launch<N, ROW_ITER, 1>(op, s, prep);
+        return row_split_launch<N, ROW_ITER, 2>(op, s, prep);
+      }
+      return invalid("the split passes cover sides 512 and 1024");
   }
   return invalid("unknown transform operation");
 }

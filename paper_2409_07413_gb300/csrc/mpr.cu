@@ -80,7 +80,7 @@ static spring_status validate_params(int n, const spring_params& p) {
 // ------------------------------------------------------------------ device layout of a run
 struct Layout {
   size_t x, w, S, Sb, sm0, sm1, err, abc, ix, ir, info, best, ph, alpha, repl, dens, part_err,
-      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, mall, total;
+      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, mall, msplit, total;
 };
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -125,6 +125,7 @@ static Layout make_layout(int n, const spring_params& p, int K = 1) {
   L.init = take(init_scratch_bytes((int)P, p.init_n_spheres) + 128);
   L.mavg = take(p.ca > 0.f ? sizeof(float) * nn : 0);
   L.mall = take(K > 1 ? sizeof(float) * nn * K : 0);  // the K modulus arrays, gathered
+  L.msplit = take(split_supported(n) ? sizeof(float) * nn * K : 0);  // M in the split passes' layout
   L.total = o;
   return L;
 }
@@ -173,6 +174,7 @@ class Run {
   unsigned* imgmax = nullptr;
   int* status = nullptr;
   float* mavg = nullptr;  // crossover averaging: (M-dot + M-double-dot) / 2
+  float* Msplit = nullptr;  // the K modulus arrays in the split column pass's layout (N = 512, 1024)
   // spring_mpr_step's trace (single-pattern runs): the improved parents' errors before
   // Select, and the parent whose area is alpha_best (device buffers owned by the caller)
   double* tr_err = nullptr;
@@ -264,6 +266,10 @@ class Run {
       Mall = m;
     } else {
       Mall = probs[0]->M;
+    }
+    if (split_supported(n)) {
+      Msplit = reinterpret_cast<float*>(mem + L.msplit);
+      SPRING_TRY(launch_split_modulus(n, Mall, Msplit, K, s));
     }
     return SPRING_OK;
   }
@@ -372,6 +378,13 @@ class Run {
       SPRING_TRY(launch_cluster_iter(n, alg, x, S, Mall, NBT, prm.beta, prm.chi, k, s, mgroup));
       z_valid = false;
       return SPRING_OK;
+    }
+    if (iteration_path(n) == 2) {  // split passes: w holds the chunked spectra
+      if (!z_valid) {
+        SPRING_TRY(launch_row_split(n, 0, true, w, x, nullptr, NBT, prm.beta, prm.chi, s));
+        z_valid = true;
+      }
+      return iterate_split(n, alg, w, x, Sb, Msplit, NBT, mgroup, prm.beta, prm.chi, k, s);
     }
     if (!z_valid) {
       SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, NBT, 1.0f, s));

@@ -357,13 +357,21 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
   if (n_iter < 0) return invalid("negative iteration count");
   if (batch == 0 || n_iter == 0) return SPRING_OK;
   if (!x || !S || !M) return invalid("null pointer");
+  if (reinterpret_cast<uintptr_t>(x) & 15u) return invalid("x must be 16-byte aligned");
   cudaStream_t s = ST(stream);
   Scratch w;
-  const size_t wbytes = sizeof(float2) * (size_t)batch * n * n;
-  SPRING_TRY(w.alloc(wbytes + (size_t)batch * n * n / 8, s));
+  const size_t wbytes = sizeof(float2) * (size_t)batch * n * n, sbytes = ((size_t)batch * n * n / 8 + 255) & ~(size_t)255;
+  const bool split = iteration_path(n) == 2;
+  SPRING_TRY(w.alloc(wbytes + sbytes + (split ? sizeof(float) * (size_t)n * n : 0), s));
   uint32_t* Sb = reinterpret_cast<uint32_t*>(static_cast<char*>(w.p) + wbytes);
   SPRING_TRY(launch_pack_support(S, Sb, (long long)batch * n * n, s));
   float2* xs = static_cast<float2*>(x);
+  if (split) {  // the split passes (sides 512 and 1024)
+    float* Mp = reinterpret_cast<float*>(static_cast<char*>(w.p) + wbytes + sbytes);
+    SPRING_TRY(launch_split_modulus(n, M, Mp, 1, s));
+    SPRING_TRY(launch_row_split(n, algorithm, true, w.as<float2>(), xs, nullptr, batch, beta, chi, s));
+    return iterate_split(n, algorithm, w.as<float2>(), xs, Sb, Mp, batch, 0, beta, chi, n_iter, s);
+  }
   SPRING_TRY(launch_row_fft(n, -1, xs, w.as<float2>(), nullptr, batch, 1.0f, s));
   for (int it = 0; it < n_iter; ++it) {
     SPRING_TRY(launch_col_pm(n, w.as<float2>(), M, batch, s));

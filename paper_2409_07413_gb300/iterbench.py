@@ -138,11 +138,16 @@ def main():
     ap.add_argument("--cufft", action="store_true", help="also time the cuFFT reference (torch.fft)")
     ap.add_argument("--variant", type=int, nargs=2, default=None, metavar=("ROW", "COL"),
                     help="launch-shape variants of the two passes (default: the built-in defaults)")
+    ap.add_argument("--path", type=int, default=None,
+                    help="iteration path: 0 two passes, 1 on chip (N <= 256), 2 split passes (512, 1024)")
     a = ap.parse_args()
-    if a.variant:
+    if a.variant or a.path is not None:
         from paper_2409_07413_gb300 import spring
         for n in a.n:
-            spring.set_kernel_variant(n, *a.variant)
+            if a.variant:
+                spring.set_kernel_variant(n, *a.variant)
+            if a.path is not None:
+                spring.set_iteration_path(n, a.path)
     for n in a.n:
         b = a.batch if a.batch > 0 else max(1, (128 * 512 * 512) // (n * n))
         if a.sweep:

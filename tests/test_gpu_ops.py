@@ -413,3 +413,103 @@ def test_autotune_picks_a_valid_variant(sp):
         assert 0 <= rv < 7 and 0 <= cv < 11
     finally:
         sp.set_kernel_variant(256, *saved)
+
+
+# ----------------------------------------------------------------------------- split passes
+@pytest.fixture
+def split_path(sp):
+    """The split passes (column transform's first stage in the row pass) for sides 512 and
+    1024, restoring each side's iteration path afterwards."""
+    saved = {n: sp.get_iteration_path(n) for n in (512, 1024)}
+    for n in saved:
+        sp.set_iteration_path(n, 2)
+    yield
+    for n, p in saved.items():
+        sp.set_iteration_path(n, p)
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+@pytest.mark.parametrize("alg", [0, 1, 2])
+@pytest.mark.parametrize("chi", [0.5, 1.0])
+def test_split_iterate_one_step(sp, split_path, n, alg, chi):
+    B = 2
+    x, S = synthetic.population_state(20 * n + alg, B, n, support_frac=0.3)
+    x = c64(x).astype(np.complex128)
+    M, mask = synthetic.random_modulus(2 * n + alg, n, masked_frac=0.1)
+    Mo, mk = as_oracle_M(M, mask)
+    xg = dev(c64(x))
+    sp.spring_iterate(xg, dev(S), dev(menc(M, mask)), alg, 0.9, chi, 1)
+    got = host(xg)
+    ref, m, out_c, margin = _expected_one_iteration(x, S, Mo, mk, alg, 0.9, chi)
+    sure = margin > 1e-4
+    assert rel(got[sure], ref[sure]) < TOL
+    for i in zip(*np.nonzero(~sure)):
+        g = got[i]
+        assert min(abs(g - m[i]), abs(g - out_c[i])) <= 1e-4 * (abs(m[i]) + abs(out_c[i]) + 1e-30)
+    assert (~sure).mean() < 1e-3
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_split_iterate_many_steps(sp, split_path, n):
+    # several iterations drift from FP64 at the FP32 rate, as the two passes do
+    k = 8
+    x, S = synthetic.population_state(4, 2, n, support_frac=0.3)
+    M, mask = synthetic.random_modulus(4, n, masked_frac=0.1)
+    Mo, mk = as_oracle_M(M, mask)
+    xg = dev(c64(x))
+    sp.spring_iterate(xg, dev(S), dev(menc(M, mask)), 2, 0.9, 1.0, k)
+    ref = oracle.iterate(c64(x), S, Mo, mk, 2, 0.9, 1.0, k)
+    drift32 = rel(np.stack([_fp32_emulation(c64(x)[b], S[b], Mo, mk, 0.9, k) for b in range(2)]), ref)
+    assert rel(host(xg), ref) < max(TOL, 3.0 * drift32)
+
+
+@pytest.mark.parametrize("n,B", [(512, 12), (1024, 4)])
+@pytest.mark.parametrize("alg", [1, 2])
+def test_split_iterate_many_sets_per_block(sp, split_path, n, B, alg):
+    # batches of more sets (Q rows each) than the row pass has resident blocks: every block
+    # runs two or more sets, each set's rows staged while the one before is transformed
+    x, S = synthetic.population_state(30 * n + alg, B, n, support_frac=0.3)
+    x = c64(x).astype(np.complex128)
+    M, mask = synthetic.random_modulus(3 * n + alg, n, masked_frac=0.1)
+    Mo, mk = as_oracle_M(M, mask)
+    xg = dev(c64(x))
+    sp.spring_iterate(xg, dev(S), dev(menc(M, mask)), alg, 0.9, 0.5, 1)
+    got = host(xg)
+    ref, m, out_c, margin = _expected_one_iteration(x, S, Mo, mk, alg, 0.9, 0.5)
+    sure = margin > 1e-4
+    assert rel(got[sure], ref[sure]) < TOL
+    for b in range(B):  # every image of the batch, not the batch as a whole
+        assert rel(got[b][sure[b]], ref[b][sure[b]]) < TOL, b
+    assert (~sure).mean() < 1e-3
+
+
+def test_iterate_rejects_misaligned_x(sp):
+    # the row passes stream x in 16-byte copies: an 8-byte offset view is refused on the host
+    import torch
+    n = 512
+    buf = torch.zeros(2 * n * n + 1, dtype=torch.complex64, device="cuda")
+    x = buf[1:].view(2, n, n)
+    S = torch.ones(2, n, n, dtype=torch.uint8, device="cuda")
+    M = torch.ones(n, n, dtype=torch.float32, device="cuda")
+    with pytest.raises(sp.SpringError) as e:
+        sp.spring_iterate(x, S, M, 2, 0.9, 1.0, 1)
+    assert e.value.status == sp.E_INVALID
+
+
+def test_split_batched_runs_equal_single_runs(sp, split_path):
+    # the split column pass reads each pattern's own permuted moduli in a batch
+    ctx = sp.Context(0)
+    try:
+        pats = [synthetic.config_pattern("ell512", s) for s in (3, 4)]
+        probs = [ctx.problem(p.intensities, p.mask, p.support0) for p in pats]
+        kw = dict(pop=4, iters_per_gen=40, generations=2, er_tail=5)
+        batch = ctx.run_batch(probs, sp.params(**kw), [5, 6])
+        for q, pr in enumerate(probs):
+            single = pr.run(sp.params(**kw, seed=5 + q))
+            for k in ("rho_avg", "support_avg", "gen_stats"):
+                assert np.array_equal(batch[q][k], single[k], equal_nan=True), k
+            assert 0 < single["final_error_best"] < 1.5
+        for pr in probs:
+            pr.destroy()
+    finally:
+        ctx.close()
