@@ -1,12 +1,12 @@
 """End to end at the 64 x 64 workload (P = 8, 5 x 100 RAAR): the GPU's final errors against
-the FP64 oracle's over the same 2000 run seeds of one pattern, with the plain 2% bar on the
+the FP64 oracle's over the same 8000 run seeds of one pattern, with the plain 2% bar on the
 mean: |mean_gpu - mean_oracle| <= 0.02 mean_oracle, for the error of the average
 reconstruction and for the best individual, with no allowance for sampling.
 
 Single trajectories are not expected to agree (HIO/RAAR and the GA amplify FP32 rounding),
 so the comparison is between the two distributions over seeds.  The error of the average
-scatters by about 19% of its mean from seed to seed; over 2000 seeds the standard error of
-each mean is about 0.4%, so the 2% bar stands at several standard errors of the difference
+scatters by about 19% of its mean from seed to seed; over 8000 seeds the standard error of
+each mean is about 0.2%, so the 2% bar stands at several standard errors of the difference
 and a real bias of 2% would not hide in the sampling.  The oracle's values are stored in
 tests/golden/oracle_sphere64_seeds.json (written by tests/golden/make_oracle_errors.py
 --seeds, which calls only the oracle)."""
@@ -31,7 +31,7 @@ def sp():
     return spring
 
 
-def test_sphere64_2000_seeds_within_two_percent(sp):
+def test_sphere64_seeds_within_two_percent(sp):
     gold = json.loads(GOLDEN.read_text())
     s0, s1 = gold["run_seeds"]
     seeds = list(range(s0, s1))
