@@ -58,6 +58,68 @@ __device__ __forceinline__ cpair rot90(cpair x) {
   return {rot90<DIR>(x.a), rot90<DIR>(x.b)};
 }
 
+// Two complex values of two independent transforms packed by component: re = (real part of
+// the first, real part of the second), im likewise.  Both lanes always take the same
+// operation, so each step is one two-lane FP32 instruction (add / sub / mul / fma .f32x2 of
+// sm_100 and later) where two float2 values take two each, and a product with +-i only
+// renames the halves.  Each lane rounds exactly as the scalar operation does.
+struct __align__(16) cpk {
+  float2 re, im;
+};
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2dup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return f2mul(a, f2dup(-1.0f)); }
+
+__device__ __forceinline__ cpk cadd(cpk x, cpk y) { return {f2add(x.re, y.re), f2add(x.im, y.im)}; }
+__device__ __forceinline__ cpk csub(cpk x, cpk y) { return {f2sub(x.re, y.re), f2sub(x.im, y.im)}; }
+__device__ __forceinline__ cpk cscale(cpk x, float s) { return {f2mul(x.re, f2dup(s)), f2mul(x.im, f2dup(s))}; }
+template <int DIR>
+__device__ __forceinline__ cpk rot90(cpk x) {
+  return DIR < 0 ? cpk{x.im, f2neg(x.re)} : cpk{f2neg(x.im), x.re};
+}
+// x * w for a twiddle held as a pair with equal lanes (w.re = (c, c), w.im = (s, s))
+__device__ __forceinline__ cpk cmul_b(cpk x, cpk w) {
+  return {f2sub(f2mul(x.re, w.re), f2mul(x.im, w.im)), f2fma(x.re, w.im, f2mul(x.im, w.re))};
+}
+__device__ __forceinline__ cpk cmul(cpk x, float2 w) { return cmul_b(x, cpk{f2dup(w.x), f2dup(w.y)}); }
+__device__ __forceinline__ cpk pack_pair(cpair p) {
+  return {make_float2(p.a.x, p.b.x), make_float2(p.a.y, p.b.y)};
+}
+__device__ __forceinline__ cpair unpack_pair(cpk v) {
+  return {make_float2(v.re.x, v.im.x), make_float2(v.re.y, v.im.y)};
+}
+
+// a + (DIR i) d and a - (DIR i) d
+template <int DIR, class V>
+__device__ __forceinline__ V add_rot(V a, V d) {
+  return cadd(a, rot90<DIR>(d));
+}
+template <int DIR, class V>
+__device__ __forceinline__ V sub_rot(V a, V d) {
+  return csub(a, rot90<DIR>(d));
+}
+template <int DIR>
+__device__ __forceinline__ cpk add_rot(cpk a, cpk d) {
+  return DIR < 0 ? cpk{f2add(a.re, d.im), f2sub(a.im, d.re)} : cpk{f2sub(a.re, d.im), f2add(a.im, d.re)};
+}
+template <int DIR>
+__device__ __forceinline__ cpk sub_rot(cpk a, cpk d) {
+  return DIR < 0 ? cpk{f2sub(a.re, d.im), f2add(a.im, d.re)} : cpk{f2add(a.re, d.im), f2sub(a.im, d.re)};
+}
+
 // a * W_R^k with W_R = e^{DIR 2 pi i / R}, R | 32, constant-folded special cases.
 template <int R, int K, int DIR>
 __device__ __forceinline__ float2 twc(float2 a) {
@@ -85,11 +147,56 @@ __device__ __forceinline__ cpair twc(cpair x) {
   return {twc<R, K, DIR>(x.a), twc<R, K, DIR>(x.b)};
 }
 
+// butterfly of a radix-R combine: lo = e + W_R^K o, hi = e - W_R^K o
+template <int R, int K, int DIR, class V>
+__device__ __forceinline__ void bfly(V& lo, V& hi, V e, V o) {
+  const V t = twc<R, K, DIR>(o);
+  lo = cadd(e, t);
+  hi = csub(e, t);
+}
+// packed pairs: products with +-1 and +-i fold into the additions, and the (+-1 +-i) / sqrt 2
+// products into two fused multiply-adds per component
+template <int R, int K, int DIR>
+__device__ __forceinline__ void bfly(cpk& lo, cpk& hi, cpk e, cpk o) {
+  constexpr int k = (K * (32 / R)) & 31;
+  if constexpr (k == 0) {
+    lo = cadd(e, o);
+    hi = csub(e, o);
+  } else if constexpr (k == 8) {
+    lo = add_rot<DIR>(e, o);
+    hi = sub_rot<DIR>(e, o);
+  } else if constexpr (k == 16) {
+    lo = csub(e, o);
+    hi = cadd(e, o);
+  } else if constexpr (k == 24) {
+    lo = add_rot<-DIR>(e, o);
+    hi = sub_rot<-DIR>(e, o);
+  } else if constexpr (k == 4 || k == 12 || k == 20 || k == 28) {
+    // W o = h (c o.re - s o.im, c o.im + s o.re) with c, s = +-1: each component is one sum
+    // or difference u, times +-h
+    constexpr float h = 0.70710678118654752440f;
+    constexpr int c = cos32(k) > 0 ? 1 : -1, sn = (sin32(k) > 0 ? 1 : -1) * DIR;
+    const float2 u = c == sn ? (c > 0 ? f2sub(o.re, o.im) : f2sub(o.im, o.re)) : f2add(o.re, o.im);
+    const float2 w = c == sn ? f2add(o.im, o.re) : (c > 0 ? f2sub(o.im, o.re) : f2sub(o.re, o.im));
+    constexpr float hu = (c != sn && c < 0) ? -h : h, hw = (c == sn && c < 0) ? -h : h;
+    lo = {f2fma(u, f2dup(hu), e.re), f2fma(w, f2dup(hw), e.im)};
+    hi = {f2fma(u, f2dup(-hu), e.re), f2fma(w, f2dup(-hw), e.im)};
+  } else {
+    constexpr float c = (float)cos32(k), sn = (float)(DIR * sin32(k));
+    const cpk t = {f2fma(o.re, f2dup(c), f2mul(o.im, f2dup(-sn))), f2fma(o.im, f2dup(c), f2mul(o.re, f2dup(sn)))};
+    lo = cadd(e, t);
+    hi = csub(e, t);
+  }
+}
+
 // v0 - t / 2 (radix 3)
 __device__ __forceinline__ float2 sub_half(float2 v0, float2 t) {
   return make_float2(v0.x - 0.5f * t.x, v0.y - 0.5f * t.y);
 }
 __device__ __forceinline__ cpair sub_half(cpair v0, cpair t) { return {sub_half(v0.a, t.a), sub_half(v0.b, t.b)}; }
+__device__ __forceinline__ cpk sub_half(cpk v0, cpk t) {
+  return {f2fma(t.re, f2dup(-0.5f), v0.re), f2fma(t.im, f2dup(-0.5f), v0.im)};
+}
 
 // In-place radix-R DFT of v[0..R), natural order in and out.
 template <int R, int DIR>
@@ -109,9 +216,7 @@ struct DFT {
   template <int K, class V>
   __device__ __forceinline__ static void combine(V* v, const V* e, const V* o, std::integral_constant<int, K>) {
     if constexpr (K < R / 2) {
-      V t = twc<R, K, DIR>(o[K]);
-      v[K] = cadd(e[K], t);
-      v[K + R / 2] = csub(e[K], t);
+      bfly<R, K, DIR>(v[K], v[K + R / 2], e[K], o[K]);
       combine(v, e, o, std::integral_constant<int, K + 1>());
     }
   }
@@ -135,11 +240,11 @@ struct DFT<4, DIR> {
   template <class V>
   __device__ __forceinline__ static void run(V* v) {
     V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    V t2 = cadd(v[1], v[3]), t3 = rot90<DIR>(csub(v[1], v[3]));
+    V t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
     v[0] = cadd(t0, t2);
     v[2] = csub(t0, t2);
-    v[1] = cadd(t1, t3);
-    v[3] = csub(t1, t3);
+    v[1] = add_rot<DIR>(t1, d);
+    v[3] = sub_rot<DIR>(t1, d);
   }
 };
 template <int DIR>
@@ -204,13 +309,29 @@ template <> struct Plan<512>  : PlanT<512, 16, 8, 8, 8> {};
 template <> struct Plan<768>  : PlanT<768, 24, 8, 8, 4, 3> {};
 template <> struct Plan<1024> : PlanT<1024, 32, 32, 32> {};
 
+// The padded exchange layout that stage s writes: output o goes to slot o + (o / G) Pd
+// with G = xgroup(s), Pd = xpad(s).  A later stage pads span(s) per group of span(s + 1),
+// its butterflies' outputs.  A first stage of radix 2, 4 or 8 pads 1 per 16 outputs where
+// one transform spans 16 threads or more: with 1 per radix, two lanes of each half-warp of
+// the next stage's 8-byte loads (elements t + (N / R) r) share a bank pair, while the
+// stores (R t + r + (R t + r) / 16) stay apart as well.  Narrower transforms share a warp,
+// where the pitch between transforms decides, and keep 1 per radix.
+template <class P>
+__host__ __device__ constexpr int xgroup(int s) {
+  return (s == 0 && P::T >= 16 && (P::R0 == 2 || P::R0 == 4 || P::R0 == 8)) ? 16 : P::span(s + 1);
+}
+template <class P>
+__host__ __device__ constexpr int xpad(int s) {
+  return P::span(s);
+}
+
 // shared-memory elements of one transform's padded exchange buffer: the largest layout
 // of a stage whose outputs go through shared memory (every stage but the last)
 template <class P>
 __host__ __device__ constexpr int pad_elems_p() {
   int m = 0;
   for (int s = 0; P::radix(s + 1) != 0; ++s) {
-    const int e = P::N + P::N / P::radix(s);
+    const int e = P::N + (P::N / xgroup<P>(s)) * xpad<P>(s);
     m = e > m ? e : m;
   }
   return m;
@@ -257,6 +378,42 @@ __device__ __forceinline__ void stage_twiddle(V (&b)[E], int t, const float2* __
   }
 }
 
+// packed pairs: both lanes share the twiddles, so the powers are formed once, as pairs
+// with equal lanes, and each product with a pair of values is five two-lane instructions
+template <int N, int E, int R, int NS, int DIR>
+__device__ __forceinline__ void stage_twiddle(cpk (&b)[E], int t, const float2* __restrict__ tw) {
+  constexpr int T = N / E;
+  constexpr int STEP = N / (NS * R);
+#pragma unroll
+  for (int u = 0; u < E / R; ++u) {
+    const int j = t + u * T;
+    const int k1 = (j % NS) * STEP;
+    cpk pw[6];
+    int np = 0;
+    {
+      const float2 w1 = __ldg(&tw[k1 % N]);
+      cpk w = {f2dup(w1.x), f2dup(DIR < 0 ? w1.y : -w1.y)};
+#pragma unroll
+      for (int q = 1; q < R; q <<= 1) {
+        pw[np++] = w;
+        w = cmul_b(w, w);
+      }
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cpk w;
+      bool have = false;
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if ((r >> q) & 1) {
+          w = have ? cmul_b(w, pw[q]) : pw[q];
+          have = true;
+        }
+      b[u * R + r] = cmul_b(b[u * R + r], w);
+    }
+  }
+}
+
 // radix-3 stages (sides 3 x 2^k) use direct table loads
 template <int N, int E, int NS, int DIR, class V>
 __device__ __forceinline__ void stage_twiddle3(V (&b)[E], int t, const float2* __restrict__ tw) {
@@ -278,14 +435,19 @@ __device__ __forceinline__ int xlayout(int i) {
   return PAD ? i + (i / L) * PADN : i;
 }
 
-// write the outputs of a stage (radix R, NS) in the exchange layout
-template <int N, int E, int R, int NS, bool PAD, int STRIDE, class V>
+// write the outputs of a stage (radix R, NS) in the exchange layout (PAD: groups of G
+// outputs, PD slots of padding after each)
+template <int N, int E, int R, int NS, bool PAD, int STRIDE, int G, int PD, class V>
 __device__ __forceinline__ void stage_store(const V (&b)[E], V* sm, int t) {
   constexpr int T = N / E;
+  // the butterfly's R outputs (base + r NS) lie in one group: G = NS R, or NS = 1 with R
+  // dividing G
+  static_assert(!PAD || G == NS * R || (NS == 1 && G % R == 0), "exchange groups");
 #pragma unroll
   for (int u = 0; u < E / R; ++u) {
     const int j = t + u * T;
-    const int base = PAD ? (j / NS) * (NS * R + NS) + (j % NS) : (j / NS) * NS * R + (j % NS);
+    const int o = (j / NS) * NS * R + (j % NS);
+    const int base = PAD ? o + (o / G) * PD : o;
 #pragma unroll
     for (int r = 0; r < R; ++r) sm[(base + r * NS) * STRIDE] = b[u * R + r];
   }
@@ -325,15 +487,15 @@ __device__ __forceinline__ void stage_tw(V (&b)[E], int t, const float2* __restr
 // (with STRIDE between consecutive elements).  tw: table of e^{-2 pi i k / N}.
 // TAIL = false leaves out the barrier after the last shared-memory read: for callers that
 // synchronise themselves before the buffer is written again, or never write it again.
-// stages S >= 1 of plan P: inputs from the layout of stage S - 1 (groups of span(S),
-// padding span(S - 1)), twiddles, radix-R DFT; then the next stage through shared memory,
+// stages S >= 1 of plan P: inputs from the layout of stage S - 1 (groups of xgroup(S - 1),
+// padding xpad(S - 1)), twiddles, radix-R DFT; then the next stage through shared memory,
 // or, after the last stage, the outputs into v
 template <class P, int DIR, bool PAD, int STRIDE, bool TAIL, int S, class Sync, class V>
 __device__ __forceinline__ void fft_stages(V (&v)[P::E], V (&b)[P::E], V* sm, int t, const float2* __restrict__ tw,
                                            const Sync& sync) {
   constexpr int N = P::N, E = P::E, R = P::radix(S), NS = P::span(S);
   constexpr bool LAST = P::radix(S + 1) == 0;
-  stage_load<N, E, R, NS, P::span(S - 1), PAD, STRIDE>(b, sm, t);
+  stage_load<N, E, R, xgroup<P>(S - 1), xpad<P>(S - 1), PAD, STRIDE>(b, sm, t);
   if (TAIL || !LAST) sync();
   stage_tw<N, E, R, NS, DIR>(b, t, tw);
   stage_dft<N, E, R, DIR>(b);
@@ -343,7 +505,7 @@ __device__ __forceinline__ void fft_stages(V (&v)[P::E], V (&b)[P::E], V* sm, in
 #pragma unroll
       for (int r = 0; r < R; ++r) v[u + r * (E / R)] = b[u * R + r];
   } else {
-    stage_store<N, E, R, NS, PAD, STRIDE>(b, sm, t);
+    stage_store<N, E, R, NS, PAD, STRIDE, xgroup<P>(S), xpad<P>(S)>(b, sm, t);
     sync();
     fft_stages<P, DIR, PAD, STRIDE, TAIL, S + 1>(v, b, sm, t, tw, sync);
   }
@@ -364,7 +526,7 @@ __device__ __forceinline__ void fft_plan(V (&v)[P::E], V* sm, int t, const float
 #pragma unroll
     for (int r = 0; r < R0; ++r) b[u * R0 + r] = v[u + r * (E / R0)];
   stage_dft<N, E, R0, DIR>(b);
-  stage_store<N, E, R0, 1, PAD, STRIDE>(b, sm, t);
+  stage_store<N, E, R0, 1, PAD, STRIDE, xgroup<P>(0), xpad<P>(0)>(b, sm, t);
   sync();
   fft_stages<P, DIR, PAD, STRIDE, TAIL, 1>(v, b, sm, t, tw, sync);
 }

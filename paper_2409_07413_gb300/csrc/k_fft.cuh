@@ -638,15 +638,17 @@ __global__ void __launch_bounds__(W * PL::T, 2) k_col_split(ColArgs a) {
 template <class P>
 __host__ __device__ constexpr int colt_stride() { return pad_elems_p<P>() | 1; }
 
-// Column pass with two adjacent columns per thread (cpair values): the column loads and
-// stores, the modulus reads and every shared-memory exchange move 16 bytes at a time, which
-// halves the load/store instructions of k_col<COL_PM>; the arithmetic per column is the
-// same as k_col's for the same plan.
+// Column pass with two adjacent columns per thread: the column loads and stores, the
+// modulus reads and every shared-memory exchange move 16 bytes at a time, and the two
+// columns' transforms run on packed pairs (cpk), one two-lane instruction per step of both;
+// per column the operations are those of k_col's transform for the same plan, rounded the
+// same way lane by lane, except that products with the radix-8 constants are fused into
+// the butterfly's additions.
 template <class P, int W>
 __global__ void __launch_bounds__((W / 2) * P::T, ((W / 2) * P::T <= 512 ? 2 : 1)) k_col2(ColArgs a) {
   constexpr int N = P::N, E = P::E, T = P::T, WP = W / 2, STRIPS = N / W;
   extern __shared__ __align__(16) float2 smem2[];
-  cpair* tile = reinterpret_cast<cpair*>(smem2);
+  cpk* tile = reinterpret_cast<cpk*>(smem2);
   float* Ms = reinterpret_cast<float*>(smem2 + (size_t)N * W);
   const int cp = threadIdx.x % WP, t = threadIdx.x / WP;
   const int img = blockIdx.x / STRIPS, strip = blockIdx.x % STRIPS;
@@ -660,9 +662,9 @@ __global__ void __launch_bounds__((W / 2) * P::T, ((W / 2) * P::T <= 512 ? 2 : 1
     }
     cp_async_commit();
   }
-  cpair v[E];
+  cpk v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = base[(size_t)(t + m * T) * (N / 2)];
+  for (int m = 0; m < E; ++m) v[m] = pack_pair(base[(size_t)(t + m * T) * (N / 2)]);
   fft_plan<P, -1, false, WP, false>(v, tile + cp, t, a.tw, sync);
   cp_async_wait_all();
   sync();  // also ends the transform's shared-memory reads
@@ -670,12 +672,14 @@ __global__ void __launch_bounds__((W / 2) * P::T, ((W / 2) * P::T <= 512 ? 2 : 1
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const float2 mv = *reinterpret_cast<const float2*>(Ms + (t + m * T) * W + 2 * cp);
-    v[m].a = pm_value(v[m].a, mv.x, inv_n);
-    v[m].b = pm_value(v[m].b, mv.y, inv_n);
+    cpair q = unpack_pair(v[m]);
+    q.a = pm_value(q.a, mv.x, inv_n);
+    q.b = pm_value(q.b, mv.y, inv_n);
+    v[m] = pack_pair(q);
   }
   fft_plan<P, +1, false, WP, false>(v, tile + cp, t, a.tw, sync);
 #pragma unroll
-  for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * (N / 2)] = v[m];
+  for (int m = 0; m < E; ++m) base[(size_t)(t + m * T) * (N / 2)] = unpack_pair(v[m]);
 }
 
 template <class P, int W>
