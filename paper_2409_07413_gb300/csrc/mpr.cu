@@ -181,6 +181,7 @@ class Run {
   int32_t* tr_best = nullptr;
   void *peaks = nullptr, *init_sc = nullptr;
   bool z_valid = false;
+  int z_path = 0;  // layout of the spectra in w while z_valid: 0 natural rows, 2 chunked (split passes)
   // precision 1: the iteration blocks keep x and w as half2 inside the w buffer
   bool fp16 = false, z16_valid = false, x16_newer = false;
 
@@ -360,7 +361,8 @@ class Run {
 
   spring_status iterations(int alg, int k) {
     if (k <= 0) return SPRING_OK;
-    if (fp16 || iteration_path(n) != 1)  // the row passes read the supports as bits
+    const int path = iteration_path(n);  // one path for the whole block
+    if (fp16 || path != 1)  // the row passes read the supports as bits
       SPRING_TRY(launch_pack_support(S, Sb, (long long)NBT * nn(), s));
     if (fp16) {
       if (!z16_valid) {
@@ -374,21 +376,23 @@ class Run {
       x16_newer = true;
       return SPRING_OK;
     }
-    if (iteration_path(n) == 1) {  // on chip: x in, x out; w is left stale
+    if (path == 1) {  // on chip: x in, x out; w is left stale
       SPRING_TRY(launch_cluster_iter(n, alg, x, S, Mall, NBT, prm.beta, prm.chi, k, s, mgroup));
       z_valid = false;
       return SPRING_OK;
     }
-    if (iteration_path(n) == 2) {  // split passes: w holds the chunked spectra
-      if (!z_valid) {
+    if (path == 2) {  // split passes: w holds the chunked spectra
+      if (!z_valid || z_path != 2) {
         SPRING_TRY(launch_row_split(n, 0, true, w, x, nullptr, NBT, prm.beta, prm.chi, s));
         z_valid = true;
+        z_path = 2;
       }
       return iterate_split(n, alg, w, x, Sb, Msplit, NBT, mgroup, prm.beta, prm.chi, k, s);
     }
-    if (!z_valid) {
+    if (!z_valid || z_path != 0) {
       SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, NBT, 1.0f, s));
       z_valid = true;
+      z_path = 0;
     }
     for (int it = 0; it < k; ++it) {
       SPRING_TRY(launch_col_pm(n, w, Mall, NBT, s, mgroup));
