@@ -395,11 +395,16 @@ def run_ours(args, wl):
         achieved = st.bytes_per_launch / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else None
         other = kst[spring.KC_COL_PM if kc == spring.KC_ROW_ITER else spring.KC_ROW_ITER]
         oavg = other.total_ms / max(1, other.timed)
+        # the kernels behind the two iteration classes depend on the path the side runs:
+        # two passes (k_row / k_col*), split passes (k_row_split / k_col_split), split with
+        # packed rows (k_row_split_pk / k_col_split); DRAM traffic is keyed the same way
+        path = spring.get_iteration_path(n)
+        knames = {2: ("row_split", "col_split"), 3: ("row_split_pk", "col_split")}.get(path, ("row_iter", "col_pm"))
         traffic = None
         prof = ROOT / "profiles" / "traffic.json"
         if prof.exists():
             try:
-                traffic = json.loads(prof.read_text()).get({0: "row_iter", 1: "col_pm"}[kc])
+                traffic = json.loads(prof.read_text()).get(knames[kc])
             except Exception:
                 traffic = None
         golden = {}
@@ -422,12 +427,12 @@ def run_ours(args, wl):
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "error": {"final_error_avg": statistics.mean(ea), "final_error_best": statistics.mean(eb),
                       "oracle": golden or None},
-            "roofline": {"bound": "hbm", "kernel": {0: "row_iter", 1: "col_pm"}[kc],
+            "roofline": {"bound": "hbm", "kernel": knames[kc], "iteration_path": path,
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "bytes_per_launch": st.bytes_per_launch, "avg_launch_ms": avg_ms,
                          "launches_timed": st.timed, "timing_stride": TIMING_STRIDE,
-                         "other_kernel": {"name": {0: "row_iter", 1: "col_pm"}[1 - kc],
+                         "other_kernel": {"name": knames[1 - kc],
                                           "avg_launch_ms": oavg,
                                           "achieved": other.bytes_per_launch / (oavg / 1000.0) / 1e9 if oavg > 0 else None}},
             "cpu_baseline": cpu,

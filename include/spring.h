@@ -449,10 +449,12 @@ spring_status spring_initialize(uint64_t seed, const uint8_t* S0, const float* M
  *   col 2: 32-column tiles (16 at N = 1024); col 3: 8-column tiles;
  *   col 4 / 5: persistent blocks fed by TMA (16 / 8-column tiles, next tile in flight);
  *   col 6 / 7: transposed tiles, one lane group per column (warp-level synchronisation);
- *   col 8 / 9: two adjacent columns per thread, 16-byte accesses throughout (16 / 32-column
- *   tiles; their plan has the default's radices at N = 64, 192, 512, column 1's at 1024).
- * Variants sharing a radix plan give bit-identical results (row 0-4, row 5-6; column 0
- * and 2-7, column 8-9); the alternative plans differ by rounding.  A run tunes each side once per process
+ *   col 8 / 9: two adjacent columns per thread, 16-byte accesses throughout, the two
+ *   columns' transforms on packed two-lane FP32 instructions (16 / 32-column tiles);
+ *   col 10: column 1's plan in 512-thread blocks held to three per SM.
+ * Variants sharing a radix plan and arithmetic give bit-identical results (row 0-4, row
+ * 5-6; column 0 and 2-7, column 1 and 10 (10 is column 0 at N = 64, 96), column 8-9); the
+ * others differ by rounding.  A run tunes each side once per process
  * (spring_autotune on the run's batch) unless the environment sets SPRING_AUTOTUNE=0 or
  * the variant was set explicitly. */
 spring_status spring_set_kernel_variant(int n, int row_variant, int col_variant); /* -1 = keep */
@@ -462,8 +464,11 @@ spring_status spring_get_kernel_variant(int n, int* row_variant, int* col_varian
 spring_status spring_autotune(int n, int batch, void* stream);
 /* How runs iterate at side n: 0 = two passes through HBM per iteration (row pass, column
  * pass), 1 = the on-chip kernel of spring_iterate_fused (N <= 256; INVALID where the
- * device cannot hold its clusters).  The autotuner picks the faster one; an explicit
- * choice is kept. */
+ * device cannot hold its clusters), 2 = the split passes (N = 512, 1024): the column
+ * transform is decimated in frequency over the rows, its first radix-8 stage runs in the
+ * row pass on the 8 rows n1 + (N/8) n2 one block holds and the column pass transforms
+ * N/8-point chunks (the same sums in another order), 3 = path 2 with the row transforms
+ * on packed pairs of rows.  The autotuner picks the fastest; an explicit choice is kept. */
 spring_status spring_set_iteration_path(int n, int path);
 spring_status spring_get_iteration_path(int n, int* path);
 

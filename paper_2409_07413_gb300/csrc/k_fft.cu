@@ -50,7 +50,8 @@ static int g_col_var[N_SIDES] = {0, 1, 2, 1, 0, 0, 0, 1, 1};
 static bool g_tuned[N_SIDES] = {};
 // iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
 // (N <= 256, k_cluster.cu), 2 = the split passes (N = 512, 1024: the column transform's
-// first stage in the row pass); chosen by the autotuner, the two-pass path until then
+// first stage in the row pass), 3 = the split passes with the row transforms on packed
+// pairs of rows; chosen by the autotuner, the two-pass path until then
 static int g_path[N_SIDES] = {};
 
 int iteration_path(int n) {
@@ -318,9 +319,10 @@ spring_status launch_split_modulus(int n, const float* M, float* Mp, int K, cuda
   return SPRING_OK;
 }
 
-// the split row pass: fwd_only = the forward row transforms and first stage from x alone
+// the split row pass: fwd_only = the forward row transforms and first stage from x alone;
+// packed = the iteration's row transforms on packed pairs of rows (k_row_split_pk)
 spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2* x, const uint32_t* Sb,
-                               long long batch, float beta, float chi, cudaStream_t s) {
+                               long long batch, float beta, float chi, cudaStream_t s, bool packed) {
   if (!split_side(n)) return invalid("the split passes cover sides 512 and 1024");
   if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
   DeviceTables tb;
@@ -328,6 +330,7 @@ spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2*
   FftOp op;
   op.kind = fwd_only ? OP_ROW_SPLIT_FWD : OP_ROW_SPLIT;
   op.alg = alg;
+  op.variant = (packed && !fwd_only) ? 1 : 0;
   op.kclass = fwd_only ? SPRING_KC_OTHER : SPRING_KC_ROW_ITER;
   op.sa.w = w;
   op.sa.x = x;
@@ -362,11 +365,12 @@ spring_status launch_col_split(int n, float2* w, const float* Mp, int batch, cud
 // k iterations (column pass, then row pass) in the split form; w must hold the chunked
 // forward spectra of x (launch_row_split with fwd_only) on entry and holds them on exit
 spring_status iterate_split(int n, int alg, float2* w, float2* x, const uint32_t* Sb, const float* Mp,
-                            long long batch, int m_group, float beta, float chi, int k, cudaStream_t s) {
+                            long long batch, int m_group, float beta, float chi, int k, cudaStream_t s,
+                            bool packed) {
   if (batch > INT32_MAX) return invalid("batch too large");
   for (int it = 0; it < k; ++it) {
     SPRING_TRY(launch_col_split(n, w, Mp, (int)batch, s, m_group));
-    SPRING_TRY(launch_row_split(n, alg, false, w, x, Sb, batch, beta, chi, s));
+    SPRING_TRY(launch_row_split(n, alg, false, w, x, Sb, batch, beta, chi, s, packed));
   }
   return SPRING_OK;
 }
@@ -607,8 +611,12 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
     SPRING_CUDA(cudaEventCreate(&e2));
     spring_status st = dispatch(n, cop, s);  // warm-up of both forms
     if (st == SPRING_OK) st = dispatch(n, op, s);
+    cudaEvent_t e3;
+    SPRING_CUDA(cudaEventCreate(&e3));
     if (st == SPRING_OK) st = launch_row_split(n, 2, true, w, x, nullptr, batch, 0.9f, 0.5f, s);
     if (st == SPRING_OK) st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, 1, s);
+    if (st == SPRING_OK)
+      st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, 1, s, true);
     cudaEventRecord(e0, s);
     for (int k = 0; k < K && st == SPRING_OK; ++k) {
       st = dispatch(n, cop, s);
@@ -617,15 +625,21 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
     cudaEventRecord(e1, s);
     if (st == SPRING_OK) st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, K, s);
     cudaEventRecord(e2, s);
-    cudaEventSynchronize(e2);
-    float two = 0.f, split = 0.f;
+    if (st == SPRING_OK)
+      st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, K, s, true);
+    cudaEventRecord(e3, s);
+    cudaEventSynchronize(e3);
+    float two = 0.f, split = 0.f, split_pk = 0.f;
     cudaEventElapsedTime(&two, e0, e1);
     cudaEventElapsedTime(&split, e1, e2);
+    cudaEventElapsedTime(&split_pk, e2, e3);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
+    cudaEventDestroy(e3);
     SPRING_TRY(st);
-    if (split < two) path = 2;
+    if (split < two && split <= split_pk) path = 2;
+    else if (split_pk < two) path = 3;
   }
   std::lock_guard<std::mutex> lk(g_var_mu);
   g_row_var[si] = best_r;
@@ -684,8 +698,9 @@ spring_status spring_autotune(int n, int batch, void* stream) {
 spring_status spring_set_iteration_path(int n, int path) {
   const int si = side_index(n);
   if (si < 0) return invalid("unsupported pattern side");
-  if (path < 0 || path > 2) return invalid("path must be 0 (two passes), 1 (on chip) or 2 (split passes)");
-  if (path == 2 && !split_side(n)) return invalid("the split passes cover sides 512 and 1024");
+  if (path < 0 || path > 3)
+    return invalid("path must be 0 (two passes), 1 (on chip), 2 (split passes) or 3 (split, packed rows)");
+  if (path >= 2 && !split_side(n)) return invalid("the split passes cover sides 512 and 1024");
   if (path == 1) {
     bool ok = false;
     SPRING_TRY(cluster_supported(n, &ok));

@@ -595,6 +595,134 @@ __global__ void __launch_bounds__(SPLIT_Q * P::T, split_row_minb<P::N>()) k_row_
   }
 }
 
+// Blocks of a packed split row pass per SM the register budget is sized for
+template <int N> constexpr int split_row_pk_minb() { return N <= 512 ? 2 : 1; }
+// shared-memory float2 elements of a packed split row pass block (always staged)
+template <class P>
+__host__ __device__ constexpr size_t split_row_pk_elems() {
+  return (size_t)SPLIT_Q * pad_elems_p<P>() + (size_t)2 * SPLIT_Q * P::N + SPLIT_Q * P::N / 64;
+}
+
+// The split row pass (ROW_ITER) on packed pairs: lane group g < Q/2 carries rows n1 + L g
+// (lane 0) and n1 + L (g + Q/2) (lane 1) through one packed transform, so each step of the
+// two rows' transforms is one two-lane instruction and each exchange a 16-byte access.
+// The cross-row first stages stay scalar, one column at a time; the update is taken lane by
+// lane.  Staged and persistent like k_row_split<..., STAGE = true>; the same arithmetic per
+// row as the packed transforms (cpk) of the same plan.
+template <class P, int ALG>
+__global__ void __launch_bounds__(SPLIT_Q / 2 * P::T, split_row_pk_minb<P::N>()) k_row_split_pk(SplitArgs a) {
+  constexpr int N = P::N, E = P::E, T = P::T, Q = SPLIT_Q, H = Q / 2, L = N / Q, TH = H * T;
+  constexpr int RS = pad_elems_p<P>(), CPT = N / TH, NW = N / 32;
+  static_assert(N % TH == 0 && RS >= N && N % 128 == 0 && (Q * N / 2) % TH == 0, "packed split row tiling");
+  extern __shared__ __align__(16) float2 smem[];
+  cpk* R = reinterpret_cast<cpk*>(smem);                   // H exchange areas of RS pairs
+  float2* Ws = smem + (size_t)Q * RS;                      // spectra rows k2 L + n1 of the set
+  float2* Xs = Ws + Q * N;                                 // the set's x rows
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(Xs + Q * N);  // their support words
+  const int tid = threadIdx.x, grp = tid / T, t = tid % T;
+  const auto gsync = GroupSync<T>::make();
+  auto stage_w = [&](long long set) {
+    if (set < a.nsets) {
+      const float2* src = a.w + (set / L) * N * N + (set % L) * N;
+#pragma unroll
+      for (int i = 0; i < Q * N / 2 / TH; ++i) {
+        const int k = tid + i * TH, k2 = k / (N / 2), q = k % (N / 2);
+        cp_async16(Ws + k2 * N + 2 * q, src + (long long)k2 * L * N + 2 * q);
+      }
+    }
+    cp_async_commit();
+  };
+  stage_w(blockIdx.x);
+  cp_async_wait_all();
+  __syncthreads();
+  for (long long set = blockIdx.x; set < a.nsets; set += gridDim.x) {
+    const long long img = set / L;
+    const int n1 = (int)(set % L);
+    float2* wi = a.w + img * N * N;
+    float2* xi = a.x + img * N * N;
+    const long long xrow0 = (long long)(n1 + L * grp) * N, xrow1 = (long long)(n1 + L * (grp + H)) * N;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {  // inverse first stage of column c, into the pairs
+      const int c = tid + j * TH;
+      float2 z[Q];
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) z[k2] = Ws[k2 * N + c];
+#pragma unroll
+      for (int k2 = 1; k2 < Q; ++k2) z[k2] = cmul(z[k2], cconj(__ldg(&a.tw[n1 * k2])));
+      DFT<Q, +1>::run(z);
+#pragma unroll
+      for (int g = 0; g < H; ++g) R[g * RS + c] = cpk{make_float2(z[g].x, z[g + H].x), make_float2(z[g].y, z[g + H].y)};
+    }
+    __syncthreads();
+    {  // the group's two x rows and their support words, then the next set's spectra
+      const uint32_t* s0 = a.Sb + (img * N * N + xrow0) / 32;
+      const uint32_t* s1 = a.Sb + (img * N * N + xrow1) / 32;
+      if constexpr (ALG != 0) {
+#pragma unroll
+        for (int i = 0; i < N / 2 / T; ++i) {
+          cp_async16(Xs + grp * N + 2 * (t + i * T), xi + xrow0 + 2 * (t + i * T));
+          cp_async16(Xs + (grp + H) * N + 2 * (t + i * T), xi + xrow1 + 2 * (t + i * T));
+        }
+      }
+      if (t < N / 128) {
+        cp_async16(Bs + grp * NW + 4 * t, s0 + 4 * t);
+        cp_async16(Bs + (grp + H) * NW + 4 * t, s1 + 4 * t);
+      }
+      cp_async_commit();
+      stage_w(set + gridDim.x);
+    }
+    cpk v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = R[grp * RS + t + m * T];
+    gsync();                                                    // before the exchange writes
+    fft_plan<P, +1, true, 1>(v, R + grp * RS, t, a.tw, gsync);  // m = P_M x_n, both rows
+    cp_async_wait_group<1>();  // this set's x rows and words (the next set's spectra may fly)
+    gsync();
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int col = t + m * T;
+      const uint32_t w0 = Bs[grp * NW + (col >> 5)], w1 = Bs[(grp + H) * NW + (col >> 5)];
+      const float2 pm0 = make_float2(v[m].re.x, v[m].im.x), pm1 = make_float2(v[m].re.y, v[m].im.y);
+      bool c0 = support_bit(w0, col), c1 = support_bit(w1, col);
+      if (a.chi_on) {
+        c0 = c0 && (pm0.x >= a.cchi * sqrtf(pm0.x * pm0.x + pm0.y * pm0.y));
+        c1 = c1 && (pm1.x >= a.cchi * sqrtf(pm1.x * pm1.x + pm1.y * pm1.y));
+      }
+      float2 xo0 = pm0, xo1 = pm1;
+      if (ALG != 0) {
+        xo0 = Xs[grp * N + col];
+        xo1 = Xs[(grp + H) * N + col];
+      }
+      const float2 x0 = update_pixel(ALG, xo0, pm0, c0, a.beta), x1 = update_pixel(ALG, xo1, pm1, c1, a.beta);
+      xi[xrow0 + col] = x0;
+      xi[xrow1 + col] = x1;
+      v[m] = cpk{make_float2(x0.x, x1.x), make_float2(x0.y, x1.y)};
+    }
+    fft_plan<P, -1, true, 1>(v, R + grp * RS, t, a.tw, gsync);  // ends with the group's barrier
+#pragma unroll
+    for (int m = 0; m < E; ++m) R[grp * RS + t + m * T] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {  // forward first stage of column c, from the pairs
+      const int c = tid + j * TH;
+      float2 y[Q];
+#pragma unroll
+      for (int g = 0; g < H; ++g) {
+        const cpk q = R[g * RS + c];
+        y[g] = make_float2(q.re.x, q.im.x);
+        y[g + H] = make_float2(q.re.y, q.im.y);
+      }
+      DFT<Q, -1>::run(y);
+#pragma unroll
+      for (int k2 = 1; k2 < Q; ++k2) y[k2] = cmul(y[k2], __ldg(&a.tw[n1 * k2]));
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) wi[(long long)(k2 * L + n1) * N + c] = y[k2];
+    }
+    cp_async_wait_all();  // the next set's spectra rows
+    __syncthreads();      // R, Ws, Xs and Bs are written again for the next set
+  }
+}
+
 // Split column pass: L-point transforms of the chunks (plan PL of side L), P_M against the
 // permuted modulus (a.M in the chunked layout; its unnormalised scale is the full N-point
 // transform's), inverse L-point transforms.  Tile = (image, chunk k2, strip of W columns).
@@ -950,8 +1078,36 @@ inline spring_status col_pm_tma_launch(const FftOp& op, cudaStream_t s, bool pre
   return SPRING_OK;
 }
 
+template <int N, int ALG>
+inline spring_status row_split_pk_launch(const FftOp& op, cudaStream_t s, bool prep) {
+  using P = SplitRowPlan<N>;
+  constexpr int TH = SPLIT_Q / 2 * P::T;
+  const size_t smem = split_row_pk_elems<P>() * sizeof(float2);
+  auto kern = k_row_split_pk<P, ALG>;
+  if (prep) return allow_smem(kern, smem);
+  const long long sets = op.sa.nsets;
+  if (sets < 1) return SPRING_OK;
+  if ((reinterpret_cast<uintptr_t>(op.sa.w) | reinterpret_cast<uintptr_t>(op.sa.x) |
+       reinterpret_cast<uintptr_t>(op.sa.Sb)) & 15u)
+    return invalid("the split row pass stages from 16-byte aligned w, x and support bits");
+  int per_sm = 0;
+  SPRING_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TH, smem));
+  if (per_sm < 1) return invalid("split row pass does not fit an SM");
+  const long long cap = (long long)per_sm * sm_count();  // persistent
+  const int blocks = (int)(sets < cap ? sets : cap);
+  launch_begin(op.kclass, s);
+  kern<<<blocks, TH, smem, s>>>(op.sa);
+  SPRING_CHECK_LAUNCH();
+  launch_end(op.kclass, s, op.bytes);
+  return SPRING_OK;
+}
+
 template <int N, int MODE, int ALG>
 inline spring_status row_split_launch(const FftOp& op, cudaStream_t s, bool prep) {
+  if constexpr (MODE == ROW_ITER) {
+    if (prep) SPRING_TRY((row_split_pk_launch<N, ALG>(op, s, true)));
+    else if (op.variant == 1) return row_split_pk_launch<N, ALG>(op, s, false);
+  }
   using P = SplitRowPlan<N>;
   constexpr bool STAGE = MODE == ROW_ITER;
   const size_t smem = split_row_elems<P, STAGE>() * sizeof(float2);

@@ -415,14 +415,15 @@ def test_autotune_picks_a_valid_variant(sp):
 
 
 # ----------------------------------------------------------------------------- split passes
-@pytest.fixture
-def split_path(sp):
-    """The split passes (column transform's first stage in the row pass) for sides 512 and
-    1024, restoring each side's iteration path afterwards."""
+@pytest.fixture(params=[2, 3], ids=["split", "split_packed"])
+def split_path(sp, request):
+    """The split passes (column transform's first stage in the row pass; path 3: the row
+    transforms on packed pairs of rows) for sides 512 and 1024, restoring each side's
+    iteration path afterwards."""
     saved = {n: sp.get_iteration_path(n) for n in (512, 1024)}
     for n in saved:
-        sp.set_iteration_path(n, 2)
-    yield
+        sp.set_iteration_path(n, request.param)
+    yield request.param
     for n, p in saved.items():
         sp.set_iteration_path(n, p)
 
@@ -480,6 +481,21 @@ def test_split_iterate_many_sets_per_block(sp, split_path, n, B, alg):
     for b in range(B):  # every image of the batch, not the batch as a whole
         assert rel(got[b][sure[b]], ref[b][sure[b]]) < TOL, b
     assert (~sure).mean() < 1e-3
+
+
+def test_iteration_path_arguments(sp):
+    # the split forms cover 512 and 1024 only; paths past 3 do not exist
+    saved = sp.get_iteration_path(256), sp.get_iteration_path(512)
+    try:
+        for n, path in ((256, 2), (256, 3), (512, 4), (512, -1)):
+            with pytest.raises(sp.SpringError) as e:
+                sp.set_iteration_path(n, path)
+            assert e.value.status == sp.E_INVALID
+        sp.set_iteration_path(512, 3)
+        assert sp.get_iteration_path(512) == 3
+    finally:
+        sp.set_iteration_path(256, saved[0])
+        sp.set_iteration_path(512, saved[1])
 
 
 def test_iterate_rejects_misaligned_x(sp):
