@@ -36,15 +36,21 @@ spring_status launch_col_fft(int n, int dir, float2* data, int batch, float scal
 // column forward transform + per-block FP64 partial sums of the Fourier error
 int err_strips(int n);
 spring_status launch_col_err(int n, float2* w, const float* M, int batch, double* partials,
-                             cudaStream_t s, int m_group = 0);
+                             cudaStream_t s, int m_group = 0, bool skip_m2 = false);
+// err = sqrt(num / den) per image; m2 != nullptr: den from m2 (one value per m_group
+// consecutive images, or m2[0] for all with m_group 0) instead of the partials
 spring_status launch_err_finalize(int n, const double* partials, int batch, double* err,
-                                  int* status, cudaStream_t s);
+                                  int* status, cudaStream_t s, const double* m2 = nullptr,
+                                  int m_group = 0);
+// m2[k] = sum of M^2 over the measured pixels (M >= 0) of the k-th of K modulus arrays, FP64
+spring_status launch_m2_sum(int n, const float* M, int K, double* m2, cudaStream_t s);
 // the same two error launchers with a caller-supplied twiddle table (all sides, laid out
 // at tw_offset(N)) instead of the per-device one
 spring_status launch_row_fft_tw(int n, int dir, const float2* in, float2* out, const uint8_t* Smul,
                                 long long batch, float scale, const float2* tw_all, cudaStream_t s);
 spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
-                                const float2* tw_all, cudaStream_t s, int m_group = 0);
+                                const float2* tw_all, cudaStream_t s, int m_group = 0,
+                                bool skip_m2 = false);
 
 // FP16 storage of the iteration buffers (precision 1): wh, xh are half2 arrays; x is kept
 // scaled by the device scalar s16 (a power of two from launch_fp16_scale), w by s16 times a

@@ -153,7 +153,7 @@ spring_status launch_col_fft(int n, int dir, float2* data, int batch, float scal
 int err_strips(int n) { return n / ERR_W; }
 
 spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, double* partials,
-                                const float2* tw_all, cudaStream_t s, int m_group) {
+                                const float2* tw_all, cudaStream_t s, int m_group, bool skip_m2) {
   FftOp op;
   op.kind = OP_COL_ERR;
   op.ca.data = w;
@@ -162,38 +162,73 @@ spring_status launch_col_err_tw(int n, float2* w, const float* M, int batch, dou
   op.ca.batch = batch;
   op.ca.partials = partials;
   op.ca.m_group = m_group;
+  op.ca.skip_m2 = skip_m2 ? 1 : 0;
   op.bytes = (double)batch * n * n * 8.0 + (double)n * n * 4.0;
   return dispatch(n, op, s);
 }
 
 spring_status launch_col_err(int n, float2* w, const float* M, int batch, double* partials,
-                             cudaStream_t s, int m_group) {
+                             cudaStream_t s, int m_group, bool skip_m2) {
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
-  return launch_col_err_tw(n, w, M, batch, partials, tb.tw, s, m_group);
+  return launch_col_err_tw(n, w, M, batch, partials, tb.tw, s, m_group, skip_m2);
 }
 
 __global__ void k_err_finalize(const double* __restrict__ partials, int strips, int batch,
-                               double* __restrict__ err, int* __restrict__ status) {
+                               double* __restrict__ err, int* __restrict__ status,
+                               const double* __restrict__ m2, int m_group) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
   double sn = 0.0, sd = 0.0;
   for (int s = 0; s < strips; ++s) {
     sn += partials[((size_t)b * strips + s) * 2 + 0];
-    sd += partials[((size_t)b * strips + s) * 2 + 1];
+    if (!m2) sd += partials[((size_t)b * strips + s) * 2 + 1];
   }
+  if (m2) sd = m2[m_group > 0 ? b / m_group : 0];
   const double e = sd > 0.0 ? sqrt(sn / sd) : 0.0;
   if (!isfinite(e) && status) atomicOr(status, 1);
   err[b] = e;
 }
 
 spring_status launch_err_finalize(int n, const double* partials, int batch, double* err,
-                                  int* status, cudaStream_t s) {
+                                  int* status, cudaStream_t s, const double* m2, int m_group) {
   if (batch < 1) return SPRING_OK;
   launch_begin(SPRING_KC_OTHER, s);
-  k_err_finalize<<<div_up(batch, 128), 128, 0, s>>>(partials, n / ERR_W, batch, err, status);
+  k_err_finalize<<<div_up(batch, 128), 128, 0, s>>>(partials, n / ERR_W, batch, err, status, m2, m_group);
   SPRING_CHECK_LAUNCH();
   launch_end(SPRING_KC_OTHER, s, 16.0 * batch * (n / ERR_W));
+  return SPRING_OK;
+}
+
+// The denominator of Eq. error_calc, sum of M^2 over the measured pixels, depends on the
+// pattern only: one block per modulus array, FP64 partial sums per thread in a fixed
+// order, then a fixed-order block reduction.
+__global__ void k_m2_sum(const float* __restrict__ M, long long nn, double* __restrict__ m2) {
+  const float* Mk = M + (size_t)blockIdx.x * nn;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < nn; i += blockDim.x) {
+    const float v = Mk[i];
+    if (v >= 0.f) acc += (double)v * (double)v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    m2[blockIdx.x] = t;
+  }
+}
+
+spring_status launch_m2_sum(int n, const float* M, int K, double* m2, cudaStream_t s) {
+  if (K < 1) return SPRING_OK;
+  launch_begin(SPRING_KC_OTHER, s);
+  k_m2_sum<<<K, 1024, 0, s>>>(M, (long long)n * n, m2);
+  SPRING_CHECK_LAUNCH();
+  launch_end(SPRING_KC_OTHER, s, 4.0 * K * n * n);
   return SPRING_OK;
 }
 

@@ -80,7 +80,7 @@ static spring_status validate_params(int n, const spring_params& p) {
 // ------------------------------------------------------------------ device layout of a run
 struct Layout {
   size_t x, w, S, Sb, sm0, sm1, err, abc, ix, ir, info, best, ph, alpha, repl, dens, part_err,
-      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, mall, msplit, total;
+      part_norm, part_dens, imgmax, stats, avg, Savg, err_avg, status, peaks, init, mavg, mall, msplit, m2, total;
 };
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -126,6 +126,7 @@ static Layout make_layout(int n, const spring_params& p, int K = 1) {
   L.mavg = take(p.ca > 0.f ? sizeof(float) * nn : 0);
   L.mall = take(K > 1 ? sizeof(float) * nn * K : 0);  // the K modulus arrays, gathered
   L.msplit = take(split_supported(n) ? sizeof(float) * nn * K : 0);  // M in the split passes' layout
+  L.m2 = take(sizeof(double) * K);  // sum of M^2 over the measured pixels, per pattern
   L.total = o;
   return L;
 }
@@ -175,6 +176,7 @@ class Run {
   int* status = nullptr;
   float* mavg = nullptr;  // crossover averaging: (M-dot + M-double-dot) / 2
   float* Msplit = nullptr;  // the K modulus arrays in the split column pass's layout (N = 512, 1024)
+  double* m2 = nullptr;     // per pattern: sum of M^2 over its measured pixels (Eq. error_calc)
   // spring_mpr_step's trace (single-pattern runs): the improved parents' errors before
   // Select, and the parent whose area is alpha_best (device buffers owned by the caller)
   double* tr_err = nullptr;
@@ -272,6 +274,8 @@ class Run {
       Msplit = reinterpret_cast<float*>(mem + L.msplit);
       SPRING_TRY(launch_split_modulus(n, Mall, Msplit, K, s));
     }
+    m2 = reinterpret_cast<double*>(mem + L.m2);
+    SPRING_TRY(launch_m2_sum(n, Mall, K, m2, s));
     return SPRING_OK;
   }
 
@@ -420,8 +424,8 @@ class Run {
     const Phase range("spring:get_error");
     SPRING_TRY(sync_x());
     SPRING_TRY(launch_row_fft(n, -1, x, w, S, NBT, 1.0f, s));
-    SPRING_TRY(launch_col_err(n, w, Mall, NBT, part_err, s, mgroup));
-    SPRING_TRY(launch_err_finalize(n, part_err, NBT, err, status, s));
+    SPRING_TRY(launch_col_err(n, w, Mall, NBT, part_err, s, mgroup, true));
+    SPRING_TRY(launch_err_finalize(n, part_err, NBT, err, status, s, m2, mgroup));
     z_valid = z16_valid = false;  // w served as scratch
     return SPRING_OK;
   }
@@ -568,8 +572,8 @@ class Run {
     SPRING_TRY(align(ix, ir, info, ph));
     SPRING_TRY(launch_average(n, x_pop(), S_pop(), info, ph, bestq(), P, avgq(), Savgq(), s));
     SPRING_TRY(launch_row_fft(n, -1, avgq(), w_new(), Savgq(), 1, 1.0f, s));
-    SPRING_TRY(launch_col_err(n, w_new(), Mq(), 1, part_err, s));
-    SPRING_TRY(launch_err_finalize(n, part_err, 1, err_avgq(), status, s));
+    SPRING_TRY(launch_col_err(n, w_new(), Mq(), 1, part_err, s, 0, true));
+    SPRING_TRY(launch_err_finalize(n, part_err, 1, err_avgq(), status, s, m2 + (K > 1 ? cq : 0)));
     return SPRING_OK;
   }
 
