@@ -157,6 +157,7 @@ def test_mpr_bounded_matches_oracle_statistically(sp, ctx):
     # gapped 128 x 128 patterns: mean final error over seeds within 2 % of the oracle's,
     # widened by two standard errors of the difference of the means
     eg, eo, eu = [], [], []
+    ea, oa = [], []
     for seed in range(12):
         pat = synthetic.config_pattern("ell128", seed)
         prob = ctx.problem(pat.intensities, pat.mask, pat.support0, saturated=pat.saturated,
@@ -166,12 +167,17 @@ def test_mpr_bounded_matches_oracle_statistically(sp, ctx):
         o = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, saturated=pat.saturated,
                            seed=seed, ub_eta=1.5, **C1)
         eg.append(r["final_error_best"])
+        ea.append(r["final_error_avg"])
         eo.append(o["final_error_best"])
+        oa.append(o["final_error_avg"])
         assert np.isfinite(r["rho_avg"]).all()
     eg, eo = np.array(eg), np.array(eo)
     se = np.sqrt(eg.var(ddof=1) / len(eg) + eo.var(ddof=1) / len(eo))
     print(f"bounded: mean E gpu {eg.mean():.4f} oracle {eo.mean():.4f} (se {se:.4f})")
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
+    ea, oa = np.array(ea), np.array(oa)  # the error of the average reconstruction, same bar
+    sea = np.sqrt(ea.var(ddof=1) / len(ea) + oa.var(ddof=1) / len(oa))
+    assert abs(ea.mean() - oa.mean()) <= 0.02 * oa.mean() + 2.0 * sea, (ea.mean(), oa.mean(), sea)
 
 
 def test_bounded_problem_changes_the_run(sp, ctx):

@@ -165,6 +165,7 @@ def test_mpr_fp16_matches_oracle_statistically(sp, ctx):
     # the same bar as the FP32 end-to-end test: mean final error over 16 seeds within 2 %
     # of the oracle's, widened by two standard errors of the difference of the means
     eg, eo = [], []
+    ea, oa = [], []
     for seed in range(16):
         pat = synthetic.config_pattern("sphere64", seed)
         prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
@@ -172,12 +173,17 @@ def test_mpr_fp16_matches_oracle_statistically(sp, ctx):
         prob.destroy()
         o = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=seed, **C1)
         eg.append(r["final_error_best"])
+        ea.append(r["final_error_avg"])
         eo.append(o["final_error_best"])
+        oa.append(o["final_error_avg"])
         assert np.isfinite(r["rho_avg"]).all()
     eg, eo = np.array(eg), np.array(eo)
     se = np.sqrt(eg.var(ddof=1) / len(eg) + eo.var(ddof=1) / len(eo))
     print(f"mean E fp16 {eg.mean():.4f} oracle {eo.mean():.4f} (se {se:.4f})")
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
+    ea, oa = np.array(ea), np.array(oa)  # the error of the average reconstruction, same bar
+    sea = np.sqrt(ea.var(ddof=1) / len(ea) + oa.var(ddof=1) / len(oa))
+    assert abs(ea.mean() - oa.mean()) <= 0.02 * oa.mean() + 2.0 * sea, (ea.mean(), oa.mean(), sea)
 
 
 @pytest.mark.parametrize("name", ["ell96", "ell128", "ell192", "ell256", "ell384", "ell512", "ell768",

@@ -124,6 +124,7 @@ def test_run_on_either_path_is_identical(sp, ctx, name):
 def test_fused_run_matches_oracle_statistically(sp, ctx):
     saved = sp.get_iteration_path(64)
     eg, eo = [], []
+    ea, oa = [], []
     try:
         sp.set_iteration_path(64, 1)
         for seed in range(10):
@@ -133,9 +134,14 @@ def test_fused_run_matches_oracle_statistically(sp, ctx):
             prob.destroy()
             o = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=seed, **C1)
             eg.append(r["final_error_best"])
+            ea.append(r["final_error_avg"])
             eo.append(o["final_error_best"])
+            oa.append(o["final_error_avg"])
     finally:
         sp.set_iteration_path(64, saved)
     eg, eo = np.array(eg), np.array(eo)
     se = np.sqrt(eg.var(ddof=1) / len(eg) + eo.var(ddof=1) / len(eo))
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
+    ea, oa = np.array(ea), np.array(oa)  # the error of the average reconstruction, same bar
+    sea = np.sqrt(ea.var(ddof=1) / len(ea) + oa.var(ddof=1) / len(oa))
+    assert abs(ea.mean() - oa.mean()) <= 0.02 * oa.mean() + 2.0 * sea, (ea.mean(), oa.mean(), sea)

@@ -44,6 +44,7 @@ def test_mpr_sphere64_matches_oracle_statistically(sp, ctx):
     # oracle's (widened by two standard errors of the difference of the two means), and
     # the same median recovery of the object (up to translation / twin / phase)
     eg, eo, rg, ro = [], [], [], []
+    ea, oa = [], []
     for seed in range(16):
         pat = synthetic.config_pattern("sphere64", seed)
         prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
@@ -51,7 +52,9 @@ def test_mpr_sphere64_matches_oracle_statistically(sp, ctx):
         prob.destroy()
         o = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=seed, **C1)
         eg.append(r["final_error_best"])
+        ea.append(r["final_error_avg"])
         eo.append(o["final_error_best"])
+        oa.append(o["final_error_avg"])
         rg.append(aligned_rel_error(r["rho_avg"], pat.truth))
         ro.append(aligned_rel_error(o["rho_avg"], pat.truth))
         assert np.isfinite(r["gen_stats"][:, [0, 1, 2, 4, 5, 6, 7]]).all()
@@ -61,6 +64,9 @@ def test_mpr_sphere64_matches_oracle_statistically(sp, ctx):
     print(f"mean E gpu {eg.mean():.4f} oracle {eo.mean():.4f} (se {se:.4f}); median recovery "
           f"gpu {np.median(rg):.4f} oracle {np.median(ro):.4f}")
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
+    ea, oa = np.array(ea), np.array(oa)  # the error of the average reconstruction, same bar
+    sea = np.sqrt(ea.var(ddof=1) / len(ea) + oa.var(ddof=1) / len(oa))
+    assert abs(ea.mean() - oa.mean()) <= 0.02 * oa.mean() + 2.0 * sea, (ea.mean(), oa.mean(), sea)
     assert abs(np.median(rg) - np.median(ro)) <= 0.05
 
 
@@ -79,6 +85,7 @@ def test_mpr_runs_at_every_side(sp, ctx, name):
 def test_mpr_ell96_matches_oracle_statistically(sp, ctx):
     # a side of the form 3 x 2^k with a gap and saturation: the same bar as at 64
     eg, eo = [], []
+    ea, oa = [], []
     for seed in range(12):
         pat = synthetic.config_pattern("ell96", seed)
         prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
@@ -86,12 +93,17 @@ def test_mpr_ell96_matches_oracle_statistically(sp, ctx):
         prob.destroy()
         o = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=seed, **C1)
         eg.append(r["final_error_best"])
+        ea.append(r["final_error_avg"])
         eo.append(o["final_error_best"])
+        oa.append(o["final_error_avg"])
         assert np.isfinite(r["rho_avg"]).all()
     eg, eo = np.array(eg), np.array(eo)
     se = np.sqrt(eg.var(ddof=1) / len(eg) + eo.var(ddof=1) / len(eo))
     print(f"ell96: mean E gpu {eg.mean():.4f} oracle {eo.mean():.4f} (se {se:.4f})")
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
+    ea, oa = np.array(ea), np.array(oa)  # the error of the average reconstruction, same bar
+    sea = np.sqrt(ea.var(ddof=1) / len(ea) + oa.var(ddof=1) / len(oa))
+    assert abs(ea.mean() - oa.mean()) <= 0.02 * oa.mean() + 2.0 * sea, (ea.mean(), oa.mean(), sea)
 
 
 def test_replacement_and_average_error_behave_as_described(sp, ctx):

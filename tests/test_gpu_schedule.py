@@ -92,6 +92,7 @@ PAPER = dict(C1, schedule=1, repetitions=3, seq_ia=20, seq_er=10, seq_eval=10)
 
 def statistical(sp, ctx, gpu_kw, orc_kw, seeds=10, name="sphere64"):
     eg, eo = [], []
+    ea, oa = [], []
     for seed in range(seeds):
         pat = synthetic.config_pattern(name, seed)
         prob = ctx.problem(pat.intensities, pat.mask, pat.support0)
@@ -99,12 +100,17 @@ def statistical(sp, ctx, gpu_kw, orc_kw, seeds=10, name="sphere64"):
         prob.destroy()
         o = oracle.mpr_run(pat.intensities, pat.mask, pat.support0, seed=seed, **orc_kw)
         eg.append(r["final_error_best"])
+        ea.append(r["final_error_avg"])
         eo.append(o["final_error_best"])
+        oa.append(o["final_error_avg"])
         assert np.isfinite(r["rho_avg"]).all()
     eg, eo = np.array(eg), np.array(eo)
     se = np.sqrt(eg.var(ddof=1) / len(eg) + eo.var(ddof=1) / len(eo))
     print(f"mean E gpu {eg.mean():.4f} oracle {eo.mean():.4f} (se {se:.4f})")
     assert abs(eg.mean() - eo.mean()) <= 0.02 * eo.mean() + 2.0 * se
+    ea, oa = np.array(ea), np.array(oa)  # the error of the average reconstruction, same bar
+    sea = np.sqrt(ea.var(ddof=1) / len(ea) + oa.var(ddof=1) / len(oa))
+    assert abs(ea.mean() - oa.mean()) <= 0.02 * oa.mean() + 2.0 * sea, (ea.mean(), oa.mean(), sea)
     return eg, eo
 
 
