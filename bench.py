@@ -396,10 +396,10 @@ def run_ours(args, wl):
         other = kst[spring.KC_COL_PM if kc == spring.KC_ROW_ITER else spring.KC_ROW_ITER]
         oavg = other.total_ms / max(1, other.timed)
         # the kernels behind the two iteration classes depend on the path the side runs:
-        # two passes (k_row / k_col*), split passes (k_row_split / k_col_split), split with
-        # packed rows (k_row_split_pk / k_col_split); DRAM traffic is keyed the same way
+        # two passes (k_row / k_col*) or split passes (at 512: k_row_pair / k_col_split);
+        # DRAM traffic is keyed the same way
         path = spring.get_iteration_path(n)
-        knames = {2: ("row_split", "col_split"), 3: ("row_split_pk", "col_split")}.get(path, ("row_iter", "col_pm"))
+        knames = {2: ("row_split", "col_split")}.get(path, ("row_iter", "col_pm"))
         traffic = None
         prof = ROOT / "profiles" / "traffic.json"
         if prof.exists():

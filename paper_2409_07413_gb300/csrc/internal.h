@@ -14,11 +14,10 @@ namespace spring {
 bool split_supported(int n);
 spring_status launch_split_modulus(int n, const float* M, float* Mp, int K, cudaStream_t s);
 spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2* x, const uint32_t* Sb,
-                               long long batch, float beta, float chi, cudaStream_t s, bool packed = false);
+                               long long batch, float beta, float chi, cudaStream_t s);
 spring_status launch_col_split(int n, float2* w, const float* Mp, int batch, cudaStream_t s, int m_group = 0);
 spring_status iterate_split(int n, int alg, float2* w, float2* x, const uint32_t* Sb, const float* Mp,
-                            long long batch, int m_group, float beta, float chi, int k, cudaStream_t s,
-                            bool packed = false);
+                            long long batch, int m_group, float beta, float chi, int k, cudaStream_t s);
 // Sb: the supports packed to one bit per pixel (launch_pack_support)
 spring_status launch_pack_support(const uint8_t* S, uint32_t* Sb, long long npix, cudaStream_t s);
 spring_status launch_row_iter(int n, int alg, float2* w, float2* x, const uint32_t* Sb,

@@ -50,8 +50,7 @@ static int g_col_var[N_SIDES] = {0, 1, 2, 1, 0, 0, 0, 1, 1};
 static bool g_tuned[N_SIDES] = {};
 // iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
 // (N <= 256, k_cluster.cu), 2 = the split passes (N = 512, 1024: the column transform's
-// first stage in the row pass), 3 = the split passes with the row transforms on packed
-// pairs of rows; chosen by the autotuner, the two-pass path until then
+// first stage in the row pass); chosen by the autotuner, the two-pass path until then
 static int g_path[N_SIDES] = {};
 
 int iteration_path(int n) {
@@ -333,13 +332,13 @@ bool split_supported(int n) { return split_side(n); }
 
 // the modulus in the split column pass's chunked layout: row k2 L + k1 of Mp is row
 // Q k1 + k2 of M (K arrays of n x n)
-__global__ void k_split_modulus(const float* __restrict__ M, float* __restrict__ Mp, int n, long long total) {
-  const int L = n / SPLIT_Q;
+__global__ void k_split_modulus(const float* __restrict__ M, float* __restrict__ Mp, int n, int Q, long long total) {
+  const int L = n / Q;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long nn = (long long)n * n, q = i / nn, r = (i / n) % n, c = i % n;
     const long long k2 = r / L, k1 = r % L;
-    Mp[i] = M[q * nn + (SPLIT_Q * k1 + k2) * n + c];
+    Mp[i] = M[q * nn + (Q * k1 + k2) * n + c];
   }
 }
 
@@ -348,16 +347,15 @@ spring_status launch_split_modulus(int n, const float* M, float* Mp, int K, cuda
   const long long total = (long long)K * n * n;
   const long long blocks = div_up(total, 256) < 16LL * sm_count() ? div_up(total, 256) : 16LL * sm_count();
   launch_begin(SPRING_KC_OTHER, s);
-  k_split_modulus<<<(int)blocks, 256, 0, s>>>(M, Mp, n, total);
+  k_split_modulus<<<(int)blocks, 256, 0, s>>>(M, Mp, n, split_q_of(n), total);
   SPRING_CHECK_LAUNCH();
   launch_end(SPRING_KC_OTHER, s, (double)total * 8.0);
   return SPRING_OK;
 }
 
-// the split row pass: fwd_only = the forward row transforms and first stage from x alone;
-// packed = the iteration's row transforms on packed pairs of rows (k_row_split_pk)
+// the split row pass: fwd_only = the forward row transforms and first stage from x alone
 spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2* x, const uint32_t* Sb,
-                               long long batch, float beta, float chi, cudaStream_t s, bool packed) {
+                               long long batch, float beta, float chi, cudaStream_t s) {
   if (!split_side(n)) return invalid("the split passes cover sides 512 and 1024");
   if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
   DeviceTables tb;
@@ -365,13 +363,12 @@ spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2*
   FftOp op;
   op.kind = fwd_only ? OP_ROW_SPLIT_FWD : OP_ROW_SPLIT;
   op.alg = alg;
-  op.variant = (packed && !fwd_only) ? 1 : 0;
   op.kclass = fwd_only ? SPRING_KC_OTHER : SPRING_KC_ROW_ITER;
   op.sa.w = w;
   op.sa.x = x;
   op.sa.Sb = Sb;
   op.sa.tw = tb.tw + tw_offset(n);
-  op.sa.nsets = batch * (n / SPLIT_Q);
+  op.sa.nsets = batch * (n / split_q_of(n));
   op.sa.beta = beta;
   op.sa.chi_on = chi < 1.0f;
   op.sa.cchi = (float)((chi == 0.5f) ? 0.0 : std::cos((double)chi * 3.14159265358979323846));
@@ -389,7 +386,7 @@ spring_status launch_col_split(int n, float2* w, const float* Mp, int batch, cud
   op.kclass = SPRING_KC_COL_PM;
   op.ca.data = w;
   op.ca.M = Mp;
-  op.ca.tw = tb.tw + tw_offset(n / SPLIT_Q);
+  op.ca.tw = tb.tw + tw_offset(n / split_q_of(n));
   op.ca.batch = batch;
   op.ca.m_group = m_group;
   const double nm = m_group > 0 ? (double)((batch + m_group - 1) / m_group) : 1.0;
@@ -400,12 +397,11 @@ spring_status launch_col_split(int n, float2* w, const float* Mp, int batch, cud
 // k iterations (column pass, then row pass) in the split form; w must hold the chunked
 // forward spectra of x (launch_row_split with fwd_only) on entry and holds them on exit
 spring_status iterate_split(int n, int alg, float2* w, float2* x, const uint32_t* Sb, const float* Mp,
-                            long long batch, int m_group, float beta, float chi, int k, cudaStream_t s,
-                            bool packed) {
+                            long long batch, int m_group, float beta, float chi, int k, cudaStream_t s) {
   if (batch > INT32_MAX) return invalid("batch too large");
   for (int it = 0; it < k; ++it) {
     SPRING_TRY(launch_col_split(n, w, Mp, (int)batch, s, m_group));
-    SPRING_TRY(launch_row_split(n, alg, false, w, x, Sb, batch, beta, chi, s, packed));
+    SPRING_TRY(launch_row_split(n, alg, false, w, x, Sb, batch, beta, chi, s));
   }
   return SPRING_OK;
 }
@@ -646,12 +642,8 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
     SPRING_CUDA(cudaEventCreate(&e2));
     spring_status st = dispatch(n, cop, s);  // warm-up of both forms
     if (st == SPRING_OK) st = dispatch(n, op, s);
-    cudaEvent_t e3;
-    SPRING_CUDA(cudaEventCreate(&e3));
     if (st == SPRING_OK) st = launch_row_split(n, 2, true, w, x, nullptr, batch, 0.9f, 0.5f, s);
     if (st == SPRING_OK) st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, 1, s);
-    if (st == SPRING_OK)
-      st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, 1, s, true);
     cudaEventRecord(e0, s);
     for (int k = 0; k < K && st == SPRING_OK; ++k) {
       st = dispatch(n, cop, s);
@@ -660,21 +652,15 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
     cudaEventRecord(e1, s);
     if (st == SPRING_OK) st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, K, s);
     cudaEventRecord(e2, s);
-    if (st == SPRING_OK)
-      st = iterate_split(n, 2, w, x, bits.as<uint32_t>(), mp.as<float>(), batch, 0, 0.9f, 0.5f, K, s, true);
-    cudaEventRecord(e3, s);
-    cudaEventSynchronize(e3);
-    float two = 0.f, split = 0.f, split_pk = 0.f;
+    cudaEventSynchronize(e2);
+    float two = 0.f, split = 0.f;
     cudaEventElapsedTime(&two, e0, e1);
     cudaEventElapsedTime(&split, e1, e2);
-    cudaEventElapsedTime(&split_pk, e2, e3);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
-    cudaEventDestroy(e3);
     SPRING_TRY(st);
-    if (split < two && split <= split_pk) path = 2;
-    else if (split_pk < two) path = 3;
+    if (split < two) path = 2;
   }
   std::lock_guard<std::mutex> lk(g_var_mu);
   g_row_var[si] = best_r;
@@ -733,9 +719,8 @@ spring_status spring_autotune(int n, int batch, void* stream) {
 spring_status spring_set_iteration_path(int n, int path) {
   const int si = side_index(n);
   if (si < 0) return invalid("unsupported pattern side");
-  if (path < 0 || path > 3)
-    return invalid("path must be 0 (two passes), 1 (on chip), 2 (split passes) or 3 (split, packed rows)");
-  if (path >= 2 && !split_side(n)) return invalid("the split passes cover sides 512 and 1024");
+  if (path < 0 || path > 2) return invalid("path must be 0 (two passes), 1 (on chip) or 2 (split passes)");
+  if (path == 2 && !split_side(n)) return invalid("the split passes cover sides 512 and 1024");
   if (path == 1) {
     bool ok = false;
     SPRING_TRY(cluster_supported(n, &ok));

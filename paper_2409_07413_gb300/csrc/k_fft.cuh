@@ -432,25 +432,30 @@ __global__ void __launch_bounds__(W * P::T, MINB) k_col(ColArgs a) {
 }
 
 // ------------------------------------------------------------------ split passes
-// The column transform of length N = Q L (Q = 8) by decimation in frequency over the rows,
+// The column transform of length N = Q L by decimation in frequency over the rows,
 // n = n1 + L n2: its first radix-Q stage combines the Q rows n1, n1 + L, ..., n1 + (Q - 1) L,
 // y[n1][k2] = W_N^{n1 k2} sum_{n2} x[n1 + L n2] W_Q^{n2 k2}, and the L-point transform of
 // y[.][k2] over n1 gives the full transform at the rows Q k1 + k2.  So the row pass of an
-// iteration, which holds the Q rows of a set n1 anyway, also runs that first stage (and,
-// on its way in, the inverse one), and the column pass transforms L-row chunks: chunk k2
-// holds y[n1][k2] at rows k2 L + n1 (the chunked layout of w), and its modulus values
-// come from a copy of M permuted to the same layout (row k2 L + k1 of it holds row
-// Q k1 + k2 of M).  The arithmetic is the same unnormalised 2D transform pair as the two
-// passes', in another order of summation.  This moves a third of the column pass's
-// transform work into the row pass, whose time is set by HBM rather than by issue.
-constexpr int SPLIT_Q = 8;
+// iteration, which transforms those rows anyway, also runs that first stage (and, on its
+// way in, the inverse one), and the column pass transforms L-row chunks: chunk k2 holds
+// y[n1][k2] at rows k2 L + n1 (the chunked layout of w), and its modulus values come from
+// a copy of M permuted to the same layout (row k2 L + k1 of it holds row Q k1 + k2 of M).
+// The arithmetic is the same unnormalised 2D transform pair as the two passes', in another
+// order of summation.  The column pass, bound by issue rather than HBM, gets shorter
+// transforms; the row pass, bound by HBM, takes the first stage.
+// Q per side: 512 = 2 x 256 (the column pass keeps 256-point transforms of one exchange, the
+// row pass only a butterfly per pixel pair), 1024 = 8 x 128
+template <int N> __host__ __device__ constexpr int split_q() { return N == 512 ? 2 : 8; }
+__host__ __device__ constexpr int split_q_of(int n) { return n == 512 ? 2 : 8; }
 
 template <int N> struct SplitRowPlan : RowAltPlan<N> {};  // row transforms of a split row pass
-// blocks of a split row pass per SM the register budget is sized for (512: 2, 64 registers;
-// 1024's 16-element rows keep one block and their registers)
-template <int N> constexpr int split_row_minb() { return N <= 512 ? 2 : 1; }
+// blocks of a split row pass per SM the register budget is sized for (Q = 2 at 512:
+// 128-thread blocks, eight per SM at 64 registers; 1024's sets of 8 rows of 16-element
+// transforms keep one 512-thread block and their registers)
+template <int N> __host__ __device__ constexpr int split_row_minb() { return N <= 512 ? 8 : 1; }
 constexpr bool split_side(int n) { return n == 512 || n == 1024; }
-constexpr int SPLIT_COL_W = 32;  // columns per tile of the split column pass
+// columns per tile of the split column pass: 16 for 256-point chunks, 32 for shorter
+template <int L> __host__ __device__ constexpr int split_col_w() { return L >= 256 ? 16 : 32; }
 
 struct SplitArgs {
   float2* w;           // chunked spectra of the batch (N x N per image)
@@ -474,7 +479,8 @@ struct FftOp {
 // staged, the next set's Q spectra rows, the set's Q x rows and its Q rows of support words
 template <class P, bool STAGE>
 __host__ __device__ constexpr size_t split_row_elems() {
-  return (size_t)SPLIT_Q * pad_elems_p<P>() + (STAGE ? (size_t)2 * SPLIT_Q * P::N + SPLIT_Q * P::N / 64 : 0);
+  constexpr int Q = split_q<P::N>();
+  return (size_t)Q * pad_elems_p<P>() + (STAGE ? (size_t)2 * Q * P::N + Q * P::N / 64 : 0);
 }
 
 // A block of Q T threads per set of Q rows n1 + L n2: lane group n2 transforms row
@@ -486,8 +492,8 @@ __host__ __device__ constexpr size_t split_row_elems() {
 // and support words while its inverse row transforms run -- so no load waits in line with
 // the arithmetic.
 template <class P, int MODE, int ALG, bool STAGE>
-__global__ void __launch_bounds__(SPLIT_Q * P::T, split_row_minb<P::N>()) k_row_split(SplitArgs a) {
-  constexpr int N = P::N, E = P::E, T = P::T, Q = SPLIT_Q, L = N / Q, TH = Q * T, RS = pad_elems_p<P>();
+__global__ void __launch_bounds__(split_q<P::N>() * P::T, split_row_minb<P::N>()) k_row_split(SplitArgs a) {
+  constexpr int N = P::N, E = P::E, T = P::T, Q = split_q<N>(), L = N / Q, TH = Q * T, RS = pad_elems_p<P>();
   constexpr int CPT = N / TH;  // columns per thread in the first stages
   static_assert(N % TH == 0 && RS >= N, "a column per thread group, rows fit their exchange areas");
   static_assert(!STAGE || MODE == ROW_ITER, "staging serves the iteration");
@@ -597,131 +603,90 @@ __global__ void __launch_bounds__(SPLIT_Q * P::T, split_row_minb<P::N>()) k_row_
   }
 }
 
-// Blocks of a packed split row pass per SM the register budget is sized for
-template <int N> constexpr int split_row_pk_minb() { return N <= 512 ? 2 : 1; }
-// shared-memory float2 elements of a packed split row pass block (always staged)
-template <class P>
-__host__ __device__ constexpr size_t split_row_pk_elems() {
-  return (size_t)SPLIT_Q * pad_elems_p<P>() + (size_t)2 * SPLIT_Q * P::N + SPLIT_Q * P::N / 64;
-}
-
-// The split row pass (ROW_ITER) on packed pairs: lane group g < Q/2 carries rows n1 + L g
-// (lane 0) and n1 + L (g + Q/2) (lane 1) through one packed transform, so each step of the
-// two rows' transforms is one two-lane instruction and each exchange a 16-byte access.
-// The cross-row first stages stay scalar, one column at a time; the update is taken lane by
-// lane.  Staged and persistent like k_row_split<..., STAGE = true>; the same arithmetic per
-// row as the packed transforms (cpk) of the same plan.
-template <class P, int ALG>
-__global__ void __launch_bounds__(SPLIT_Q / 2 * P::T, split_row_pk_minb<P::N>()) k_row_split_pk(SplitArgs a) {
-  constexpr int N = P::N, E = P::E, T = P::T, Q = SPLIT_Q, H = Q / 2, L = N / Q, TH = H * T;
-  constexpr int RS = pad_elems_p<P>(), CPT = N / TH, NW = N / 32;
-  static_assert(N % TH == 0 && RS >= N && N % 128 == 0 && (Q * N / 2) % TH == 0, "packed split row tiling");
-  extern __shared__ __align__(16) float2 smem[];
-  cpk* R = reinterpret_cast<cpk*>(smem);                   // H exchange areas of RS pairs
-  float2* Ws = smem + (size_t)Q * RS;                      // spectra rows k2 L + n1 of the set
-  float2* Xs = Ws + Q * N;                                 // the set's x rows
-  uint32_t* Bs = reinterpret_cast<uint32_t*>(Xs + Q * N);  // their support words
-  const int tid = threadIdx.x, grp = tid / T, t = tid % T;
-  const auto gsync = GroupSync<T>::make();
-  auto stage_w = [&](long long set) {
-    if (set < a.nsets) {
-      const float2* src = a.w + (set / L) * N * N + (set % L) * N;
-#pragma unroll
-      for (int i = 0; i < Q * N / 2 / TH; ++i) {
-        const int k = tid + i * TH, k2 = k / (N / 2), q = k % (N / 2);
-        cp_async16(Ws + k2 * N + 2 * q, src + (long long)k2 * L * N + 2 * q);
-      }
-    }
-    cp_async_commit();
-  };
-  stage_w(blockIdx.x);
-  cp_async_wait_all();
-  __syncthreads();
-  for (long long set = blockIdx.x; set < a.nsets; set += gridDim.x) {
+// The split row pass for Q = 2 with both rows of a set in one lane group: rows n1 and
+// n1 + L (L = N / 2) are read at the same columns, so the column transform's first radix-2
+// stage and its inverse run in registers, and the two row transforms follow one another
+// through the group's exchange area.  No shared-memory transposes and no block barriers:
+// ROW_THREADS threads per block, one set per lane group.  The arithmetic is that of
+// k_row_split with Q = 2 (a twiddle W_N^{n1} per set, then an add and a subtract).
+template <class P, int MODE, int ALG, int MINB>
+__global__ void __launch_bounds__(ROW_THREADS, MINB) k_row_pair(SplitArgs a) {
+  constexpr int N = P::N, E = P::E, T = P::T, G = ROW_THREADS / T, L = N / 2, SME = pad_elems_p<P>();
+  static_assert(split_q<N>() == 2 && E * T == N && G * T == ROW_THREADS, "a pair of rows per lane group");
+  extern __shared__ float2 smem[];
+  const int grp = threadIdx.x / T, t = threadIdx.x % T;
+  float2* sm = smem + grp * SME;
+  // each thread's own elements of the row that waits: row b's input while row a is processed,
+  // then row a's result while row b is
+  float2* hold = smem + G * SME + grp * N;
+  const auto sync = GroupSync<T>::make();
+  for (long long set = (long long)blockIdx.x * G + grp; set < a.nsets; set += (long long)gridDim.x * G) {
     const long long img = set / L;
     const int n1 = (int)(set % L);
     float2* wi = a.w + img * N * N;
     float2* xi = a.x + img * N * N;
-    const long long xrow0 = (long long)(n1 + L * grp) * N, xrow1 = (long long)(n1 + L * (grp + H)) * N;
+    const long long ra = (long long)n1 * N, rb = (long long)(n1 + L) * N;  // x rows = chunk rows
+    const float2 wt = __ldg(&a.tw[n1]);  // W_N^{n1}
+    float2 va[E], vb[E];
+    if constexpr (MODE == ROW_ITER) {
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) {  // inverse first stage of column c, into the pairs
-      const int c = tid + j * TH;
-      float2 z[Q];
+      for (int m = 0; m < E; ++m) {  // inverse first stage
+        const float2 y0 = wi[ra + t + m * T], y1 = cmul(wi[rb + t + m * T], cconj(wt));
+        va[m] = cadd(y0, y1);
+        vb[m] = csub(y0, y1);
+      }
+      // row r of x: inverse transform (m = P_M x_n), update, forward transform
+      auto iterate_row = [&](float2 (&v)[E], long long r) {
+        fft_plan<P, +1, true, 1>(v, sm, t, a.tw, sync);
+        const uint32_t* srow = a.Sb + (img * N * N + r) / 32;
+        uint32_t sw[E];
+        float2 xo[E];
 #pragma unroll
-      for (int k2 = 0; k2 < Q; ++k2) z[k2] = Ws[k2 * N + c];
-#pragma unroll
-      for (int k2 = 1; k2 < Q; ++k2) z[k2] = cmul(z[k2], cconj(__ldg(&a.tw[n1 * k2])));
-      DFT<Q, +1>::run(z);
-#pragma unroll
-      for (int g = 0; g < H; ++g) R[g * RS + c] = cpk{make_float2(z[g].x, z[g + H].x), make_float2(z[g].y, z[g + H].y)};
-    }
-    __syncthreads();
-    {  // the group's two x rows and their support words, then the next set's spectra
-      const uint32_t* s0 = a.Sb + (img * N * N + xrow0) / 32;
-      const uint32_t* s1 = a.Sb + (img * N * N + xrow1) / 32;
-      if constexpr (ALG != 0) {
-#pragma unroll
-        for (int i = 0; i < N / 2 / T; ++i) {
-          cp_async16(Xs + grp * N + 2 * (t + i * T), xi + xrow0 + 2 * (t + i * T));
-          cp_async16(Xs + (grp + H) * N + 2 * (t + i * T), xi + xrow1 + 2 * (t + i * T));
+        for (int m = 0; m < E; ++m) {
+          sw[m] = srow[(t + m * T) >> 5];
+          if (ALG != 0) xo[m] = xi[r + t + m * T];
         }
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const float2 pm = v[m];
+          bool in_c = support_bit(sw[m], t + m * T);
+          if (a.chi_on) in_c = in_c && (pm.x >= a.cchi * sqrtf(pm.x * pm.x + pm.y * pm.y));
+          const float2 xn = update_pixel(ALG, ALG ? xo[m] : pm, pm, in_c, a.beta);
+          v[m] = xn;
+          xi[r + t + m * T] = xn;
+        }
+        fft_plan<P, -1, true, 1>(v, sm, t, a.tw, sync);  // ends with the group's barrier
+      };
+#pragma unroll
+      for (int m = 0; m < E; ++m) hold[t + m * T] = vb[m];
+      iterate_row(va, ra);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        vb[m] = hold[t + m * T];
+        hold[t + m * T] = va[m];
       }
-      if (t < N / 128) {
-        cp_async16(Bs + grp * NW + 4 * t, s0 + 4 * t);
-        cp_async16(Bs + (grp + H) * NW + 4 * t, s1 + 4 * t);
+      iterate_row(vb, rb);
+#pragma unroll
+      for (int m = 0; m < E; ++m) va[m] = hold[t + m * T];
+    } else {  // ROW_FWD: the forward row transforms of x
+#pragma unroll
+      for (int m = 0; m < E; ++m) va[m] = xi[ra + t + m * T];
+      fft_plan<P, -1, true, 1>(va, sm, t, a.tw, sync);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        hold[t + m * T] = va[m];
+        vb[m] = xi[rb + t + m * T];
       }
-      cp_async_commit();
-      stage_w(set + gridDim.x);
+      fft_plan<P, -1, true, 1>(vb, sm, t, a.tw, sync);
+#pragma unroll
+      for (int m = 0; m < E; ++m) va[m] = hold[t + m * T];
     }
-    cpk v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = R[grp * RS + t + m * T];
-    gsync();                                                    // before the exchange writes
-    fft_plan<P, +1, true, 1>(v, R + grp * RS, t, a.tw, gsync);  // m = P_M x_n, both rows
-    cp_async_wait_group<1>();  // this set's x rows and words (the next set's spectra may fly)
-    gsync();
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int col = t + m * T;
-      const uint32_t w0 = Bs[grp * NW + (col >> 5)], w1 = Bs[(grp + H) * NW + (col >> 5)];
-      const float2 pm0 = make_float2(v[m].re.x, v[m].im.x), pm1 = make_float2(v[m].re.y, v[m].im.y);
-      bool c0 = support_bit(w0, col), c1 = support_bit(w1, col);
-      if (a.chi_on) {
-        c0 = c0 && (pm0.x >= a.cchi * sqrtf(pm0.x * pm0.x + pm0.y * pm0.y));
-        c1 = c1 && (pm1.x >= a.cchi * sqrtf(pm1.x * pm1.x + pm1.y * pm1.y));
-      }
-      float2 xo0 = pm0, xo1 = pm1;
-      if (ALG != 0) {
-        xo0 = Xs[grp * N + col];
-        xo1 = Xs[(grp + H) * N + col];
-      }
-      const float2 x0 = update_pixel(ALG, xo0, pm0, c0, a.beta), x1 = update_pixel(ALG, xo1, pm1, c1, a.beta);
-      xi[xrow0 + col] = x0;
-      xi[xrow1 + col] = x1;
-      v[m] = cpk{make_float2(x0.x, x1.x), make_float2(x0.y, x1.y)};
+    for (int m = 0; m < E; ++m) {  // forward first stage, into the chunks
+      const float2 y0 = cadd(va[m], vb[m]), y1 = cmul(csub(va[m], vb[m]), wt);
+      wi[ra + t + m * T] = y0;
+      wi[rb + t + m * T] = y1;
     }
-    fft_plan<P, -1, true, 1>(v, R + grp * RS, t, a.tw, gsync);  // ends with the group's barrier
-#pragma unroll
-    for (int m = 0; m < E; ++m) R[grp * RS + t + m * T] = v[m];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < CPT; ++j) {  // forward first stage of column c, from the pairs
-      const int c = tid + j * TH;
-      float2 y[Q];
-#pragma unroll
-      for (int g = 0; g < H; ++g) {
-        const cpk q = R[g * RS + c];
-        y[g] = make_float2(q.re.x, q.im.x);
-        y[g + H] = make_float2(q.re.y, q.im.y);
-      }
-      DFT<Q, -1>::run(y);
-#pragma unroll
-      for (int k2 = 1; k2 < Q; ++k2) y[k2] = cmul(y[k2], __ldg(&a.tw[n1 * k2]));
-#pragma unroll
-      for (int k2 = 0; k2 < Q; ++k2) wi[(long long)(k2 * L + n1) * N + c] = y[k2];
-    }
-    cp_async_wait_all();  // the next set's spectra rows
-    __syncthreads();      // R, Ws, Xs and Bs are written again for the next set
   }
 }
 
@@ -731,7 +696,7 @@ __global__ void __launch_bounds__(SPLIT_Q / 2 * P::T, split_row_pk_minb<P::N>())
 template <class PL, int N, int W>
 __global__ void __launch_bounds__(W * PL::T, 2) k_col_split(ColArgs a) {
   constexpr int L = PL::N, E = PL::E, T = PL::T, Q = N / L, STRIPS = N / W, CH = W / 4;
-  static_assert(Q == SPLIT_Q && W % 4 == 0 && N % W == 0, "split column tile");
+  static_assert(Q == split_q<N>() && W % 4 == 0 && N % W == 0, "split column tile");
   extern __shared__ float2 smem[];
   float* Ms = reinterpret_cast<float*>(smem + (size_t)L * W);
   const int c = threadIdx.x % W, t = threadIdx.x / W;
@@ -1080,25 +1045,19 @@ inline spring_status col_pm_tma_launch(const FftOp& op, cudaStream_t s, bool pre
   return SPRING_OK;
 }
 
-template <int N, int ALG>
-inline spring_status row_split_pk_launch(const FftOp& op, cudaStream_t s, bool prep) {
+template <int N, int MODE, int ALG>
+inline spring_status row_pair_launch(const FftOp& op, cudaStream_t s, bool prep) {
   using P = SplitRowPlan<N>;
-  constexpr int TH = SPLIT_Q / 2 * P::T;
-  const size_t smem = split_row_pk_elems<P>() * sizeof(float2);
-  auto kern = k_row_split_pk<P, ALG>;
+  constexpr int G = ROW_THREADS / P::T;
+  const size_t smem = (size_t)G * (pad_elems_p<P>() + P::N) * sizeof(float2);
+  auto kern = k_row_pair<P, MODE, ALG, MODE == ROW_ITER ? 4 : 3>;
   if (prep) return allow_smem(kern, smem);
-  const long long sets = op.sa.nsets;
-  if (sets < 1) return SPRING_OK;
-  if ((reinterpret_cast<uintptr_t>(op.sa.w) | reinterpret_cast<uintptr_t>(op.sa.x) |
-       reinterpret_cast<uintptr_t>(op.sa.Sb)) & 15u)
-    return invalid("the split row pass stages from 16-byte aligned w, x and support bits");
-  int per_sm = 0;
-  SPRING_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TH, smem));
-  if (per_sm < 1) return invalid("split row pass does not fit an SM");
-  const long long cap = (long long)per_sm * sm_count();  // persistent
-  const int blocks = (int)(sets < cap ? sets : cap);
+  long long blocks = (op.sa.nsets + G - 1) / G;
+  const long long cap = 64LL * sm_count();
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
-  kern<<<blocks, TH, smem, s>>>(op.sa);
+  kern<<<(int)blocks, ROW_THREADS, smem, s>>>(op.sa);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;
@@ -1106,42 +1065,42 @@ inline spring_status row_split_pk_launch(const FftOp& op, cudaStream_t s, bool p
 
 template <int N, int MODE, int ALG>
 inline spring_status row_split_launch(const FftOp& op, cudaStream_t s, bool prep) {
-  if constexpr (MODE == ROW_ITER) {
-    if (prep) SPRING_TRY((row_split_pk_launch<N, ALG>(op, s, true)));
-    else if (op.variant == 1) return row_split_pk_launch<N, ALG>(op, s, false);
+  if constexpr (split_q<N>() == 2) {  // pairs of rows in one lane group
+    return row_pair_launch<N, MODE, ALG>(op, s, prep);
+  } else {
+    using P = SplitRowPlan<N>;
+    constexpr bool STAGE = MODE == ROW_ITER;
+    const size_t smem = split_row_elems<P, STAGE>() * sizeof(float2);
+    auto kern = k_row_split<P, MODE, ALG, STAGE>;
+    if (prep) return allow_smem(kern, smem);
+    const long long sets = op.sa.nsets;
+    if (sets < 1) return SPRING_OK;
+    if (STAGE && ((reinterpret_cast<uintptr_t>(op.sa.w) | reinterpret_cast<uintptr_t>(op.sa.x) |
+                   reinterpret_cast<uintptr_t>(op.sa.Sb)) & 15u))
+      return invalid("the split row pass stages from 16-byte aligned w, x and support bits");
+    int per_sm = 0;
+    SPRING_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, split_q<N>() * P::T, smem));
+    if (per_sm < 1) return invalid("split row pass does not fit an SM");
+    const long long cap = (long long)per_sm * sm_count() * (STAGE ? 1 : 4);  // staged: persistent
+    const int blocks = (int)(sets < cap ? sets : cap);
+    launch_begin(op.kclass, s);
+    kern<<<blocks, split_q<N>() * P::T, smem, s>>>(op.sa);
+    SPRING_CHECK_LAUNCH();
+    launch_end(op.kclass, s, op.bytes);
+    return SPRING_OK;
   }
-  using P = SplitRowPlan<N>;
-  constexpr bool STAGE = MODE == ROW_ITER;
-  const size_t smem = split_row_elems<P, STAGE>() * sizeof(float2);
-  auto kern = k_row_split<P, MODE, ALG, STAGE>;
-  if (prep) return allow_smem(kern, smem);
-  const long long sets = op.sa.nsets;
-  if (sets < 1) return SPRING_OK;
-  if (STAGE && ((reinterpret_cast<uintptr_t>(op.sa.w) | reinterpret_cast<uintptr_t>(op.sa.x) |
-                 reinterpret_cast<uintptr_t>(op.sa.Sb)) & 15u))
-    return invalid("the split row pass stages from 16-byte aligned w, x and support bits");
-  int per_sm = 0;
-  SPRING_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPLIT_Q * P::T, smem));
-  if (per_sm < 1) return invalid("split row pass does not fit an SM");
-  const long long cap = (long long)per_sm * sm_count() * (STAGE ? 1 : 4);  // staged: persistent
-  const int blocks = (int)(sets < cap ? sets : cap);
-  launch_begin(op.kclass, s);
-  kern<<<blocks, SPLIT_Q * P::T, smem, s>>>(op.sa);
-  SPRING_CHECK_LAUNCH();
-  launch_end(op.kclass, s, op.bytes);
-  return SPRING_OK;
 }
 
 template <int N>
 inline spring_status col_split_launch(const FftOp& op, cudaStream_t s, bool prep) {
-  using PL = Plan<N / SPLIT_Q>;
-  constexpr int W = SPLIT_COL_W;
+  using PL = Plan<N / split_q<N>()>;
+  constexpr int W = split_col_w<PL::N>();
   const size_t smem = (size_t)PL::N * W * (sizeof(float2) + sizeof(float));
   auto kern = k_col_split<PL, N, W>;
   if (prep) return allow_smem(kern, smem);
   if (op.ca.batch < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
-  kern<<<op.ca.batch * SPLIT_Q * (N / W), W * PL::T, smem, s>>>(op.ca);
+  kern<<<op.ca.batch * split_q<N>() * (N / W), W * PL::T, smem, s>>>(op.ca);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;

@@ -385,13 +385,13 @@ class Run {
       z_valid = false;
       return SPRING_OK;
     }
-    if (path >= 2) {  // split passes: w holds the chunked spectra
+    if (path == 2) {  // split passes: w holds the chunked spectra
       if (!z_valid || z_path != 2) {
         SPRING_TRY(launch_row_split(n, 0, true, w, x, nullptr, NBT, prm.beta, prm.chi, s));
         z_valid = true;
         z_path = 2;
       }
-      return iterate_split(n, alg, w, x, Sb, Msplit, NBT, mgroup, prm.beta, prm.chi, k, s, path == 3);
+      return iterate_split(n, alg, w, x, Sb, Msplit, NBT, mgroup, prm.beta, prm.chi, k, s);
     }
     if (!z_valid || z_path != 0) {
       SPRING_TRY(launch_row_fft(n, -1, x, w, nullptr, NBT, 1.0f, s));

@@ -361,8 +361,7 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
   cudaStream_t s = ST(stream);
   Scratch w;
   const size_t wbytes = sizeof(float2) * (size_t)batch * n * n, sbytes = ((size_t)batch * n * n / 8 + 255) & ~(size_t)255;
-  const int path = iteration_path(n);
-  const bool split = path >= 2;
+  const bool split = iteration_path(n) == 2;
   SPRING_TRY(w.alloc(wbytes + sbytes + (split ? sizeof(float) * (size_t)n * n : 0), s));
   uint32_t* Sb = reinterpret_cast<uint32_t*>(static_cast<char*>(w.p) + wbytes);
   SPRING_TRY(launch_pack_support(S, Sb, (long long)batch * n * n, s));
@@ -371,7 +370,7 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
     float* Mp = reinterpret_cast<float*>(static_cast<char*>(w.p) + wbytes + sbytes);
     SPRING_TRY(launch_split_modulus(n, M, Mp, 1, s));
     SPRING_TRY(launch_row_split(n, algorithm, true, w.as<float2>(), xs, nullptr, batch, beta, chi, s));
-    return iterate_split(n, algorithm, w.as<float2>(), xs, Sb, Mp, batch, 0, beta, chi, n_iter, s, path == 3);
+    return iterate_split(n, algorithm, w.as<float2>(), xs, Sb, Mp, batch, 0, beta, chi, n_iter, s);
   }
   SPRING_TRY(launch_row_fft(n, -1, xs, w.as<float2>(), nullptr, batch, 1.0f, s));
   for (int it = 0; it < n_iter; ++it) {

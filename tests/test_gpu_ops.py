@@ -415,15 +415,15 @@ def test_autotune_picks_a_valid_variant(sp):
 
 
 # ----------------------------------------------------------------------------- split passes
-@pytest.fixture(params=[2, 3], ids=["split", "split_packed"])
-def split_path(sp, request):
-    """The split passes (column transform's first stage in the row pass; path 3: the row
-    transforms on packed pairs of rows) for sides 512 and 1024, restoring each side's
-    iteration path afterwards."""
+@pytest.fixture
+def split_path(sp):
+    """The split passes (the column transform's first radix-Q stage in the row pass: Q = 2
+    at 512, pairs of rows in one lane group; Q = 8 at 1024) for sides 512 and 1024,
+    restoring each side's iteration path afterwards."""
     saved = {n: sp.get_iteration_path(n) for n in (512, 1024)}
     for n in saved:
-        sp.set_iteration_path(n, request.param)
-    yield request.param
+        sp.set_iteration_path(n, 2)
+    yield
     for n, p in saved.items():
         sp.set_iteration_path(n, p)
 
@@ -484,15 +484,15 @@ def test_split_iterate_many_sets_per_block(sp, split_path, n, B, alg):
 
 
 def test_iteration_path_arguments(sp):
-    # the split forms cover 512 and 1024 only; paths past 3 do not exist
+    # the split passes cover 512 and 1024 only; paths past 2 do not exist
     saved = sp.get_iteration_path(256), sp.get_iteration_path(512)
     try:
-        for n, path in ((256, 2), (256, 3), (512, 4), (512, -1)):
+        for n, path in ((256, 2), (512, 3), (512, -1)):
             with pytest.raises(sp.SpringError) as e:
                 sp.set_iteration_path(n, path)
             assert e.value.status == sp.E_INVALID
-        sp.set_iteration_path(512, 3)
-        assert sp.get_iteration_path(512) == 3
+        sp.set_iteration_path(512, 2)
+        assert sp.get_iteration_path(512) == 2
     finally:
         sp.set_iteration_path(256, saved[0])
         sp.set_iteration_path(512, saved[1])
