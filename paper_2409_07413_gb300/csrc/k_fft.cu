@@ -50,8 +50,9 @@ static int g_col_var[N_SIDES] = {0, 1, 2, 1, 0, 0, 0, 1, 1};
 static bool g_tuned[N_SIDES] = {};
 // iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
 // (N <= 256, k_cluster.cu), 2 = the split passes (N = 512, 1024: the column transform's
-// first stage in the row pass); chosen by the autotuner, the two-pass path until then
-static int g_path[N_SIDES] = {};
+// first stage in the row pass); chosen by the autotuner, until then the fastest measured
+// on a GB300 (the split passes at 512 and 1024)
+static int g_path[N_SIDES] = {0, 0, 0, 0, 0, 0, 2, 0, 2};
 
 int iteration_path(int n) {
   const int si = side_index(n);

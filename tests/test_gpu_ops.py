@@ -377,9 +377,10 @@ def test_kernel_variants_parity(sp, n):
     x, S = synthetic.population_state(7 * n, B, n, support_frac=0.3)
     M, mask = synthetic.random_modulus(7 * n, n, masked_frac=0.1)
     ref = oracle.iterate(c64(x), S, *as_oracle_M(M, mask), 2, 0.9, 1.0, 1)
-    saved = sp.get_kernel_variant(n)
+    saved, spath = sp.get_kernel_variant(n), sp.get_iteration_path(n)
     out = {}
     try:
+        sp.set_iteration_path(n, 0)  # the variants are shapes of the two passes
         for rv in range(7):
             for cv in range(11):
                 sp.set_kernel_variant(n, rv, cv)
@@ -390,6 +391,7 @@ def test_kernel_variants_parity(sp, n):
                 out[(rv, cv)] = got
     finally:
         sp.set_kernel_variant(n, *saved)
+        sp.set_iteration_path(n, spath)
     # same plans give the same bits: row variants 0-4 share the default plan, 5-6 the
     # alternative row plan; column variants 0 and 2-7 the default column plan, 1 and 10 the
     # alternative one (10 falls back to the default plan at 64 and 96); the paired
