@@ -93,8 +93,21 @@ def main():
         out[name] = {"final_error_avg": r["final_error_avg"], "final_error_best": r["final_error_best"],
                      "run_seed": run_seed, "pattern_seed": pseed, "seconds": time.time() - t0,
                      "threads": oracle.get_threads(), "gen_best": r["gen_stats"][:, 0].tolist()}
-        out_path.write_text(json.dumps(out, indent=1))
+        merge_entry(out_path, name, out[name])
         print(name, out[name]["final_error_best"], out[name]["final_error_avg"], flush=True)
+
+
+def merge_entry(path, name, entry):
+    """Add one workload's result to the file under an exclusive lock, re-reading it first, so
+    that several sweeps (over different workloads) can write to it at once."""
+    import fcntl
+    with open(str(path) + ".lock", "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        cur = json.loads(path.read_text()) if path.exists() else {}
+        cur[name] = entry
+        tmp = path.with_suffix(".tmp")
+        tmp.write_text(json.dumps(cur, indent=1))
+        tmp.replace(path)
 
 
 if __name__ == "__main__":
