@@ -84,17 +84,21 @@ __global__ void __launch_bounds__(256) k_smooth_cols(const float* __restrict__ t
 constexpr int SW_CK = 8;  // column outputs per thread
 
 // Radius-specialised smoothing (r = R <= 8, i.e. sigma <= 2), both passes in one kernel: taps
-// in registers, and a block produces a tile of SW_TILE_ROWS rows x 32 columns.  |x| of the tile and its periodic halo (R rows above and below, R columns left
-// and right) is read once into shared memory, the row sums are formed for every row of the
-// halo'd tile, then the column sums from them.  Each output is summed over d = 0..2R in the
-// same order as in the general two-pass kernels above (same bits); the row-smoothed image
-// never goes through HBM.
+// in registers, and a block produces a tile of SW_TILE_ROWS rows x 32 columns.  |x| of the
+// tile and its periodic halo (R rows above and below, R columns left and right) is read once
+// into shared memory, the row sums are formed for every row of the halo'd tile, then the
+// column sums from them.  A row sum thread forms four adjacent outputs from a window of
+// 2R + 4 values that it reads as 16-byte words (one shared-memory load per output instead of
+// 2R + 1).  Each output is summed over d = 0..2R in the same order as in the general
+// two-pass kernels above (same bits); the row-smoothed image never goes through HBM.
 template <int R>
 __global__ void __launch_bounds__(256) k_smooth2d_r(const float2* __restrict__ x, float* __restrict__ out,
                                                     int n, const Taps taps, unsigned* __restrict__ img_max) {
   constexpr int TW = 32, IW = TW + 2 * R, IH = SW_TILE_ROWS + 2 * R;
-  __shared__ float a[IH * IW];  // |x| with halo
-  __shared__ float b[IH * TW];  // row sums
+  constexpr int IWP = (IW + 3) & ~3, NQ = (2 * R + 4 + 3) / 4;  // row pitch; 16-byte words per window
+  static_assert(4 * (TW / 4 - 1) + 4 * NQ <= IWP, "every window inside its row");
+  __shared__ __align__(16) float a[IH * IWP];  // |x| with halo
+  __shared__ __align__(16) float b[IH * TW];   // row sums
   const int tiles_x = n / TW, tiles_y = (n + SW_TILE_ROWS - 1) / SW_TILE_ROWS;
   const int img = blockIdx.x / (tiles_x * tiles_y);
   const int rem = blockIdx.x % (tiles_x * tiles_y);
@@ -126,19 +130,34 @@ __global__ void __launch_bounds__(256) k_smooth2d_r(const float2* __restrict__ x
   for (int q = 0; q < KPW; ++q) {
     const int k = ly + 8 * q;
     if (k < rows_in) {
-      a[k * IW + lx] = sqrtf(va[q].x * va[q].x + va[q].y * va[q].y);
-      if (has_b) a[k * IW + 32 + lx] = sqrtf(vb[q].x * vb[q].x + vb[q].y * vb[q].y);
+      a[k * IWP + lx] = sqrtf(va[q].x * va[q].x + va[q].y * va[q].y);
+      if (has_b) a[k * IWP + 32 + lx] = sqrtf(vb[q].x * vb[q].x + vb[q].y * vb[q].y);
     }
   }
   float w[2 * R + 1];
 #pragma unroll
   for (int d = 0; d <= 2 * R; ++d) w[d] = taps.w[d];
   __syncthreads();
-  for (int k = ly; k < rows_in; k += 8) {
-    float acc = 0.f;
+  for (int item = threadIdx.x; item < rows_in * (TW / 4); item += blockDim.x) {
+    const int k = item / (TW / 4), j = item % (TW / 4);  // row k, outputs 4 j .. 4 j + 3
+    const float4* src = reinterpret_cast<const float4*>(a + k * IWP + 4 * j);
+    float win[4 * NQ];
 #pragma unroll
-    for (int d = 0; d <= 2 * R; ++d) acc = fmaf(w[d], a[k * IW + lx + d], acc);
-    b[k * TW + lx] = acc;
+    for (int q = 0; q < NQ; ++q) {
+      const float4 v = src[q];
+      win[4 * q] = v.x;
+      win[4 * q + 1] = v.y;
+      win[4 * q + 2] = v.z;
+      win[4 * q + 3] = v.w;
+    }
+    float acc[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      acc[o] = 0.f;
+#pragma unroll
+      for (int d = 0; d <= 2 * R; ++d) acc[o] = fmaf(w[d], win[o + d], acc[o]);
+    }
+    *reinterpret_cast<float4*>(b + k * TW + 4 * j) = make_float4(acc[0], acc[1], acc[2], acc[3]);
   }
   __syncthreads();
   unsigned vmax = 0u;
