@@ -443,17 +443,17 @@ __global__ void __launch_bounds__(W * P::T, MINB) k_col(ColArgs a) {
 // The arithmetic is the same unnormalised 2D transform pair as the two passes', in another
 // order of summation.  The column pass, bound by issue rather than HBM, gets shorter
 // transforms; the row pass, bound by HBM, takes the first stage.
-// Q per side: 512 = 2 x 256 (the column pass keeps 256-point transforms of one exchange, the
-// row pass only a butterfly per pixel pair), 1024 = 8 x 128
-template <int N> __host__ __device__ constexpr int split_q() { return N == 512 ? 2 : 8; }
-__host__ __device__ constexpr int split_q_of(int n) { return n == 512 ? 2 : 8; }
+// Q per side: 512 = 2 x 256 and 384 = 3 x 128, 768 = 3 x 256 (the column pass runs
+// power-of-two transforms of one exchange, the row pass a radix-2 or radix-3 butterfly per
+// set of pixels in registers), 1024 = 8 x 128
+__host__ __device__ constexpr int split_q_of(int n) { return n == 512 ? 2 : (n == 384 || n == 768) ? 3 : 8; }
+template <int N> __host__ __device__ constexpr int split_q() { return split_q_of(N); }
 
 template <int N> struct SplitRowPlan : RowAltPlan<N> {};  // row transforms of a split row pass
-// blocks of a split row pass per SM the register budget is sized for (Q = 2 at 512:
-// 128-thread blocks, eight per SM at 64 registers; 1024's sets of 8 rows of 16-element
-// transforms keep one 512-thread block and their registers)
-template <int N> __host__ __device__ constexpr int split_row_minb() { return N <= 512 ? 8 : 1; }
-constexpr bool split_side(int n) { return n == 512 || n == 1024; }
+// blocks per SM the register budget of the 8-row set kernel (Q = 8, at 1024) is sized for:
+// one 512-thread block of 16-element transforms
+template <int N> __host__ __device__ constexpr int split_row_minb() { return 1; }
+constexpr bool split_side(int n) { return n == 384 || n == 512 || n == 768 || n == 1024; }
 // columns per tile of the split column pass: 16 for 256-point chunks, 32 for shorter
 template <int L> __host__ __device__ constexpr int split_col_w() { return L >= 256 ? 16 : 32; }
 
@@ -603,40 +603,46 @@ __global__ void __launch_bounds__(split_q<P::N>() * P::T, split_row_minb<P::N>()
   }
 }
 
-// The split row pass for Q = 2 with both rows of a set in one lane group: rows n1 and
-// n1 + L (L = N / 2) are read at the same columns, so the column transform's first radix-2
-// stage and its inverse run in registers, and the two row transforms follow one another
-// through the group's exchange area.  No shared-memory transposes and no block barriers:
-// ROW_THREADS threads per block, one set per lane group.  The arithmetic is that of
-// k_row_split with Q = 2 (a twiddle W_N^{n1} per set, then an add and a subtract).
-template <class P, int MODE, int ALG, int MINB>
-__global__ void __launch_bounds__(ROW_THREADS, MINB) k_row_pair(SplitArgs a) {
-  constexpr int N = P::N, E = P::E, T = P::T, G = ROW_THREADS / T, L = N / 2, SME = pad_elems_p<P>();
-  static_assert(split_q<N>() == 2 && E * T == N && G * T == ROW_THREADS, "a pair of rows per lane group");
+// The split row pass for Q = 2 or 3 with all rows of a set in one lane group: rows
+// n1 + L n2 (L = N / Q) are read at the same columns, so the column transform's first
+// radix-Q stage and its inverse run in registers, and the Q row transforms follow one
+// another through the group's exchange area.  No shared-memory transposes and no block
+// barriers: one set per lane group.  Each thread parks its own elements of the rows that
+// wait in shared memory (slot j: row j + 1's input, then row j's result), which needs no
+// barrier and keeps one row in registers at a time.  The arithmetic is that of k_row_split
+// with the same Q (the twiddles W_N^{n1 k2}, then a radix-Q DFT).
+template <class P, int MODE, int ALG, int BT, int MINB>
+__global__ void __launch_bounds__(BT, MINB) k_row_group(SplitArgs a) {
+  constexpr int N = P::N, E = P::E, T = P::T, G = BT / T, Q = split_q<N>(), L = N / Q, SME = pad_elems_p<P>();
+  static_assert((Q == 2 || Q == 3) && E * T == N && G * T == BT && L * Q == N, "Q rows per lane group");
   extern __shared__ float2 smem[];
   const int grp = threadIdx.x / T, t = threadIdx.x % T;
   float2* sm = smem + grp * SME;
-  // each thread's own elements of the row that waits: row b's input while row a is processed,
-  // then row a's result while row b is
-  float2* hold = smem + G * SME + grp * N;
+  float2* hold = smem + G * SME + grp * (Q - 1) * N;  // Q - 1 parking slots of N
   const auto sync = GroupSync<T>::make();
   for (long long set = (long long)blockIdx.x * G + grp; set < a.nsets; set += (long long)gridDim.x * G) {
     const long long img = set / L;
     const int n1 = (int)(set % L);
     float2* wi = a.w + img * N * N;
     float2* xi = a.x + img * N * N;
-    const long long ra = (long long)n1 * N, rb = (long long)(n1 + L) * N;  // x rows = chunk rows
-    const float2 wt = __ldg(&a.tw[n1]);  // W_N^{n1}
-    float2 va[E], vb[E];
+    // rows n1 + L n2 of x are the chunk rows k2 L + n1 of w (the same row indices)
+    auto row = [&](int q) { return (long long)(n1 + L * q) * N; };
+    float2 v[E];
     if constexpr (MODE == ROW_ITER) {
 #pragma unroll
       for (int m = 0; m < E; ++m) {  // inverse first stage
-        const float2 y0 = wi[ra + t + m * T], y1 = cmul(wi[rb + t + m * T], cconj(wt));
-        va[m] = cadd(y0, y1);
-        vb[m] = csub(y0, y1);
+        float2 z[Q];
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) z[k2] = wi[row(k2) + t + m * T];
+#pragma unroll
+        for (int k2 = 1; k2 < Q; ++k2) z[k2] = cmul(z[k2], cconj(__ldg(&a.tw[n1 * k2])));
+        DFT<Q, +1>::run(z);
+        v[m] = z[0];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) hold[(q - 1) * N + t + m * T] = z[q];
       }
       // row r of x: inverse transform (m = P_M x_n), update, forward transform
-      auto iterate_row = [&](float2 (&v)[E], long long r) {
+      auto iterate_row = [&](long long r) {
         fft_plan<P, +1, true, 1>(v, sm, t, a.tw, sync);
         const uint32_t* srow = a.Sb + (img * N * N + r) / 32;
         uint32_t sw[E];
@@ -657,35 +663,40 @@ __global__ void __launch_bounds__(ROW_THREADS, MINB) k_row_pair(SplitArgs a) {
         }
         fft_plan<P, -1, true, 1>(v, sm, t, a.tw, sync);  // ends with the group's barrier
       };
+      iterate_row(row(0));
+#pragma unroll 1
+      for (int q = 1; q < Q; ++q) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) hold[t + m * T] = vb[m];
-      iterate_row(va, ra);
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        vb[m] = hold[t + m * T];
-        hold[t + m * T] = va[m];
+        for (int m = 0; m < E; ++m) {  // slot q - 1: row q's input out, row q - 1's result in
+          const float2 nxt = hold[(q - 1) * N + t + m * T];
+          hold[(q - 1) * N + t + m * T] = v[m];
+          v[m] = nxt;
+        }
+        iterate_row(row(q));
       }
-      iterate_row(vb, rb);
-#pragma unroll
-      for (int m = 0; m < E; ++m) va[m] = hold[t + m * T];
     } else {  // ROW_FWD: the forward row transforms of x
 #pragma unroll
-      for (int m = 0; m < E; ++m) va[m] = xi[ra + t + m * T];
-      fft_plan<P, -1, true, 1>(va, sm, t, a.tw, sync);
+      for (int q = 0; q < Q; ++q) {
+        if (q > 0) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        hold[t + m * T] = va[m];
-        vb[m] = xi[rb + t + m * T];
+          for (int m = 0; m < E; ++m) hold[(q - 1) * N + t + m * T] = v[m];
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = xi[row(q) + t + m * T];
+        fft_plan<P, -1, true, 1>(v, sm, t, a.tw, sync);
       }
-      fft_plan<P, -1, true, 1>(vb, sm, t, a.tw, sync);
-#pragma unroll
-      for (int m = 0; m < E; ++m) va[m] = hold[t + m * T];
     }
 #pragma unroll
     for (int m = 0; m < E; ++m) {  // forward first stage, into the chunks
-      const float2 y0 = cadd(va[m], vb[m]), y1 = cmul(csub(va[m], vb[m]), wt);
-      wi[ra + t + m * T] = y0;
-      wi[rb + t + m * T] = y1;
+      float2 y[Q];
+#pragma unroll
+      for (int q = 0; q < Q - 1; ++q) y[q] = hold[q * N + t + m * T];
+      y[Q - 1] = v[m];
+      DFT<Q, -1>::run(y);
+#pragma unroll
+      for (int k2 = 1; k2 < Q; ++k2) y[k2] = cmul(y[k2], __ldg(&a.tw[n1 * k2]));
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) wi[row(k2) + t + m * T] = y[k2];
     }
   }
 }
@@ -1045,19 +1056,26 @@ inline spring_status col_pm_tma_launch(const FftOp& op, cudaStream_t s, bool pre
   return SPRING_OK;
 }
 
+// blocks of the row-group kernel: 256 threads at Q = 2 (registers allow four per SM), 128 at
+// Q = 3 (the parking slots of two more rows per group make shared memory the limit)
+template <int N> constexpr int row_group_threads() { return split_q<N>() == 2 ? ROW_THREADS : 128; }
+template <int N, int MODE> constexpr int row_group_minb() {
+  return split_q<N>() == 2 ? (MODE == ROW_ITER ? 4 : 3) : 4;
+}
+
 template <int N, int MODE, int ALG>
-inline spring_status row_pair_launch(const FftOp& op, cudaStream_t s, bool prep) {
+inline spring_status row_group_launch(const FftOp& op, cudaStream_t s, bool prep) {
   using P = SplitRowPlan<N>;
-  constexpr int G = ROW_THREADS / P::T;
-  const size_t smem = (size_t)G * (pad_elems_p<P>() + P::N) * sizeof(float2);
-  auto kern = k_row_pair<P, MODE, ALG, MODE == ROW_ITER ? 4 : 3>;
+  constexpr int BT = row_group_threads<N>(), G = BT / P::T, Q = split_q<N>();
+  const size_t smem = (size_t)G * (pad_elems_p<P>() + (Q - 1) * P::N) * sizeof(float2);
+  auto kern = k_row_group<P, MODE, ALG, BT, row_group_minb<N, MODE>()>;
   if (prep) return allow_smem(kern, smem);
   long long blocks = (op.sa.nsets + G - 1) / G;
   const long long cap = 64LL * sm_count();
   if (blocks > cap) blocks = cap;
   if (blocks < 1) return SPRING_OK;
   launch_begin(op.kclass, s);
-  kern<<<(int)blocks, ROW_THREADS, smem, s>>>(op.sa);
+  kern<<<(int)blocks, BT, smem, s>>>(op.sa);
   SPRING_CHECK_LAUNCH();
   launch_end(op.kclass, s, op.bytes);
   return SPRING_OK;
@@ -1065,8 +1083,8 @@ inline spring_status row_pair_launch(const FftOp& op, cudaStream_t s, bool prep)
 
 template <int N, int MODE, int ALG>
 inline spring_status row_split_launch(const FftOp& op, cudaStream_t s, bool prep) {
-  if constexpr (split_q<N>() == 2) {  // pairs of rows in one lane group
-    return row_pair_launch<N, MODE, ALG>(op, s, prep);
+  if constexpr (split_q<N>() <= 3) {  // all rows of a set in one lane group
+    return row_group_launch<N, MODE, ALG>(op, s, prep);
   } else {
     using P = SplitRowPlan<N>;
     constexpr bool STAGE = MODE == ROW_ITER;
@@ -1184,7 +1202,7 @@ spring_status run_fft_op(const FftOp& op, cudaStream_t s, bool prep) {
         if (op.alg == 1) return row_split_launch<N, ROW_ITER, 1>(op, s, prep);
         return row_split_launch<N, ROW_ITER, 2>(op, s, prep);
       }
-      return invalid("the split passes cover sides 512 and 1024");
+      return invalid("the split passes cover sides 384, 512, 768 and 1024");
   }
   return invalid("unknown transform operation");
 }

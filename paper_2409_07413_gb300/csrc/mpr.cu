@@ -175,7 +175,7 @@ class Run {
   unsigned* imgmax = nullptr;
   int* status = nullptr;
   float* mavg = nullptr;  // crossover averaging: (M-dot + M-double-dot) / 2
-  float* Msplit = nullptr;  // the K modulus arrays in the split column pass's layout (N = 512, 1024)
+  float* Msplit = nullptr;  // the K modulus arrays in the split column pass's layout (split sides)
   double* m2 = nullptr;     // per pattern: sum of M^2 over its measured pixels (Eq. error_calc)
   // spring_mpr_step's trace (single-pattern runs): the improved parents' errors before
   // Select, and the parent whose area is alpha_best (device buffers owned by the caller)

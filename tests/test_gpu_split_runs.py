@@ -1,7 +1,7 @@
 """Whole runs on the split passes against whole runs on the two passes (iteration paths 2 and
-0) at 512 x 512 and 1024 x 1024: the same patterns and run seeds, many of them, and the
-means of the final errors (of the average reconstruction and of the best individual) within
-the plain 2% of each other.  Both paths compute the same unnormalised 2D transform pair in
+0) at 384 x 384 (Q = 3), 512 x 512 (Q = 2) and 1024 x 1024 (Q = 8): the same patterns and
+run seeds, many of them, and the means of the final errors (of the average reconstruction
+and of the best individual) within the plain 2% of each other.  Both paths compute the same unnormalised 2D transform pair in
 another order of summation; single trajectories part after a few iterations (HIO/RAAR and
 the GA amplify rounding), so the comparison is between the two distributions over seeds.
 With a short schedule the runs take milliseconds, so enough seeds fit that the standard
@@ -23,6 +23,7 @@ def sp():
 
 
 CASES = {
+    "ell384": (dict(pop=16, iters_per_gen=100, generations=4, er_tail=10, sw_period=20), 200),
     "ell512": (dict(pop=16, iters_per_gen=100, generations=4, er_tail=10, sw_period=20), 200),
     "ell1024": (dict(pop=8, iters_per_gen=100, generations=3, er_tail=10, sw_period=20), 100),
 }
