@@ -298,7 +298,8 @@ spring_status spring_project_modulus(const void* x, void* out, const float* M, i
  *   RAAR: x' = m on C, beta x + (1 - 2 beta) m elsewhere.
  * S: batch supports.  x must be 16-byte aligned (the row passes stream it into shared memory
  * in 16-byte copies; every device allocation is); INVALID otherwise.  Scratch: one
- * batch x N x N complex64 work buffer and the supports packed to bits. */
+ * batch x N x N complex64 work buffer, the supports packed to bits and, where the side runs
+ * the split passes (spring_set_iteration_path), M in their chunked layout. */
 spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batch, int n,
                              int algorithm, float beta, float chi, int n_iter, void* stream);
 
