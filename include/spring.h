@@ -465,13 +465,13 @@ spring_status spring_get_kernel_variant(int n, int* row_variant, int* col_varian
 spring_status spring_autotune(int n, int batch, void* stream);
 /* How runs iterate at side n: 0 = two passes through HBM per iteration (row pass, column
  * pass), 1 = the on-chip kernel of spring_iterate_fused (N <= 256; INVALID where the
- * device cannot hold its clusters), 2 = the split passes (N = 384, 512, 768, 1024): the
- * column transform is decimated in frequency over the rows, n = n1 + (N/Q) n2, its first
- * radix-Q stage runs in the row pass on the Q rows n1 + (N/Q) n2 (Q = 3 at 384 and 768,
- * 2 at 512: all rows of a set in one lane group, the stage in registers; Q = 8 at 1024: one
- * block per set of 8 rows) and the column pass transforms N/Q-point chunks (the same sums
- * in another order).  The autotuner picks the fastest; an explicit choice is kept; until
- * either, the fastest measured on a GB300 (2 at 384-1024, 0 elsewhere). */
+ * device cannot hold its clusters), 2 = the split passes (N = 192, 384, 512, 768, 1024):
+ * the column transform is decimated in frequency over the rows, n = n1 + (N/Q) n2, its
+ * first radix-Q stage runs in the row pass on the Q rows n1 + (N/Q) n2 (Q = 3 at 192, 384
+ * and 768, 2 at 512: all rows of a set in one lane group, the stage in registers; Q = 8 at
+ * 1024: one block per set of 8 rows) and the column pass transforms N/Q-point chunks (the
+ * same sums in another order).  The autotuner picks the fastest; an explicit choice is
+ * kept; until either, the fastest measured on a GB300 (2 at 192 and 384-1024, 0 elsewhere). */
 spring_status spring_set_iteration_path(int n, int path);
 spring_status spring_get_iteration_path(int n, int* path);
 

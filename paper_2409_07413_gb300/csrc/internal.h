@@ -8,7 +8,7 @@ namespace spring {
 
 // ---------------------------------------------------------------- k_fft.cu
 // iteration row pass: w (column-pass output) -> P_M x -> update -> x, rowFFT(x) -> w
-// split passes (sides 384, 512, 768 and 1024; k_fft.cuh): the modulus permuted to the chunked layout,
+// split passes (sides 192, 384, 512, 768 and 1024; k_fft.cuh): the modulus permuted to the chunked layout,
 // the split row pass (fwd_only: forward row transforms and first stage of x alone), the
 // split column pass, and k iterations of the two
 bool split_supported(int n);

@@ -49,10 +49,10 @@ static int g_row_var[N_SIDES] = {0, 6, 5, 6, 0, 6, 6, 6, 5};
 static int g_col_var[N_SIDES] = {0, 1, 2, 1, 0, 0, 0, 1, 1};
 static bool g_tuned[N_SIDES] = {};
 // iteration path per side: 0 = the two passes through HBM, 1 = the on-chip cluster kernel
-// (N <= 256, k_cluster.cu), 2 = the split passes (N = 384, 512, 768, 1024: the column
+// (N <= 256, k_cluster.cu), 2 = the split passes (N = 192, 384, 512, 768, 1024: the column
 // transform's first radix-Q stage in the row pass); chosen by the autotuner, until then the
-// fastest measured on a GB300 (the split passes at all four)
-static int g_path[N_SIDES] = {0, 0, 0, 0, 0, 2, 2, 2, 2};
+// fastest measured on a GB300 (the split passes at all five)
+static int g_path[N_SIDES] = {0, 0, 0, 2, 0, 2, 2, 2, 2};
 
 int iteration_path(int n) {
   const int si = side_index(n);
@@ -328,7 +328,7 @@ spring_status launch_row_init16(int n, const float2* x, void* xh, void* wh, long
   return dispatch(n, op, s);
 }
 
-// ------------------------------------------------------------------ split passes (N = 384, 512, 768, 1024)
+// ------------------------------------------------------------------ split passes (N = 192, 384, 512, 768, 1024)
 bool split_supported(int n) { return split_side(n); }
 
 // the modulus in the split column pass's chunked layout: row k2 L + k1 of Mp is row
@@ -344,7 +344,7 @@ __global__ void k_split_modulus(const float* __restrict__ M, float* __restrict__
 }
 
 spring_status launch_split_modulus(int n, const float* M, float* Mp, int K, cudaStream_t s) {
-  if (!split_side(n)) return invalid("the split passes cover sides 384, 512, 768 and 1024");
+  if (!split_side(n)) return invalid("the split passes cover sides 192, 384, 512, 768 and 1024");
   const long long total = (long long)K * n * n;
   const long long blocks = div_up(total, 256) < 16LL * sm_count() ? div_up(total, 256) : 16LL * sm_count();
   launch_begin(SPRING_KC_OTHER, s);
@@ -357,7 +357,7 @@ spring_status launch_split_modulus(int n, const float* M, float* Mp, int K, cuda
 // the split row pass: fwd_only = the forward row transforms and first stage from x alone
 spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2* x, const uint32_t* Sb,
                                long long batch, float beta, float chi, cudaStream_t s) {
-  if (!split_side(n)) return invalid("the split passes cover sides 384, 512, 768 and 1024");
+  if (!split_side(n)) return invalid("the split passes cover sides 192, 384, 512, 768 and 1024");
   if (alg < 0 || alg > 2) return invalid("algorithm must be 0 (ER), 1 (HIO) or 2 (RAAR)");
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
@@ -379,7 +379,7 @@ spring_status launch_row_split(int n, int alg, bool fwd_only, float2* w, float2*
 }
 
 spring_status launch_col_split(int n, float2* w, const float* Mp, int batch, cudaStream_t s, int m_group) {
-  if (!split_side(n)) return invalid("the split passes cover sides 384, 512, 768 and 1024");
+  if (!split_side(n)) return invalid("the split passes cover sides 192, 384, 512, 768 and 1024");
   DeviceTables tb;
   SPRING_TRY(device_tables(&tb));
   FftOp op;
@@ -628,7 +628,7 @@ spring_status autotune_n(int n, int batch, cudaStream_t s) {
     SPRING_TRY(st);
     path = one < two ? 1 : 0;
   }
-  // the split passes (N = 384, 512, 768, 1024) against the two passes with the chosen variants over a
+  // the split passes (N = 192-1024) against the two passes with the chosen variants over a
   // block of 20 iterations
   if (split_side(n)) {
     constexpr int K = 20;
@@ -721,7 +721,7 @@ spring_status spring_set_iteration_path(int n, int path) {
   const int si = side_index(n);
   if (si < 0) return invalid("unsupported pattern side");
   if (path < 0 || path > 2) return invalid("path must be 0 (two passes), 1 (on chip) or 2 (split passes)");
-  if (path == 2 && !split_side(n)) return invalid("the split passes cover sides 384, 512, 768 and 1024");
+  if (path == 2 && !split_side(n)) return invalid("the split passes cover sides 192, 384, 512, 768 and 1024");
   if (path == 1) {
     bool ok = false;
     SPRING_TRY(cluster_supported(n, &ok));

@@ -443,17 +443,19 @@ __global__ void __launch_bounds__(W * P::T, MINB) k_col(ColArgs a) {
 // The arithmetic is the same unnormalised 2D transform pair as the two passes', in another
 // order of summation.  The column pass, bound by issue rather than HBM, gets shorter
 // transforms; the row pass, bound by HBM, takes the first stage.
-// Q per side: 512 = 2 x 256 and 384 = 3 x 128, 768 = 3 x 256 (the column pass runs
-// power-of-two transforms of one exchange, the row pass a radix-2 or radix-3 butterfly per
-// set of pixels in registers), 1024 = 8 x 128
-__host__ __device__ constexpr int split_q_of(int n) { return n == 512 ? 2 : (n == 384 || n == 768) ? 3 : 8; }
+// Q per side: 512 = 2 x 256 and 192 = 3 x 64, 384 = 3 x 128, 768 = 3 x 256 (the column pass
+// runs power-of-two transforms of one exchange, the row pass a radix-2 or radix-3 butterfly
+// per set of pixels in registers), 1024 = 8 x 128
+__host__ __device__ constexpr int split_q_of(int n) {
+  return n == 512 ? 2 : (n == 192 || n == 384 || n == 768) ? 3 : 8;
+}
 template <int N> __host__ __device__ constexpr int split_q() { return split_q_of(N); }
 
 template <int N> struct SplitRowPlan : RowAltPlan<N> {};  // row transforms of a split row pass
 // blocks per SM the register budget of the 8-row set kernel (Q = 8, at 1024) is sized for:
 // one 512-thread block of 16-element transforms
 template <int N> __host__ __device__ constexpr int split_row_minb() { return 1; }
-constexpr bool split_side(int n) { return n == 384 || n == 512 || n == 768 || n == 1024; }
+constexpr bool split_side(int n) { return n == 192 || n == 384 || n == 512 || n == 768 || n == 1024; }
 // columns per tile of the split column pass: 16 for 256-point chunks, 32 for shorter
 template <int L> __host__ __device__ constexpr int split_col_w() { return L >= 256 ? 16 : 32; }
 
@@ -1202,7 +1204,7 @@ spring_status run_fft_op(const FftOp& op, cudaStream_t s, bool prep) {
         if (op.alg == 1) return row_split_launch<N, ROW_ITER, 1>(op, s, prep);
         return row_split_launch<N, ROW_ITER, 2>(op, s, prep);
       }
-      return invalid("the split passes cover sides 384, 512, 768 and 1024");
+      return invalid("the split passes cover sides 192, 384, 512, 768 and 1024");
   }
   return invalid("unknown transform operation");
 }

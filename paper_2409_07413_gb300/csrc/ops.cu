@@ -366,7 +366,7 @@ spring_status spring_iterate(void* x, const uint8_t* S, const float* M, int batc
   uint32_t* Sb = reinterpret_cast<uint32_t*>(static_cast<char*>(w.p) + wbytes);
   SPRING_TRY(launch_pack_support(S, Sb, (long long)batch * n * n, s));
   float2* xs = static_cast<float2*>(x);
-  if (split) {  // the split passes (sides 384, 512, 768, 1024)
+  if (split) {  // the split passes (sides 192-1024)
     float* Mp = reinterpret_cast<float*>(static_cast<char*>(w.p) + wbytes + sbytes);
     SPRING_TRY(launch_split_modulus(n, M, Mp, 1, s));
     SPRING_TRY(launch_row_split(n, algorithm, true, w.as<float2>(), xs, nullptr, batch, beta, chi, s));

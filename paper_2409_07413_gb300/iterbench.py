@@ -139,7 +139,7 @@ def main():
     ap.add_argument("--variant", type=int, nargs=2, default=None, metavar=("ROW", "COL"),
                     help="launch-shape variants of the two passes (default: the built-in defaults)")
     ap.add_argument("--path", type=int, default=None,
-                    help="iteration path: 0 two passes, 1 on chip (N <= 256), 2 split passes (384-1024); "
+                    help="iteration path: 0 two passes, 1 on chip (N <= 256), 2 split passes (192-1024); "
                          "with --variant or --sweep and no --path, 0 (the variants are shapes of the two passes)")
     a = ap.parse_args()
     if (a.variant or a.sweep) and a.path is None:

@@ -472,8 +472,8 @@ def autotune(n, batch):
 # ------------------------------------------------------------------ instrumentation
 def set_iteration_path(n, path):
     """0: two passes through HBM per iteration; 1: on chip (N <= 256); 2: the split passes
-    (N = 384, 512, 768, 1024: the column transform's first radix-Q stage in the row pass,
-    Q = 3 at 384 and 768, 2 at 512, 8 at 1024)."""
+    (N = 192, 384, 512, 768, 1024: the column transform's first radix-Q stage in the row
+    pass, Q = 3 at 192, 384 and 768, 2 at 512, 8 at 1024)."""
     _call("spring_set_iteration_path", int(n), int(path))
 
 

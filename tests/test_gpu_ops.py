@@ -417,14 +417,14 @@ def test_autotune_picks_a_valid_variant(sp):
 
 
 # ----------------------------------------------------------------------------- split passes
-SPLIT_SIDES = [384, 512, 768, 1024]
+SPLIT_SIDES = [192, 384, 512, 768, 1024]
 
 
 @pytest.fixture
 def split_path(sp):
     """The split passes (the column transform's first radix-Q stage in the row pass: Q = 3
-    at 384 and 768 and Q = 2 at 512, all rows of a set in one lane group; Q = 8 at 1024) for
-    every split side, restoring each side's iteration path afterwards."""
+    at 192, 384 and 768 and Q = 2 at 512, all rows of a set in one lane group; Q = 8 at 1024)
+    for every split side, restoring each side's iteration path afterwards."""
     saved = {n: sp.get_iteration_path(n) for n in SPLIT_SIDES}
     for n in saved:
         sp.set_iteration_path(n, 2)
@@ -468,7 +468,7 @@ def test_split_iterate_many_steps(sp, split_path, n):
     assert rel(host(xg), ref) < max(TOL, 3.0 * drift32)
 
 
-@pytest.mark.parametrize("n,B", [(384, 24), (512, 12), (768, 6), (1024, 4)])
+@pytest.mark.parametrize("n,B", [(192, 48), (384, 24), (512, 12), (768, 6), (1024, 4)])
 @pytest.mark.parametrize("alg", [1, 2])
 def test_split_iterate_many_sets_per_block(sp, split_path, n, B, alg):
     # batches of more sets (Q rows each) than the row pass has resident blocks: every block
@@ -489,7 +489,7 @@ def test_split_iterate_many_sets_per_block(sp, split_path, n, B, alg):
 
 
 def test_iteration_path_arguments(sp):
-    # the split passes cover 384, 512, 768 and 1024 only; paths past 2 do not exist
+    # the split passes cover 192, 384, 512, 768 and 1024 only; paths past 2 do not exist
     saved = sp.get_iteration_path(256), sp.get_iteration_path(512)
     try:
         for n, path in ((256, 2), (512, 3), (512, -1)):
